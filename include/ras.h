@@ -1,0 +1,230 @@
+/*
+ * ras.h - C ABI of the GB300 (sm_103a) RAS / RASPEN solver.
+ *
+ * The library solves the eps-smoothed, reduced first-order optimality system
+ * of the L1-regularised semilinear elliptic optimal control problem (P) of
+ * Ciaramella, Kartmann & Mueller, arXiv 2411.00546:
+ *
+ *   F_y = A y + phi(y) - f + (1/nu) (p + mu P_eps(-p/mu)) = 0
+ *   F_p = A p + phi'(y) p - y + y_d                     = 0      (Sec. 3.3)
+ *
+ * on Omega = (0,1)^2 with A = -Laplace (5-point finite differences, zero
+ * Dirichlet data) and P_eps the smoothed projection of Sec. 3.1, by the
+ * restricted-additive-Schwarz methods of Sec. 4: the nonlinear RAS function
+ * (Alg. 3), RASPEN (Alg. 2) and Newton_RAS (Alg. 1 with RAS-preconditioned
+ * GMRES).
+ *
+ * Conventions for every entry point:
+ *  - Grid functions (y, p, y_d, f, residuals, directions) are n*n FP64 arrays,
+ *    row-major with the x1 index fastest: element [j*n + i] is the node
+ *    ((i+1)h, (j+1)h), h = 1/(n+1). Pointers are DEVICE pointers unless the
+ *    name says _host. The caller owns them; they must stay valid for the call.
+ *  - The library allocates (cudaMalloc) and owns its internal buffers
+ *    (local factors, Krylov basis, scratch) from ras_create until ras_destroy.
+ *  - All GPU work is enqueued on the CUDA stream given to ras_create. Every
+ *    call returns after that work is complete (it synchronises the stream).
+ *  - Return value: RAS_OK (0) or a positive success variant, or a negative
+ *    RAS_E* code. After an error, ras_last_error() describes it. A CUDA error
+ *    is reported as RAS_ECUDA and leaves the handle usable only for
+ *    ras_destroy.
+ *  - One problem handle may be used by one host thread at a time.
+ */
+#ifndef RAS_H
+#define RAS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- status */
+#define RAS_OK           0   /* converged by the tolerance test               */
+#define RAS_OK_FLOOR     1   /* converged: residual at FP64 rounding level     */
+#define RAS_EINVAL      -1   /* invalid argument                               */
+#define RAS_ENOMEM      -2   /* device allocation failed                       */
+#define RAS_ENOCONV     -3   /* iteration limit reached (Alg. 1 / Alg. 2 kmax) */
+#define RAS_ESINGULAR   -5   /* zero pivot in a local factorisation            */
+#define RAS_ENONFINITE  -6   /* NaN or Inf in a residual                       */
+#define RAS_ENOTIMPL    -8   /* not available in this build                    */
+#define RAS_ECUDA       -9   /* CUDA runtime error                             */
+#define RAS_ESTATE     -10   /* call needs state that is not there (e.g. a JVP
+                                 before any ras_apply)                          */
+
+/* Nonlinearity phi of the state equation (Assumption 1: C^2, increasing). */
+#define RAS_PHI_CUBIC 0      /* phi(y) = y^3                                  */
+#define RAS_PHI_EXP   1      /* phi(y) = exp(y)                               */
+#define RAS_PHI_KAPPA 2      /* phi(y) = kappa (y^3 + exp(kappa y)), Sec. 4   */
+
+/* Arithmetic of the local factorisations and solves. */
+#define RAS_FP64  0          /* everything in FP64                            */
+#define RAS_MIXED 1          /* FP32 local factors and solves; FP64 residuals,
+                                iterative refinement of every local Newton
+                                direction in FP64, FP64 GMRES, line search and
+                                stop tests                                     */
+
+/* Solver parameters. ras_default_opts fills the paper's values (Sec. 5). */
+typedef struct {
+    double tol;            /* outer tolerance (Alg. 1 / Alg. 2), 1e-10      */
+    double inner_tol;      /* tolerance of the local Newton solves, 1e-8     */
+    double sigma;          /* relaxed backtracking parameter, 1.1            */
+    double eps0;           /* initial smoothing parameter, 1                 */
+    double gamma;          /* continuation factor eps <- max(gamma eps, eps_min), 1/5 */
+    double eps_min;        /* target smoothing parameter                     */
+    int    kmax_outer_raspen;   /* 50  */
+    int    kmax_outer_newton;   /* 200 */
+    int    kmax_inner;          /* 100 */
+    int    max_halvings;        /* 20: backtracking halvings per step         */
+    int    gmres_restart;       /* 30  */
+    int    gmres_maxit;         /* 1000 total Krylov steps per linear solve    */
+    double gmres_rtol;          /* 1e-8 relative to the right-hand side        */
+    double floor_factor;        /* 16: rounding-floor stop multiplier          */
+    int    precision;           /* RAS_FP64 or RAS_MIXED                       */
+    int    ir_max;              /* mixed: max refinement corrections, 6        */
+    double ir_rtol;             /* mixed: refine until ||r|| <= ir_rtol ||b||, 1e-12 */
+    double kappa;               /* parameter of RAS_PHI_KAPPA, 0.1             */
+    int    jvp_ir;              /* mixed: FP64 refinement corrections of every
+                                   local solve inside the Jacobian action of
+                                   Alg. 4, 1 (0 = plain FP32 solves)            */
+    int    reserved;            /* must be 0                                   */
+} ras_opts;
+
+/* Counters of the last solve or RASPEN-function evaluation. */
+typedef struct {
+    int    status;         /* RAS_OK, RAS_OK_FLOOR or RAS_E*                  */
+    int    outer_its;      /* outer Newton steps (RASPEN or Newton_RAS)       */
+    int    gmres_its;      /* Krylov steps, summed over the outer steps       */
+    int    evaluations;    /* RASPEN-function evaluations (Alg. 3 calls)      */
+    int    inner_its_max;  /* max local Newton steps of one subdomain, summed
+                              over evaluations                                  */
+    long long inner_its_sum;  /* sum over subdomains and evaluations         */
+    int    halvings;       /* backtracking halvings, all levels               */
+    int    exhausted;      /* steps taken after max_halvings failed halvings  */
+    int    local_failures; /* local solves that ended with a negative status  */
+    double res0;           /* ||F(x0)|| (Newton_RAS) or ||RASPEN F(x0)||       */
+    double res;            /* final norm of the same quantity                 */
+    double eps_final;      /* smoothing parameter of the final iterate        */
+} ras_stats;
+
+typedef struct ras_problem ras_problem;
+
+/* Fill *o with the paper's settings (Sec. 5): tol 1e-10, inner_tol 1e-8,
+ * sigma 1.1, eps0 1, gamma 1/5, eps_min 1e-6 (the paper sweeps eps_min), and
+ * this library's defaults for the unspecified rest. Returns RAS_EINVAL on NULL. */
+int ras_default_opts(ras_opts* o);
+
+/* Create a problem on an n x n grid split into sx x sy non-overlapping blocks
+ * (balanced sizes, larger blocks first), each grown by `overlap` node layers on
+ * every side and clipped at the boundary (Sec. 4.2).
+ *   phi      RAS_PHI_*; nu, mu > 0 are the cost weights of (P) (Sec. 1).
+ *   y_d      device, n*n, copied (the caller keeps ownership).
+ *   f        device, n*n, copied; NULL means f = 0.
+ *   o        options (copied); NULL means ras_default_opts.
+ *   stream   cudaStream_t to use, NULL for the legacy default stream.
+ * Limits: n >= 2, 1 <= sx, sy <= n, overlap >= 0, and every local block row
+ * has 2*wx <= 160 unknowns (wx = subdomain width in nodes) -> RAS_EINVAL.
+ * On success *out receives the handle. */
+int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu,
+               const double* y_d, const double* f, const ras_opts* o,
+               void* stream, ras_problem** out);
+
+/* Set the target smoothing parameter eps_min (> 0; P_eps is not smooth at 0). */
+int ras_set_eps(ras_problem* h, double eps_min);
+
+/* Replace the options (validated as in ras_create; layout fixed at create). */
+int ras_set_opts(ras_problem* h, const ras_opts* o);
+
+/* Replace y_d (and f; NULL means 0). Device pointers, n*n, copied. */
+int ras_set_data(ras_problem* h, const double* y_d, const double* f);
+
+/* F(x, eps) of Sec. 3.3 at x = (y, p): writes Fy, Fp (device, n*n; either may
+ * be NULL) and, if norm_host != NULL, ||(Fy, Fp)||_2 to *norm_host. */
+int ras_residual(ras_problem* h, const double* y, const double* p, double eps,
+                 double* Fy, double* Fp, double* norm_host);
+
+/* The RASPEN function of Alg. 3 / Sec. 4.2 at x = (y, p):
+ *   F_eps(x) = sum_i tilde P_i C_i(x),  R_i F_eps(x + P_i C_i(x)) = 0,
+ * each C_i computed by Alg. 1 from 0 with a direct local solve; with
+ * continuation != 0 the local solves run eps from eps0 down to eps_min, else
+ * they start at eps_min. Writes Fy, Fp (device, n*n). Keeps the local
+ * Jacobians factorised at x^(i) = x + P_i C_i(x) for ras_jvp. *stats (may be
+ * NULL) receives the local iteration counts. Returns the worst local status. */
+int ras_apply(ras_problem* h, const double* y, const double* p, int continuation,
+              double* Fy, double* Fp, ras_stats* stats);
+
+/* Jacobian action of the RASPEN function at the x of the last ras_apply
+ * (Alg. 4): out = F_eps'(x) d = -d - sum_i tilde P_i J_i(x^(i))^-1 B_i d,
+ * where B_i d = R_i A (I - P_i R_i) d is the coupling of d outside Omega_i
+ * (the transmission identity of Sec. 4.2). Device n*n arrays.
+ * RAS_ESTATE if no ras_apply has run. */
+int ras_jvp(ras_problem* h, const double* dy, const double* dp, double* oy, double* op);
+
+/* Linear RAS preconditioner at x (Newton_RAS, Sec. 4.1):
+ *   z = sum_i tilde P_i (R_i F_eps'(x) P_i)^-1 R_i r.
+ * Factorises the local Jacobians at (x, eps), then applies them to r. */
+int ras_precondition(ras_problem* h, const double* y, const double* p, double eps,
+                     const double* ry, const double* rp, double* zy, double* zp);
+
+/* RASPEN (Alg. 2): Newton on F_eps(x) = 0 with x <- x + d, d from GMRES with
+ * the action of Alg. 4; eps-continuation only in the local solves of the first
+ * evaluation. (y, p): device n*n, initial guess on entry, solution on exit. */
+int ras_raspen_solve(ras_problem* h, double* y, double* p, ras_stats* stats);
+
+/* Newton_RAS (Alg. 1 on F_eps(x) = 0, eps-continuation when eps0 > eps_min,
+ * GMRES right-preconditioned by linear RAS). In/out as ras_raspen_solve. */
+int ras_newton_ras_solve(ras_problem* h, double* y, double* p, ras_stats* stats);
+
+#define RAS_METHOD_RASPEN     0
+#define RAS_METHOD_NEWTON_RAS 1
+/* End-to-end call on HOST buffers: copies y_d_host (n*n, NULL keeps the
+ * current y_d) and the initial guess y_host, p_host to the device, solves with
+ * `method`, and copies the solution back into y_host, p_host. */
+int ras_solve_host(ras_problem* h, int method, const double* y_d_host,
+                   double* y_host, double* p_host, ras_stats* stats);
+
+/* Local Newton step counts of the last ras_apply, one per subdomain (index
+ * i = by*sx + bx), into its_host[0..count). Returns the number written. */
+int ras_local_iterations(const ras_problem* h, int* its_host, int count);
+
+/* Number of subdomains; device bytes held by the handle. */
+int ras_subdomain_count(const ras_problem* h);
+size_t ras_device_bytes(const ras_problem* h);
+
+/* Text of the last error on this handle (never NULL). */
+const char* ras_last_error(const ras_problem* h);
+
+/* Release every device buffer of the handle. NULL is a no-op. */
+void ras_destroy(ras_problem* h);
+
+/* Kernel launches issued by this library since load (all handles). */
+long long ras_launch_count(void);
+
+/* Live kernel timing (diagnostics; not part of the paper's method).
+ * ras_profile(h, 1) clears the counters and records a CUDA event pair on the
+ * handle's stream around every kernel launch until ras_profile(h, 0).
+ * ras_profile_read returns, for one kernel kind, the summed device time (ms),
+ * the number of launches and the summed algorithmic work of those launches:
+ *   RAS_K_FACTOR     flops, 16 wx^3 wy per factorised subdomain (the
+ *                    no-fill band-LU count 2 N_loc kl ku with kl = ku = 2 wx)
+ *   RAS_K_DIRECTION  bytes of factor blocks read (2 passes per local solve)
+ *   RAS_K_JVP, RAS_K_PRECOND  bytes of factor blocks read (2 passes)
+ *   RAS_K_RESIDUAL   bytes (y, p, y_d, f read once, F written once)
+ *   others           0
+ * Returns RAS_EINVAL for an unknown kind. */
+#define RAS_K_INIT       0
+#define RAS_K_FACTOR     1
+#define RAS_K_DIRECTION  2
+#define RAS_K_LINESEARCH 3
+#define RAS_K_JVP        4
+#define RAS_K_PRECOND    5
+#define RAS_K_RESIDUAL   6
+#define RAS_K_KRYLOV     7
+#define RAS_K_OTHER      8
+#define RAS_K_COUNT      9
+int ras_profile(ras_problem* h, int enable);
+int ras_profile_read(ras_problem* h, int kind, double* ms, long long* launches, double* work);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAS_H */

@@ -1,0 +1,192 @@
+// Internal declarations of the RAS / RASPEN CUDA library (sm_103a).
+//
+// Layout in HBM
+//  * grid functions: n*n FP64, row-major, x1 index fastest (node (i, j) at
+//    [j*n + i]); global Krylov vectors are planar [y-plane | p-plane], 2*n*n.
+//  * per subdomain i (box Omega_i of wx*wy nodes at (x0, y0)):
+//      local vectors: 2*wx*wy FP64, interleaved (y, p) per node, nodes
+//                     lexicographic with the x1 index fastest, at voff;
+//      node arrays:   wx*wy FP64 (Jacobian coefficients), at noff;
+//      factors:       wy blocks G_j of (2wx)^2 T (row-major), at goff, where
+//                     G_j is the inverse of the j-th Schur complement of the
+//                     block-tridiagonal local Jacobian.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ras {
+
+constexpr int MAX_M = 160;          // max unknowns of one local block row (2*wx)
+constexpr int FACT_THREADS = 256;   // threads of the factorisation kernel
+constexpr int LOC_THREADS = 256;    // threads of the per-subdomain kernels
+constexpr int VEC_THREADS = 256;    // threads of the grid-stride vector kernels
+constexpr int VEC_BLOCKS = 608;     // 4 x 152 SMs: fixed grid => fixed reduction order
+
+struct ProbDev {
+    int n;
+    int phi;
+    double h, beta, nu, mu, kappa;
+    const double* yd;
+    const double* f;      // nullptr means f = 0
+    long long ofs;        // offset of this problem's y-plane in every global
+                          // vector buffer; its p-plane follows at ofs + n*n
+};
+
+struct SubDev {
+    int prob;
+    int x0, y0, wx, wy;       // Omega_i
+    int ox0, oy0, owx, owy;   // tilde Omega_i (owned nodes)
+    long long goff;           // factor offset (elements of T)
+    long long voff;           // local-vector offset (doubles), length 2*wx*wy
+    long long noff;           // node-array offset (doubles), length wx*wy
+};
+
+// State of Alg. 1 for one subdomain.
+struct LocalState {
+    double eps, nrm, nrm0, stop, flr;
+    int k, status, active, halvings, exhausted, solves;   // solves: local solves done
+};
+
+struct NewtonParams {
+    double eps_min, gamma, sigma, tol, floor_factor, ir_rtol;
+    int kmax, max_halvings, ir_max, pad;
+};
+
+// Status values (same numbers as the public RAS_* codes).
+constexpr int ST_OK = 0;
+constexpr int ST_OK_FLOOR = 1;
+constexpr int ST_ENOCONV = -3;
+constexpr int ST_ESINGULAR = -5;
+constexpr int ST_ENONFINITE = -6;
+
+// ------------------------------------------------------------- pointwise math
+// Smoothed projection of Sec. 3.1 in the cancellation-free quotient form of
+// Lemma 5's proof: P_eps(x) = 2x / (sqrt((x+1)^2+eps) + sqrt((x-1)^2+eps)).
+__device__ __forceinline__ double P_eps(double x, double eps) {
+    double a = x + 1.0, b = x - 1.0;
+    return 2.0 * x / (sqrt(a * a + eps) + sqrt(b * b + eps));
+}
+
+// P_eps'(x) = ((x+1)/sqrt((x+1)^2+eps) - (x-1)/sqrt((x-1)^2+eps)) / 2 (Sec. 3.1).
+__device__ __forceinline__ double dP_eps(double x, double eps) {
+    double a = x + 1.0, b = x - 1.0;
+    return 0.5 * (a / sqrt(a * a + eps) - b / sqrt(b * b + eps));
+}
+
+// phi, phi', phi'' of the three nonlinearities.
+__device__ __forceinline__ void phi_eval(int kind, double kappa, double y,
+                                         double& ph, double& d1, double& d2) {
+    if (kind == 0) {
+        double y2 = y * y;
+        ph = y2 * y; d1 = 3.0 * y2; d2 = 6.0 * y;
+    } else if (kind == 1) {
+        double e = exp(y);
+        ph = e; d1 = e; d2 = e;
+    } else {
+        double e = exp(kappa * y);
+        ph = kappa * (y * y * y + e);
+        d1 = kappa * (3.0 * y * y + kappa * e);
+        d2 = kappa * (6.0 * y + kappa * kappa * e);
+    }
+}
+
+// eps_{k+1} = max(gamma eps_k, eps_min), with a product within a relative 1e-9
+// of eps_min taken as eps_min (the FP64 rounding of the geometric sequence).
+__device__ __host__ __forceinline__ double next_eps(double eps, double gamma, double eps_min) {
+    double e = gamma * eps;
+    return (e <= eps_min * (1.0 + 1e-9)) ? eps_min : e;
+}
+
+// Deterministic block sum of two values (fixed tree over the threads).
+template <int NT>
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
+    const int t = threadIdx.x;
+    red[t] = a;
+    red[NT + t] = b;
+    __syncthreads();
+#pragma unroll
+    for (int s = NT / 2; s > 0; s >>= 1) {
+        if (t < s) {
+            red[t] += red[t + s];
+            red[NT + t] += red[NT + t + s];
+        }
+        __syncthreads();
+    }
+    a = red[0];
+    b = red[NT];
+    __syncthreads();
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum1(double a, double* red) {
+    const int t = threadIdx.x;
+    red[t] = a;
+    __syncthreads();
+#pragma unroll
+    for (int s = NT / 2; s > 0; s >>= 1) {
+        if (t < s) red[t] += red[t + s];
+        __syncthreads();
+    }
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace ras
+
+// ------------------------------------------------------------- launchers
+// Implemented in the .cu files; every launcher returns the cudaError_t of
+// its launch and counts the launch.
+namespace ras {
+void count_launch();
+
+// global (grid) kernels: residual.cu
+cudaError_t launch_residual_global(cudaStream_t st, const ProbDev& P, const double* y, const double* p,
+                                   const double* dy, const double* dp, double alpha, double eps,
+                                   double* Fy, double* Fp, double* partials);
+cudaError_t launch_reduce_partials(cudaStream_t st, const double* partials, int nparts, int nvals,
+                                   double* out);
+cudaError_t launch_coef_global(cudaStream_t st, const ProbDev& P, const double* y, const double* p,
+                               double eps, double* coef);
+cudaError_t launch_jacvec_global(cudaStream_t st, const ProbDev& P, const double* coef,
+                                 const double* vy, const double* vp, double* oy, double* op);
+cudaError_t launch_dot_multi(cudaStream_t st, const double* V, long long ld, int nv, const double* w,
+                             long long len, double* partials);
+cudaError_t launch_axpy_multi(cudaStream_t st, const double* V, long long ld, int nv, const double* h,
+                              double sign, double* w, long long len);
+cudaError_t launch_scale_copy(cudaStream_t st, const double* src, const double* num, const double* den,
+                              double sign, double* dst, long long len);
+cudaError_t launch_axpy(cudaStream_t st, double a, const double* x, double* y, long long len);
+cudaError_t launch_add_scaled(cudaStream_t st, const double* x, const double* d, double alpha,
+                              double* out, long long len);
+
+// per-subdomain kernels: local.cu. X, F, D, O, R, Z are global vector bases
+// (problem k at ProbDev.ofs); pools are indexed by SubDev offsets.
+cudaError_t launch_local_init(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,
+                              const double* X, LocalState* ls, double eps_start, NewtonParams np,
+                              double* cpool, double* Kpool, int* active_count);
+template <typename T>
+cudaError_t launch_local_factor(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
+                                const ProbDev* probs, const double* X, LocalState* ls,
+                                const double* cpool, double* coef, T* gpool, int only_active);
+template <typename T>
+cudaError_t launch_local_direction(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
+                                   const ProbDev* probs, LocalState* ls, NewtonParams np,
+                                   const double* coef, const T* gpool, const double* Kpool,
+                                   double* dpool, double* rpool, T* wpool);
+cudaError_t launch_local_linesearch(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,
+                                    const double* X, LocalState* ls, NewtonParams np, double* cpool,
+                                    const double* dpool, double* Kpool, double* Ktpool,
+                                    int* active_count);
+cudaError_t launch_local_prolong(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,
+                                 const double* cpool, double* F);
+template <typename T>
+cudaError_t launch_local_jvp(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
+                             const ProbDev* probs, const T* gpool, T* wpool, const double* coef,
+                             double* zpool, double* rpool, double* bpool, int nir, const double* D,
+                             double* O);
+template <typename T>
+cudaError_t launch_local_precond(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
+                                 const ProbDev* probs, const T* gpool, T* wpool, const double* R,
+                                 double* Z);
+}  // namespace ras

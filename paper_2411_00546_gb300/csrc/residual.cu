@@ -1,0 +1,242 @@
+// Grid-wide kernels: the residual F(x, eps) of Sec. 3.3 on the whole grid,
+// the Jacobian action F'(x, eps) v (Newton_RAS's Krylov operator), and the
+// vector kernels of GMRES (multi-dot, multi-axpy, scaling). All reductions use
+// a fixed grid (VEC_BLOCKS) and fixed trees, so results do not depend on
+// scheduling.
+#include "ras_internal.cuh"
+
+namespace ras {
+
+namespace {
+
+constexpr int NT = VEC_THREADS;
+constexpr int NB = VEC_BLOCKS;
+
+__device__ __forceinline__ double gval(const double* Z, int n, int i, int j) {
+    return (i < 0 || i >= n || j < 0 || j >= n) ? 0.0 : Z[(long long)j * n + i];
+}
+
+// F at x + alpha d (d may be null). Writes Fy/Fp when non-null; per-block
+// partial sums of ||F||^2 and of the rounding-floor estimate into
+// partials[blockIdx] and partials[NB + blockIdx].
+__global__ void __launch_bounds__(NT) k_residual_global(ProbDev P, const double* __restrict__ y,
+                                                        const double* __restrict__ p,
+                                                        const double* __restrict__ dy,
+                                                        const double* __restrict__ dp, double alpha,
+                                                        double eps, double* Fy, double* Fp,
+                                                        double* partials) {
+    __shared__ double red[2 * NT];
+    const int n = P.n;
+    const long long nn = (long long)n * n;
+    const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu;
+    auto vy = [=](int i, int j) -> double {
+        if (i < 0 || i >= n || j < 0 || j >= n) return 0.0;
+        const long long g = (long long)j * n + i;
+        return dy ? fma(alpha, dy[g], y[g]) : y[g];
+    };
+    auto vp = [=](int i, int j) -> double {
+        if (i < 0 || i >= n || j < 0 || j >= n) return 0.0;
+        const long long g = (long long)j * n + i;
+        return dp ? fma(alpha, dp[g], p[g]) : p[g];
+    };
+    double a = 0.0, b = 0.0;
+    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < nn; g += (long long)NB * NT) {
+        const int i = (int)(g % n), j = (int)(g / n);
+        const double yc = vy(i, j), yw = vy(i - 1, j), ye = vy(i + 1, j), ys = vy(i, j - 1), yn = vy(i, j + 1);
+        const double pc = vp(i, j), pw = vp(i - 1, j), pe = vp(i + 1, j), ps = vp(i, j - 1), pn = vp(i, j + 1);
+        double ph, d1, d2;
+        phi_eval(P.phi, P.kappa, yc, ph, d1, d2);
+        const double fv = P.f ? P.f[g] : 0.0;
+        const double pe_ = P_eps(-pc / mu, eps);
+        const double Fyv = beta * (4.0 * yc - yw - ye - ys - yn) + ph - fv + inu * (pc + mu * pe_);
+        const double Fpv = beta * (4.0 * pc - pw - pe - ps - pn) + d1 * pc - yc + P.yd[g];
+        const double My = beta * (4.0 * fabs(yc) + fabs(yw) + fabs(ye) + fabs(ys) + fabs(yn)) + fabs(ph) +
+                          fabs(fv) + inu * (fabs(pc) + mu * fabs(pe_));
+        const double Mp = beta * (4.0 * fabs(pc) + fabs(pw) + fabs(pe) + fabs(ps) + fabs(pn)) +
+                          fabs(d1 * pc) + fabs(yc) + fabs(P.yd[g]);
+        if (Fy) Fy[g] = Fyv;
+        if (Fp) Fp[g] = Fpv;
+        a += Fyv * Fyv + Fpv * Fpv;
+        b += My * My + Mp * Mp;
+    }
+    block_sum2<NT>(a, b, red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = a;
+        partials[NB + blockIdx.x] = b;
+    }
+}
+
+// out[v] = sum over the nparts partials of row v, in index order (one warp per row).
+__global__ void k_reduce_partials(const double* __restrict__ partials, int nparts, int nvals,
+                                  double* out) {
+    const int v = blockIdx.x;
+    if (v >= nvals) return;
+    __shared__ double red[NT];
+    double a = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += NT) a += partials[(long long)v * nparts + k];
+    a = block_sum1<NT>(a, red);
+    if (threadIdx.x == 0) out[v] = a;
+}
+
+// Jacobian coefficients at (x, eps): phi'(y), (1/nu)(1 - P_eps'(-p/mu)), phi''(y) p - 1.
+__global__ void __launch_bounds__(NT) k_coef_global(ProbDev P, const double* __restrict__ y,
+                                                    const double* __restrict__ p, double eps,
+                                                    double* coef) {
+    const long long nn = (long long)P.n * P.n;
+    const double inu = 1.0 / P.nu, mu = P.mu;
+    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < nn; g += (long long)NB * NT) {
+        double ph, d1, d2;
+        const double yv = y[g], pv = p[g];
+        phi_eval(P.phi, P.kappa, yv, ph, d1, d2);
+        coef[g] = d1;
+        coef[nn + g] = inu * (1.0 - dP_eps(-pv / mu, eps));
+        coef[2 * nn + g] = d2 * pv - 1.0;
+    }
+}
+
+// F'(x, eps) v with stored coefficients (Jacobian of Sec. 3.3).
+__global__ void __launch_bounds__(NT) k_jacvec_global(ProbDev P, const double* __restrict__ coef,
+                                                      const double* __restrict__ vy,
+                                                      const double* __restrict__ vp, double* oy,
+                                                      double* op) {
+    const int n = P.n;
+    const long long nn = (long long)n * n;
+    const double beta = P.beta;
+    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < nn; g += (long long)NB * NT) {
+        const int i = (int)(g % n), j = (int)(g / n);
+        const double yc = vy[g], pc = vp[g];
+        const double sy = gval(vy, n, i - 1, j) + gval(vy, n, i + 1, j) + gval(vy, n, i, j - 1) + gval(vy, n, i, j + 1);
+        const double sp = gval(vp, n, i - 1, j) + gval(vp, n, i + 1, j) + gval(vp, n, i, j - 1) + gval(vp, n, i, j + 1);
+        const double a = coef[g], b = coef[nn + g], c = coef[2 * nn + g];
+        oy[g] = beta * (4.0 * yc - sy) + a * yc + b * pc;
+        op[g] = beta * (4.0 * pc - sp) + c * yc + a * pc;
+    }
+}
+
+// partials[v * NB + block] = partial dot of V_v (row v of V, stride ld) with w.
+constexpr int MAXV = 32;
+__global__ void __launch_bounds__(NT) k_dot_multi(const double* __restrict__ V, long long ld, int nv,
+                                                  const double* __restrict__ w, long long len,
+                                                  double* partials) {
+    __shared__ double red[NT];
+    double acc[MAXV];
+#pragma unroll
+    for (int v = 0; v < MAXV; ++v) acc[v] = 0.0;
+    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < len; g += (long long)NB * NT) {
+        const double wv = w[g];
+#pragma unroll
+        for (int v = 0; v < MAXV; ++v)
+            if (v < nv) acc[v] += V[(long long)v * ld + g] * wv;
+    }
+    for (int v = 0; v < nv; ++v) {
+        const double s = block_sum1<NT>(acc[v < MAXV ? v : 0], red);
+        if (threadIdx.x == 0) partials[(long long)v * NB + blockIdx.x] = s;
+    }
+}
+
+// w += sign * sum_v h[v] V_v
+__global__ void __launch_bounds__(NT) k_axpy_multi(const double* __restrict__ V, long long ld, int nv,
+                                                   const double* __restrict__ h, double sign, double* w,
+                                                   long long len) {
+    __shared__ double hs[MAXV];
+    if (threadIdx.x < nv && threadIdx.x < MAXV) hs[threadIdx.x] = sign * h[threadIdx.x];
+    __syncthreads();
+    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < len; g += (long long)NB * NT) {
+        double acc = w[g];
+        for (int v = 0; v < nv; ++v) acc += hs[v] * V[(long long)v * ld + g];
+        w[g] = acc;
+    }
+}
+
+// dst = sign * src * num / den (num, den: device scalars; null means 1).
+__global__ void __launch_bounds__(NT) k_scale_copy(const double* src, const double* num,
+                                                   const double* den, double sign, double* dst,
+                                                   long long len) {
+    double s = sign;
+    if (num) s *= *num;
+    if (den) s /= *den;
+    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < len; g += (long long)NB * NT)
+        dst[g] = s * src[g];
+}
+
+__global__ void __launch_bounds__(NT) k_axpy(double a, const double* __restrict__ x, double* y,
+                                             long long len) {
+    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < len; g += (long long)NB * NT)
+        y[g] = fma(a, x[g], y[g]);
+}
+
+// out = fma(alpha, d, x): the same rounding as the trial point of the residual kernel.
+__global__ void __launch_bounds__(NT) k_add_scaled(const double* x, const double* d,
+                                                   double alpha, double* out, long long len) {
+    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < len; g += (long long)NB * NT)
+        out[g] = fma(alpha, d[g], x[g]);
+}
+
+}  // namespace
+
+cudaError_t launch_residual_global(cudaStream_t st, const ProbDev& P, const double* y, const double* p,
+                                   const double* dy, const double* dp, double alpha, double eps,
+                                   double* Fy, double* Fp, double* partials) {
+    count_launch();
+    k_residual_global<<<NB, NT, 0, st>>>(P, y, p, dy, dp, alpha, eps, Fy, Fp, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(cudaStream_t st, const double* partials, int nparts, int nvals,
+                                   double* out) {
+    count_launch();
+    k_reduce_partials<<<nvals, NT, 0, st>>>(partials, nparts, nvals, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coef_global(cudaStream_t st, const ProbDev& P, const double* y, const double* p,
+                               double eps, double* coef) {
+    count_launch();
+    k_coef_global<<<NB, NT, 0, st>>>(P, y, p, eps, coef);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jacvec_global(cudaStream_t st, const ProbDev& P, const double* coef,
+                                 const double* vy, const double* vp, double* oy, double* op) {
+    count_launch();
+    k_jacvec_global<<<NB, NT, 0, st>>>(P, coef, vy, vp, oy, op);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot_multi(cudaStream_t st, const double* V, long long ld, int nv, const double* w,
+                             long long len, double* partials) {
+    if (nv > MAXV || nv < 1) return cudaErrorInvalidValue;
+    count_launch();
+    k_dot_multi<<<NB, NT, 0, st>>>(V, ld, nv, w, len, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_multi(cudaStream_t st, const double* V, long long ld, int nv, const double* h,
+                              double sign, double* w, long long len) {
+    if (nv > MAXV || nv < 1) return cudaErrorInvalidValue;
+    count_launch();
+    k_axpy_multi<<<NB, NT, 0, st>>>(V, ld, nv, h, sign, w, len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_copy(cudaStream_t st, const double* src, const double* num, const double* den,
+                              double sign, double* dst, long long len) {
+    count_launch();
+    k_scale_copy<<<NB, NT, 0, st>>>(src, num, den, sign, dst, len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(cudaStream_t st, double a, const double* x, double* y, long long len) {
+    count_launch();
+    k_axpy<<<NB, NT, 0, st>>>(a, x, y, len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_scaled(cudaStream_t st, const double* x, const double* d, double alpha,
+                              double* out, long long len) {
+    count_launch();
+    k_add_scaled<<<NB, NT, 0, st>>>(x, d, alpha, out, len);
+    return cudaGetLastError();
+}
+
+}  // namespace ras

@@ -1,0 +1,289 @@
+"""Thin ctypes binding of libras.so (include/ras.h), with the C ABI's names.
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+Grid functions are torch CUDA float64 tensors of n*n elements (any shape,
+contiguous, row-major with the x1 index fastest). Host buffers for
+ras_solve_host are CPU float64 tensors (pinned for speed). There is no CPU
+fallback: if libras.so is missing, loading fails with an error.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libras.so")
+
+RAS_OK = 0
+RAS_OK_FLOOR = 1
+RAS_EINVAL = -1
+RAS_ENOMEM = -2
+RAS_ENOCONV = -3
+RAS_ESINGULAR = -5
+RAS_ENONFINITE = -6
+RAS_ENOTIMPL = -8
+RAS_ECUDA = -9
+RAS_ESTATE = -10
+
+RAS_PHI_CUBIC = 0
+RAS_PHI_EXP = 1
+RAS_PHI_KAPPA = 2
+
+RAS_FP64 = 0
+RAS_MIXED = 1
+
+RAS_METHOD_RASPEN = 0
+RAS_METHOD_NEWTON_RAS = 1
+
+
+class ras_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("eps0", ctypes.c_double), ("gamma", ctypes.c_double), ("eps_min", ctypes.c_double),
+                ("kmax_outer_raspen", ctypes.c_int), ("kmax_outer_newton", ctypes.c_int),
+                ("kmax_inner", ctypes.c_int), ("max_halvings", ctypes.c_int),
+                ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
+                ("gmres_rtol", ctypes.c_double), ("floor_factor", ctypes.c_double),
+                ("precision", ctypes.c_int), ("ir_max", ctypes.c_int), ("ir_rtol", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("jvp_ir", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class ras_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_its", ctypes.c_int), ("gmres_its", ctypes.c_int),
+                ("evaluations", ctypes.c_int), ("inner_its_max", ctypes.c_int),
+                ("inner_its_sum", ctypes.c_longlong), ("halvings", ctypes.c_int),
+                ("exhausted", ctypes.c_int), ("local_failures", ctypes.c_int), ("res0", ctypes.c_double),
+                ("res", ctypes.c_double), ("eps_final", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class RasError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("ras error %d: %s" % (code, msg))
+        self.code = code
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_SIGS = {
+    "ras_default_opts": (_I, [ctypes.POINTER(ras_opts)]),
+    "ras_create": (_I, [_I, _I, _I, _I, _I, _D, _D, _P, _P, ctypes.POINTER(ras_opts), _P, ctypes.POINTER(_P)]),
+    "ras_set_eps": (_I, [_P, _D]),
+    "ras_set_opts": (_I, [_P, ctypes.POINTER(ras_opts)]),
+    "ras_set_data": (_I, [_P, _P, _P]),
+    "ras_residual": (_I, [_P, _P, _P, _D, _P, _P, ctypes.POINTER(_D)]),
+    "ras_apply": (_I, [_P, _P, _P, _I, _P, _P, ctypes.POINTER(ras_stats)]),
+    "ras_jvp": (_I, [_P, _P, _P, _P, _P]),
+    "ras_precondition": (_I, [_P, _P, _P, _D, _P, _P, _P, _P]),
+    "ras_raspen_solve": (_I, [_P, _P, _P, ctypes.POINTER(ras_stats)]),
+    "ras_newton_ras_solve": (_I, [_P, _P, _P, ctypes.POINTER(ras_stats)]),
+    "ras_solve_host": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(ras_stats)]),
+    "ras_local_iterations": (_I, [_P, ctypes.POINTER(_I), _I]),
+    "ras_subdomain_count": (_I, [_P]),
+    "ras_device_bytes": (ctypes.c_size_t, [_P]),
+    "ras_last_error": (ctypes.c_char_p, [_P]),
+    "ras_destroy": (None, [_P]),
+    "ras_launch_count": (ctypes.c_longlong, []),
+    "ras_profile": (_I, [_P, _I]),
+    "ras_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)]),
+}
+
+RAS_K_NAMES = ["init", "factor", "direction", "linesearch", "jvp", "precond", "residual", "krylov", "other"]
+
+_lib = None
+
+
+def lib():
+    """Load libras.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libras.so not found at %s; build it with __graft_entry__.build() "
+                               "or python -m paper_2411_00546_gb300.build" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(t, n=None, device=True):
+    if t is None:
+        return None
+    if device and not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not device and t.is_cuda:
+        raise ValueError("expected a CPU tensor")
+    import torch
+    if t.dtype != torch.float64:
+        raise ValueError("expected float64")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError("expected %d elements, got %d" % (n, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Handle:
+    """Opaque ras_problem* plus the grid size, for argument checks."""
+
+    def __init__(self, ptr, n):
+        self.ptr = ptr
+        self.n = n
+
+    def _check(self, rc, ok=(RAS_OK, RAS_OK_FLOOR)):
+        if rc not in ok:
+            raise RasError(rc, ras_last_error(self))
+        return rc
+
+
+def ras_default_opts():
+    o = ras_opts()
+    lib().ras_default_opts(ctypes.byref(o))
+    return o
+
+
+def ras_create(n, sx, sy, overlap, phi, nu, mu, y_d, f=None, opts=None, stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    out = ctypes.c_void_p()
+    rc = lib().ras_create(n, sx, sy, overlap, phi, nu, mu, _ptr(y_d, n * n), _ptr(f, n * n),
+                          ctypes.byref(opts) if opts is not None else None, ctypes.c_void_p(stream),
+                          ctypes.byref(out))
+    if rc != RAS_OK:
+        raise RasError(rc, "ras_create failed")
+    return Handle(out, n)
+
+
+def ras_set_eps(h, eps_min):
+    return h._check(lib().ras_set_eps(h.ptr, eps_min))
+
+
+def ras_set_opts(h, opts):
+    return h._check(lib().ras_set_opts(h.ptr, ctypes.byref(opts)))
+
+
+def ras_set_data(h, y_d, f=None):
+    nn = h.n * h.n
+    return h._check(lib().ras_set_data(h.ptr, _ptr(y_d, nn), _ptr(f, nn)))
+
+
+def ras_residual(h, y, p, eps, Fy=None, Fp=None):
+    nn = h.n * h.n
+    nrm = ctypes.c_double()
+    h._check(lib().ras_residual(h.ptr, _ptr(y, nn), _ptr(p, nn), eps, _ptr(Fy, nn), _ptr(Fp, nn),
+                                ctypes.byref(nrm)))
+    return nrm.value
+
+
+def ras_apply(h, y, p, continuation, Fy, Fp, check=True):
+    nn = h.n * h.n
+    st = ras_stats()
+    rc = lib().ras_apply(h.ptr, _ptr(y, nn), _ptr(p, nn), int(continuation), _ptr(Fy, nn), _ptr(Fp, nn),
+                         ctypes.byref(st))
+    if check:
+        h._check(rc)
+    return rc, st
+
+
+def ras_jvp(h, dy, dp, oy, op):
+    nn = h.n * h.n
+    return h._check(lib().ras_jvp(h.ptr, _ptr(dy, nn), _ptr(dp, nn), _ptr(oy, nn), _ptr(op, nn)))
+
+
+def ras_precondition(h, y, p, eps, ry, rp, zy, zp):
+    nn = h.n * h.n
+    return h._check(lib().ras_precondition(h.ptr, _ptr(y, nn), _ptr(p, nn), eps, _ptr(ry, nn), _ptr(rp, nn),
+                                           _ptr(zy, nn), _ptr(zp, nn)))
+
+
+def ras_raspen_solve(h, y, p, check=True):
+    nn = h.n * h.n
+    st = ras_stats()
+    rc = lib().ras_raspen_solve(h.ptr, _ptr(y, nn), _ptr(p, nn), ctypes.byref(st))
+    if check:
+        h._check(rc)
+    return rc, st
+
+
+def ras_newton_ras_solve(h, y, p, check=True):
+    nn = h.n * h.n
+    st = ras_stats()
+    rc = lib().ras_newton_ras_solve(h.ptr, _ptr(y, nn), _ptr(p, nn), ctypes.byref(st))
+    if check:
+        h._check(rc)
+    return rc, st
+
+
+def ras_solve_host(h, method, y_d_host, y_host, p_host, check=True):
+    nn = h.n * h.n
+    st = ras_stats()
+    rc = lib().ras_solve_host(h.ptr, int(method), _ptr(y_d_host, nn, device=False),
+                              _ptr(y_host, nn, device=False), _ptr(p_host, nn, device=False),
+                              ctypes.byref(st))
+    if check:
+        h._check(rc)
+    return rc, st
+
+
+def ras_local_iterations(h):
+    k = ras_subdomain_count(h)
+    buf = (ctypes.c_int * k)()
+    got = lib().ras_local_iterations(h.ptr, buf, k)
+    return list(buf)[:got]
+
+
+def ras_subdomain_count(h):
+    return lib().ras_subdomain_count(h.ptr)
+
+
+def ras_device_bytes(h):
+    return lib().ras_device_bytes(h.ptr)
+
+
+def ras_last_error(h):
+    r = lib().ras_last_error(h.ptr)
+    return r.decode() if r else ""
+
+
+def ras_destroy(h):
+    if h.ptr:
+        lib().ras_destroy(h.ptr)
+        h.ptr = None
+
+
+def ras_launch_count():
+    return lib().ras_launch_count()
+
+
+def ras_profile(h, enable):
+    return h._check(lib().ras_profile(h.ptr, int(enable)))
+
+
+def ras_profile_read(h, kind):
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    w = ctypes.c_double()
+    h._check(lib().ras_profile_read(h.ptr, int(kind), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
+    return ms.value, n.value, w.value
+
+
+def ras_profile_all(h):
+    return {name: ras_profile_read(h, k) for k, name in enumerate(RAS_K_NAMES)}
+
+
+def make_opts(**kw):
+    """ras_default_opts() with fields overridden by keyword."""
+    o = ras_default_opts()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
