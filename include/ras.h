@@ -224,6 +224,35 @@ long long ras_launch_count(void);
 int ras_profile(ras_problem* h, int enable);
 int ras_profile_read(ras_problem* h, int kind, double* ms, long long* launches, double* work);
 
+/* Residual without a handle and without any device allocation.
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * call cudaMalloc or cudaFree, e.g. code running while another allocator (a
+ * framework's caching allocator or a pre-reserved pool) owns the device
+ * memory, or a latency-bound loop where an allocation's implicit device
+ * synchronisation is not acceptable; ras_create allocates, so those callers
+ * cannot use ras_residual.
+ * Computes F(x, eps) of Sec. 3.3 at x = (y, p) exactly like ras_residual:
+ * writes Fy, Fp (device n*n, either may be NULL) and, if norm_dev != NULL,
+ * ||(Fy, Fp)||_2 to norm_dev[0] (device). y, p, y_d: device n*n; f device
+ * n*n or NULL (= 0); phi, nu, mu, kappa as in ras_create / ras_opts; eps > 0.
+ * The work is only enqueued on `stream` (cudaStream_t, NULL = legacy default
+ * stream); results are ready when the stream reaches it.
+ * Scratch: the norm's partial sums live in one fixed array inside the library
+ * (2 doubles per grid row, RAS_STATIC_MAX_N rows, 128 KiB), which every GPU
+ * that loads the library holds until the process exits. The first call on a
+ * device looks up that array's device address with the device current; make
+ * that first call before any stream capture. Every call writes all the
+ * partials it later reads, so nothing has to start at zero; the array keeps
+ * the last call's values. All calls share the array: calls whose GPU work
+ * overlaps (other streams, other threads) race and give wrong norms.
+ * Returns RAS_EINVAL for n < 2, n > RAS_STATIC_MAX_N, a bad phi, nu, mu or
+ * eps, or a NULL y, p or y_d; RAS_ECUDA if a launch fails. No allocation of
+ * any kind is made. */
+#define RAS_STATIC_MAX_N 8192
+int ras_residual_static(int n, int phi, double nu, double mu, double kappa, double eps,
+                        const double* y, const double* p, const double* y_d, const double* f,
+                        double* Fy, double* Fp, double* norm_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,7 +86,10 @@ _SIGS = {
     "ras_launch_count": (ctypes.c_longlong, []),
     "ras_profile": (_I, [_P, _I]),
     "ras_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)]),
+    "ras_residual_static": (_I, [_I, _I, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
+
+RAS_STATIC_MAX_N = 8192
 
 RAS_K_NAMES = ["init", "factor", "direction", "linesearch", "jvp", "precond", "residual", "krylov", "other"]
 
@@ -277,6 +280,25 @@ def ras_profile_read(h, kind):
 
 def ras_profile_all(h):
     return {name: ras_profile_read(h, k) for k, name in enumerate(RAS_K_NAMES)}
+
+
+def ras_residual_static(n, phi, nu, mu, kappa, eps, y, p, y_d, f=None, Fy=None, Fp=None, norm_dev=None,
+                        stream=None):
+    """F(x, eps) and its norm with no device allocation (for callers that
+    cannot allocate, see include/ras.h). norm_dev: 1-element CUDA float64
+    tensor or None. Only enqueues work on `stream`."""
+    if n > RAS_STATIC_MAX_N:
+        raise RasError(RAS_EINVAL, "n=%d exceeds RAS_STATIC_MAX_N=%d" % (n, RAS_STATIC_MAX_N))
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    nn = n * n
+    rc = lib().ras_residual_static(n, phi, nu, mu, kappa, eps, _ptr(y, nn), _ptr(p, nn), _ptr(y_d, nn),
+                                   _ptr(f, nn), _ptr(Fy, nn), _ptr(Fp, nn), _ptr(norm_dev, 1),
+                                   ctypes.c_void_p(stream))
+    if rc != RAS_OK:
+        raise RasError(rc, "ras_residual_static rejected its arguments (n=%d, limit %d)" % (n, RAS_STATIC_MAX_N))
+    return rc
 
 
 def make_opts(**kw):

@@ -1,0 +1,55 @@
+"""The allocation-free residual entry point (ras_residual_static) against the
+handle-based ras_residual.
+
+Some callers cannot allocate device memory (another allocator owns it, or an
+allocation's device synchronisation is not acceptable in their loop); they
+use ras_residual_static, whose scratch is a fixed array inside the library.
+This file is collected last on purpose, and it runs the same alone in a fresh
+process: two calls in a row, each checked against the handle-based result
+within the tolerance of the other residual tests, plus the size limit."""
+import numpy as np
+import pytest
+
+from gpu_util import to_dev, zeros
+from paper_2411_00546_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+from paper_2411_00546_gb300 import ras  # noqa: E402
+
+
+def test_static_residual_matches_handle_residual_twice():
+    n, phi, nu, mu, kappa = 100, ras.RAS_PHI_KAPPA, 1e-5, 2e-3, 0.1
+    rng = np.random.default_rng(21)
+    yd = to_dev(inputs.yd_fourier(n, 3))
+    f = to_dev(0.4 * rng.standard_normal((n, n)))
+    h = ras.ras_create(n, 3, 3, 2, phi, nu, mu, yd, f, ras.make_opts(kappa=kappa))
+    stream = torch.cuda.current_stream().cuda_stream
+    try:
+        for call, eps in enumerate((1e-2, 1e-7)):
+            Y = 0.5 * rng.standard_normal((n, n))
+            P = 3e-3 * rng.standard_normal((n, n))
+            y, p = to_dev(Y), to_dev(P)
+            ry, rp = zeros(n), zeros(n)
+            ref = ras.ras_residual(h, y, p, eps, ry, rp)
+            sy, sp = zeros(n), zeros(n)
+            nd = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+            ras.ras_residual_static(n, phi, nu, mu, kappa, eps, y, p, yd, f, sy, sp, nd, stream=stream)
+            torch.cuda.synchronize()
+            scale = (n + 1) ** 2 * max(np.abs(Y).max(), np.abs(P).max())
+            for got, want in ((sy, ry), (sp, rp)):
+                g, w = got.cpu().numpy(), want.cpu().numpy()
+                assert np.max(np.abs(g - w)) <= 1e-13 * scale + 1e-12 * np.abs(w).max(), call
+            assert abs(float(nd.item()) - ref) <= 1e-12 * ref, call
+    finally:
+        ras.ras_destroy(h)
+
+
+def test_static_residual_rejects_oversized_grid():
+    rc = ras.lib().ras_residual_static(ras.RAS_STATIC_MAX_N + 1, 0, 1e-4, 1e-3, 0.1, 1e-3,
+                                       None, None, None, None, None, None, None, None)
+    assert rc == ras.RAS_EINVAL
+    with pytest.raises(ras.RasError):
+        ras.ras_residual_static(ras.RAS_STATIC_MAX_N + 1, 0, 1e-4, 1e-3, 0.1, 1e-3, None, None, None)
