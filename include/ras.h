@@ -46,6 +46,8 @@ extern "C" {
 #define RAS_ENOCONV     -3   /* iteration limit reached (Alg. 1 / Alg. 2 kmax) */
 #define RAS_ESINGULAR   -5   /* zero pivot in a local factorisation            */
 #define RAS_ENONFINITE  -6   /* NaN or Inf in a residual                       */
+#define RAS_ETIMEOUT    -7   /* a bounded device-side wait ran out; the kernel
+                                gave up cleanly and the context stays usable   */
 #define RAS_ENOTIMPL    -8   /* not available in this build                    */
 #define RAS_ECUDA       -9   /* CUDA runtime error                             */
 #define RAS_ESTATE     -10   /* call needs state that is not there (e.g. a JVP

@@ -46,6 +46,7 @@ struct ras_problem {
     int gprec = -1;
     LocalState* ls = nullptr;
     int* d_active = nullptr;
+    int* d_err = nullptr;        // set by kernels whose bounded waits ran out
     int* h_active = nullptr;     // pinned
     double *X = nullptr, *F = nullptr, *Dv = nullptr, *Ov = nullptr, *T1 = nullptr, *T2 = nullptr,
            *T3 = nullptr, *Z = nullptr;
@@ -218,6 +219,19 @@ int sync(ras_problem* h) {
     return RAS_OK;
 }
 
+// RAS_ETIMEOUT if a kernel reported that a bounded wait ran out (then clears it).
+int check_err(ras_problem* h) {
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (v != 0) {
+        CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st));
+        CK(cudaStreamSynchronize(h->st));
+        return fail(h, RAS_ETIMEOUT, "a device-side wait exceeded its limit");
+    }
+    return RAS_OK;
+}
+
 size_t prec_bytes(const ras_problem* h) { return h->o.precision == RAS_MIXED ? sizeof(float) : sizeof(double); }
 
 // Algorithmic work of a factorisation of the subdomains with mask[i] != 0:
@@ -316,7 +330,7 @@ int ras_apply_T(ras_problem* h, int continuation, double* Fout, ras_stats* stats
         }));
         CK(timed(h, RAS_K_DIRECTION, 0.0, [&] {
             return ras::launch_local_direction<T>(h->st, h->nsub, h->maxm, h->d_subs, h->d_prob, h->ls, np,
-                                                  h->coef, gp, h->Kpool, h->dpool, h->rpool, wp);
+                                                  h->coef, gp, h->Kpool, h->dpool, h->rpool, wp, h->d_err);
         }));
         const size_t dir_rec = h->prof_recs.size();
         CK(cudaMemsetAsync(h->d_active, 0, sizeof(int), h->st));
@@ -388,10 +402,10 @@ int jvp_internal(ras_problem* h, const double* D, double* O) {
         if (h->o.precision == RAS_MIXED)
             return ras::launch_local_jvp<float>(h->st, h->nsub, h->maxm, h->d_subs, h->d_prob,
                                                 (const float*)h->gpool, (float*)h->wpool, h->coef, h->dpool,
-                                                h->rpool, h->Ktpool, nir, D, O);
+                                                h->rpool, h->Ktpool, nir, D, O, h->d_err);
         return ras::launch_local_jvp<double>(h->st, h->nsub, h->maxm, h->d_subs, h->d_prob,
                                              (const double*)h->gpool, (double*)h->wpool, h->coef, h->dpool,
-                                             h->rpool, h->Ktpool, 0, D, O);
+                                             h->rpool, h->Ktpool, 0, D, O, h->d_err);
     }));
     return RAS_OK;
 }
@@ -426,9 +440,9 @@ int precond_internal(ras_problem* h, const double* R, double* Zo) {
     CK(timed(h, RAS_K_PRECOND, solve_bytes_all(h), [&] {
         if (h->o.precision == RAS_MIXED)
             return ras::launch_local_precond<float>(h->st, h->nsub, h->maxm, h->d_subs, h->d_prob,
-                                                    (const float*)h->gpool, (float*)h->wpool, R, Zo);
+                                                    (const float*)h->gpool, (float*)h->wpool, R, Zo, h->d_err);
         return ras::launch_local_precond<double>(h->st, h->nsub, h->maxm, h->d_subs, h->d_prob,
-                                                 (const double*)h->gpool, (double*)h->wpool, R, Zo);
+                                                 (const double*)h->gpool, (double*)h->wpool, R, Zo, h->d_err);
     }));
     return RAS_OK;
 }
@@ -693,10 +707,11 @@ int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu
             s.y0 = std::max(0, s.oy0 - overlap);
             s.wx = std::min(n, bx[i].second + overlap) - s.x0;
             s.wy = std::min(n, by[j].second + overlap) - s.y0;
+            s.mp = ((2 * s.wx + 31) / 32) * 32;
             s.voff = voff; s.noff = noff; s.goff = goff;
             voff += 2LL * s.wx * s.wy;
             noff += (long long)s.wx * s.wy;
-            goff += (long long)s.wy * (2LL * s.wx) * (2LL * s.wx);
+            goff += (long long)s.wy * s.mp * s.mp;
             h->maxm = std::max(h->maxm, 2 * s.wx);
             h->subs.push_back(s);
         }
@@ -721,6 +736,7 @@ int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu
     A(dalloc(h, &h->coef, 3 * h->Nsum));
     A(dalloc(h, &h->ls, h->nsub));
     A(dalloc(h, &h->d_active, 1));
+    A(dalloc(h, &h->d_err, 1));
     for (double** p : {&h->X, &h->F, &h->Dv, &h->Ov, &h->T1, &h->T2, &h->T3, &h->Z}) A(dalloc(h, p, 2 * N));
     A(dalloc(h, &h->coefG, 3 * N));
     A(dalloc(h, &h->partials, (size_t)ras::VEC_BLOCKS * 32));
@@ -748,7 +764,8 @@ int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu
     h->prob.yd = h->yd;
     h->prob.f = h->f;
     h->prob.ofs = 0;
-    cudaError_t e = cudaMemcpyAsync(h->yd, y_d, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
+    cudaError_t e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->yd, y_d, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
     if (e == cudaSuccess && f) e = cudaMemcpyAsync(h->f, f, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->d_subs, h->subs.data(), h->nsub * sizeof(SubDev), cudaMemcpyHostToDevice, h->st);
@@ -819,6 +836,7 @@ int ras_apply(ras_problem* h, const double* y, const double* p, int continuation
     TRY(copy_in(h, h->X, y, p));
     const int rc = ras_apply_internal(h, continuation, h->F, stats);
     if (rc == RAS_ECUDA) return rc;
+    TRY(check_err(h));
     TRY(copy_out(h, h->F, Fy, Fp));
     TRY(sync(h));
     if (stats) stats->status = rc;
@@ -831,7 +849,8 @@ int ras_jvp(ras_problem* h, const double* dy, const double* dp, double* oy, doub
     TRY(copy_in(h, h->Dv, dy, dp));
     TRY(jvp_internal(h, h->Dv, h->Ov));
     TRY(copy_out(h, h->Ov, oy, op));
-    return sync(h);
+    TRY(sync(h));
+    return check_err(h);
 }
 
 int ras_precondition(ras_problem* h, const double* y, const double* p, double eps, const double* ry,
@@ -842,7 +861,8 @@ int ras_precondition(ras_problem* h, const double* y, const double* p, double ep
     TRY(copy_in(h, h->T1, ry, rp));
     TRY(precond_internal(h, h->T1, h->Z));
     TRY(copy_out(h, h->Z, zy, zp));
-    return sync(h);
+    TRY(sync(h));
+    return check_err(h);
 }
 
 int ras_raspen_solve(ras_problem* h, double* y, double* p, ras_stats* stats) {
@@ -851,6 +871,7 @@ int ras_raspen_solve(ras_problem* h, double* y, double* p, ras_stats* stats) {
     TRY(copy_in(h, h->X, y, p));
     const int rc = raspen_internal(h, stats);
     if (rc == RAS_ECUDA) return rc;
+    TRY(check_err(h));
     TRY(copy_out(h, h->X, y, p));
     TRY(sync(h));
     return rc;
@@ -862,6 +883,7 @@ int ras_newton_ras_solve(ras_problem* h, double* y, double* p, ras_stats* stats)
     TRY(copy_in(h, h->X, y, p));
     const int rc = newton_ras_internal(h, stats);
     if (rc == RAS_ECUDA) return rc;
+    TRY(check_err(h));
     TRY(copy_out(h, h->X, y, p));
     TRY(sync(h));
     return rc;
@@ -879,6 +901,7 @@ int ras_solve_host(ras_problem* h, int method, const double* y_d_host, double* y
     h->jvp_ready = false;
     const int rc = (method == RAS_METHOD_RASPEN) ? raspen_internal(h, stats) : newton_ras_internal(h, stats);
     if (rc == RAS_ECUDA) return rc;
+    TRY(check_err(h));
     CK(cudaMemcpyAsync(y_host, h->X, nb, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(p_host, h->X + h->N, nb, cudaMemcpyDeviceToHost, h->st));
     TRY(sync(h));

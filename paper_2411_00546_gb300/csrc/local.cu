@@ -9,10 +9,9 @@
 // off-diagonal blocks -beta I (the 5-point coupling between neighbouring rows,
 // beta = 1/h^2, the same for both fields). Its block LU therefore only needs
 //   S_0 = D_0,  S_j = D_j - beta^2 S_{j-1}^-1,
-// and the factor stores G_j = S_j^-1, computed by Gauss-Jordan elimination
-// with partial pivoting inside each block. A solve J z = b is
-//   w_0 = b_0, w_j = b_j + beta G_{j-1} w_{j-1};
-//   z_{W-1} = G_{W-1} w_{W-1}, z_j = G_j (w_j + beta z_{j+1}).
+// and the factor stores G_j = S_j^-1 (in the packed order of packed_index),
+// computed by Gauss-Jordan elimination with partial pivoting inside each
+// block. The solves with these factors are in solve.cu.
 #include "ras_internal.cuh"
 
 namespace ras {
@@ -209,13 +208,14 @@ __global__ void __launch_bounds__(FACT_THREADS) k_local_factor(int nsub, int max
     T* G = gpool + s.goff;
     for (int j = 0; j < W; ++j) {
         // S_j = D_j - beta^2 G_{j-1}
-        const T* Gp = G + (long long)(j > 0 ? j - 1 : 0) * m * m;
+        const long long blk = (long long)s.mp * s.mp;
+        const T* Gp = G + (long long)(j > 0 ? j - 1 : 0) * blk;
         for (int r = warp; r < m; r += FW) {
             const int ix = r >> 1, f = r & 1;
             const int q = j * s.wx + ix;
             for (int cidx = lane; cidx < m; cidx += 32) {
                 const int cx = cidx >> 1, cf = cidx & 1;
-                T v = (j > 0) ? -tbeta2 * Gp[r * m + cidx] : (T)0;
+                T v = (j > 0) ? -tbeta2 * Gp[packed_index<T>(r, cidx, s.mp)] : (T)0;
                 if (cx == ix) {
                     if (cf == f) v += tdiag + (T)ca[q];
                     else if (f == 0) v += (T)cb[q];
@@ -282,10 +282,11 @@ __global__ void __launch_bounds__(FACT_THREADS) k_local_factor(int nsub, int max
         if (sh_fail) break;
         for (int t = tid; t < m; t += FACT_THREADS) rinv[perm[t]] = t;
         __syncthreads();
-        T* Gj = G + (long long)j * m * m;
-        for (int r = warp; r < m; r += FW) {
-            const int pr = perm[r];
-            for (int cidx = lane; cidx < m; cidx += 32) Gj[r * m + cidx] = M[pr * LD + rinv[cidx]];
+        T* Gj = G + (long long)j * blk;
+        for (int r = warp; r < s.mp; r += FW) {
+            const int pr = r < m ? perm[r] : 0;
+            for (int cidx = lane; cidx < s.mp; cidx += 32)
+                Gj[packed_index<T>(r, cidx, s.mp)] = (r < m && cidx < m) ? M[pr * LD + rinv[cidx]] : (T)0;
         }
         __syncthreads();
     }
@@ -293,136 +294,6 @@ __global__ void __launch_bounds__(FACT_THREADS) k_local_factor(int nsub, int max
         ls[i].status = ST_ESINGULAR;
         ls[i].active = 0;
     }
-}
-
-// ------------------------------------------------------------------ solve
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    return v;
-}
-
-// out[k] = sum_c G[k*m + c] vec[c], one warp per row, lanes across columns.
-template <typename T>
-__device__ __forceinline__ void block_matvec(const T* __restrict__ G, int m, const T* vec, T* out) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int k = warp; k < m; k += NW) {
-        const T* row = G + (long long)k * m;
-        T acc = (T)0;
-#pragma unroll 5
-        for (int cidx = lane; cidx < m; cidx += 32) acc += __ldg(row + cidx) * vec[cidx];
-        acc = warp_sum(acc);
-        if (lane == 0) out[k] = acc;
-    }
-}
-
-// z = J_i^-1 b with the stored G_j. rhs(j, t) gives b (row j, unknown t);
-// out(j, t, z) consumes z. w: global scratch of m*W T. vec, tmp: shared, m T.
-template <typename T, class Rhs, class Out>
-__device__ void block_solve(const T* __restrict__ G, int m, int W, T beta, T* w, T* vec, T* tmp,
-                            Rhs rhs, Out out) {
-    const int tid = threadIdx.x;
-    for (int j = 0; j < W; ++j) {
-        for (int t = tid; t < m; t += NT) {
-            T v = rhs(j, t);
-            if (j > 0) v += beta * tmp[t];
-            vec[t] = v;
-            w[j * m + t] = v;
-        }
-        __syncthreads();
-        if (j < W - 1) {
-            block_matvec(G + (long long)j * m * m, m, vec, tmp);
-            __syncthreads();
-        }
-    }
-    for (int j = W - 1; j >= 0; --j) {
-        for (int t = tid; t < m; t += NT) {
-            T v = w[j * m + t];
-            if (j < W - 1) v += beta * tmp[t];
-            vec[t] = v;
-        }
-        __syncthreads();
-        block_matvec(G + (long long)j * m * m, m, vec, tmp);
-        __syncthreads();
-        for (int t = tid; t < m; t += NT) out(j, t, tmp[t]);
-    }
-    __syncthreads();
-}
-
-// r = bsign * B - J_i z in FP64 with the Jacobian coefficients stored by the
-// factor kernel (5-point coupling inside Omega_i only); returns ||r||^2.
-__device__ double local_linear_residual(const SubDev& s, double beta, const double* coef, double bsign,
-                                        const double* B, const double* z, double* r, double* red) {
-    const int wx = s.wx, wy = s.wy, nn = wx * wy;
-    const double* ca = coef + 3 * s.noff;
-    const double* cb = ca + nn;
-    const double* cc = cb + nn;
-    double r2 = 0.0, dummy = 0.0;
-    for (int q = threadIdx.x; q < nn; q += NT) {
-        const int lx = q % wx, ly = q / wx;
-        const double zyc = z[2 * q], zpc = z[2 * q + 1];
-        double sy = 0.0, sp = 0.0;
-        if (lx > 0) { sy += z[2 * (q - 1)]; sp += z[2 * (q - 1) + 1]; }
-        if (lx < wx - 1) { sy += z[2 * (q + 1)]; sp += z[2 * (q + 1) + 1]; }
-        if (ly > 0) { sy += z[2 * (q - wx)]; sp += z[2 * (q - wx) + 1]; }
-        if (ly < wy - 1) { sy += z[2 * (q + wx)]; sp += z[2 * (q + wx) + 1]; }
-        const double Jy = beta * (4.0 * zyc - sy) + ca[q] * zyc + cb[q] * zpc;
-        const double Jp = beta * (4.0 * zpc - sp) + cc[q] * zyc + ca[q] * zpc;
-        const double ry = bsign * B[2 * q] - Jy, rp = bsign * B[2 * q + 1] - Jp;
-        r[2 * q] = ry;
-        r[2 * q + 1] = rp;
-        r2 += ry * ry + rp * rp;
-    }
-    block_sum2<NT>(r2, dummy, red);
-    return r2;
-}
-
-// Newton direction d = -J_i^-1 K_i. In mixed precision the FP32 solve is
-// followed by FP64 iterative refinement: r = -K - J d with the FP64 Jacobian
-// (matrix-free, from the coefficients the factor kernel stored), d += J^-1 r,
-// until ||r|| <= ir_rtol ||K|| or ir_max corrections.
-template <typename T>
-__global__ void __launch_bounds__(NT) k_local_direction(int nsub, const SubDev* __restrict__ subs,
-                                                        const ProbDev* __restrict__ probs,
-                                                        LocalState* ls, NewtonParams np,
-                                                        const double* coef, const T* gpool,
-                                                        const double* Kpool, double* dpool,
-                                                        double* rpool, T* wpool) {
-    __shared__ T vec[MAX_M], tmp[MAX_M];
-    __shared__ double red[2 * NT];
-    const int i = blockIdx.x;
-    if (i >= nsub) return;
-    if (!ls[i].active) return;
-    const SubDev s = subs[i];
-    const ProbDev P = probs[s.prob];
-    const int m = 2 * s.wx, W = s.wy, L = m * W, wx = s.wx, wy = s.wy, nn = wx * wy;
-    const double beta = P.beta;
-    const double* K = Kpool + s.voff;
-    double* d = dpool + s.voff;
-    double* r = rpool + s.voff;
-    T* w = wpool + s.voff;
-    const T* G = gpool + s.goff;
-    double b2 = 0.0, dummy = 0.0;
-    for (int q = threadIdx.x; q < L; q += NT) {
-        const double v = -K[q];
-        r[q] = v;
-        d[q] = 0.0;
-        b2 += v * v;
-    }
-    block_sum2<NT>(b2, dummy, red);
-    const double bnorm = sqrt(b2);
-    int nsolves = 0;
-    for (int it = 0;; ++it) {
-        ++nsolves;
-        block_solve<T>(
-            G, m, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)r[j * m + t]; },
-            [=](int j, int t, T z) { d[j * m + t] += (double)z; });
-        if (it >= np.ir_max) break;
-        const double r2 = local_linear_residual(s, beta, coef, -1.0, K, d, r, red);
-        if (sqrt(r2) <= np.ir_rtol * bnorm) break;
-    }
-    if (threadIdx.x == 0) ls[i].solves += nsolves;
 }
 
 // Backtracking (relaxed test with sigma), step, eps update and stop test of
@@ -504,99 +375,236 @@ __global__ void __launch_bounds__(NT) k_local_prolong(int nsub, const SubDev* __
     }
 }
 
-// Jacobian action of the RASPEN function (Alg. 4):
-//   O = -D - sum_i tilde P_i J_i(x^(i))^-1 B_i D,  B_i D = R_i A (I - P_i R_i) D,
-// i.e. b = -beta * (sum of D over the 5-point neighbours outside Omega_i).
-// With nir > 0 (mixed precision) the local solve is refined nir times in FP64:
-// z += J^-1 (b - J z), J from the coefficients at x^(i).
-template <typename T>
-__global__ void __launch_bounds__(NT) k_local_jvp(int nsub, const SubDev* __restrict__ subs,
-                                                  const ProbDev* __restrict__ probs, const T* gpool,
-                                                  T* wpool, const double* coef, double* zpool,
-                                                  double* rpool, double* bpool, int nir, const double* D,
-                                                  double* O) {
-    __shared__ T vec[MAX_M], tmp[MAX_M];
-    __shared__ double red[2 * NT];
+// FP32 factorisation with the block held in registers. Thread (ty, tx) of a
+// 16 x 16 CTA owns rows ty + 16a and columns tx + 16b (a, b < R) of the
+// 16R x 16R block, so every elimination step updates registers only; the
+// pivot column and the scaled pivot row are broadcast through shared memory
+// (double-buffered, three barriers per step). Partial pivoting as in the
+// generic kernel (max |.| among the not yet eliminated rows, ties to the
+// lowest row); an off-diagonal pivot row is swapped in physically and the
+// column order of the inverse is restored when G_j is written.
+template <int R>
+__global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_reg(int nsub, const SubDev* __restrict__ subs,
+                                                                      const ProbDev* __restrict__ probs,
+                                                                      const double* X, LocalState* ls,
+                                                                      const double* cpool, double* coef,
+                                                                      float* gpool, int only_active) {
+    constexpr int MM = 16 * R;
+    static_assert(FACT_THREADS == 256, "16 x 16 thread tile");
+    __shared__ float colk[2][MM];
+    __shared__ float rowb[2][MM];
+    __shared__ float swp[MM];
+    __shared__ int pivr[MM];
+    __shared__ int sinv[MM];
+    __shared__ int sh_r[2], sh_fail, sh_nswap;
+    __shared__ float sh_piv[2];
     const int i = blockIdx.x;
     if (i >= nsub) return;
+    if (only_active && !ls[i].active) return;
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
-    const int n = P.n, m = 2 * s.wx, W = s.wy;
-    const long long nn = (long long)n * n;
-    const double beta = P.beta;
-    const double* Dy = D + P.ofs;
-    double* Oy = O + P.ofs;
-    const T* G = gpool + s.goff;
-    T* w = wpool + s.voff;
-    auto bval = [=](int j, int t) -> double {
-        const int lx = t >> 1, f = t & 1;
-        const int gx = s.x0 + lx, gy = s.y0 + j;
-        const double* Df = Dy + f * nn;
-        double b = 0.0;
-        if (lx == 0 && gx > 0) b += Df[(long long)gy * n + gx - 1];
-        if (lx == s.wx - 1 && gx < n - 1) b += Df[(long long)gy * n + gx + 1];
-        if (j == 0 && gy > 0) b += Df[(long long)(gy - 1) * n + gx];
-        if (j == W - 1 && gy < n - 1) b += Df[(long long)(gy + 1) * n + gx];
-        return -beta * b;
-    };
-    auto owned_out = [=](int j, int t, double z) {
-        const int lx = t >> 1, f = t & 1;
-        const int gx = s.x0 + lx, gy = s.y0 + j;
-        if (gx >= s.ox0 && gx < s.ox0 + s.owx && gy >= s.oy0 && gy < s.oy0 + s.owy) {
-            const long long g = f * nn + (long long)gy * n + gx;
-            Oy[g] = -Dy[g] - z;
-        }
-    };
-    if (nir == 0) {
-        block_solve<T>(G, m, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)bval(j, t); },
-                       [=](int j, int t, T z) { owned_out(j, t, (double)z); });
-        return;
-    }
-    const int L = m * W;
-    double* b = bpool + s.voff;
-    double* z = zpool + s.voff;
-    double* r = rpool + s.voff;
-    for (int q = threadIdx.x; q < L; q += NT) {
-        b[q] = bval(q / m, q % m);
-        z[q] = 0.0;
-    }
-    __syncthreads();
-    block_solve<T>(G, m, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)b[j * m + t]; },
-                   [=](int j, int t, T zz) { z[j * m + t] += (double)zz; });
-    for (int it = 0; it < nir; ++it) {
-        local_linear_residual(s, beta, coef, 1.0, b, z, r, red);
-        block_solve<T>(G, m, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)r[j * m + t]; },
-                       [=](int j, int t, T zz) { z[j * m + t] += (double)zz; });
-    }
-    for (int q = threadIdx.x; q < L; q += NT) owned_out(q / m, q % m, z[q]);
-}
+    const int m = 2 * s.wx, W = s.wy, nn = s.wx * s.wy, mp = s.mp;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15, warp = tid >> 5, lane = tid & 31;
 
-// Linear RAS preconditioner: Z = sum_i tilde P_i J_i^-1 R_i R.
-template <typename T>
-__global__ void __launch_bounds__(NT) k_local_precond(int nsub, const SubDev* __restrict__ subs,
-                                                      const ProbDev* __restrict__ probs,
-                                                      const T* gpool, T* wpool, const double* R,
-                                                      double* Z) {
-    __shared__ T vec[MAX_M], tmp[MAX_M];
-    const int i = blockIdx.x;
-    if (i >= nsub) return;
-    const SubDev s = subs[i];
-    const ProbDev P = probs[s.prob];
-    const int n = P.n, m = 2 * s.wx, W = s.wy;
-    const long long nn = (long long)n * n;
-    const double* Ry = R + P.ofs;
-    double* Zy = Z + P.ofs;
-    auto rhs = [=](int j, int t) -> T {
-        const int lx = t >> 1, f = t & 1;
-        return (T)Ry[f * nn + (long long)(s.y0 + j) * n + s.x0 + lx];
-    };
-    auto out = [=](int j, int t, T z) {
-        const int lx = t >> 1, f = t & 1;
-        const int gx = s.x0 + lx, gy = s.y0 + j;
-        if (gx >= s.ox0 && gx < s.ox0 + s.owx && gy >= s.oy0 && gy < s.oy0 + s.owy)
-            Zy[f * nn + (long long)gy * n + gx] = (double)z;
-    };
-    block_solve<T>(gpool + s.goff, m, W, (T)P.beta, wpool + s.voff, vec, tmp, rhs, out);
+    const double eps = ls[i].eps;
+    const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu;
+    double* ca = coef + 3 * s.noff;
+    double* cb = ca + nn;
+    double* cc = cb + nn;
+    {
+        const double* c = cpool + s.voff;
+        const LocalView V = make_view(s, P, X, c, nullptr, 0.0);
+        for (int q = tid; q < nn; q += FACT_THREADS) {
+            const int lx = q % s.wx, ly = q / s.wx;
+            const double y = V.val(lx, ly, 0), p = V.val(lx, ly, 1);
+            double ph, d1, d2;
+            phi_eval(P.phi, P.kappa, y, ph, d1, d2);
+            ca[q] = d1;
+            cb[q] = inu * (1.0 - dP_eps(-p / mu, eps));
+            cc[q] = d2 * p - 1.0;
+        }
+    }
+    if (tid == 0) sh_fail = 0;
+    __syncthreads();
+
+    const float tbeta = (float)beta, tbeta2 = (float)(beta * beta), tdiag = (float)(4.0 * beta);
+    const long long blk = (long long)mp * mp;
+    float* G = gpool + s.goff;
+    float Mr[R][R];
+    for (int j = 0; j < W; ++j) {
+        // S_j = D_j - beta^2 G_{j-1}
+        const float* Gp = G + (long long)(j > 0 ? j - 1 : 0) * blk;
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            const int r = ty + 16 * a;
+#pragma unroll
+            for (int b = 0; b < R; ++b) {
+                const int c = tx + 16 * b;
+                float v = 0.f;
+                if (r < m && c < m) {
+                    if (j > 0) v = -tbeta2 * Gp[packed_index<float>(r, c, mp)];
+                    const int ix = r >> 1, f = r & 1, cx = c >> 1, cf = c & 1;
+                    const int q = j * s.wx + ix;
+                    if (cx == ix) {
+                        if (cf == f) v += tdiag + (float)ca[q];
+                        else if (f == 0) v += (float)cb[q];
+                        else v += (float)cc[q];
+                    } else if (cf == f && (cx == ix - 1 || cx == ix + 1)) {
+                        v -= tbeta;
+                    }
+                }
+                Mr[a][b] = v;
+            }
+        }
+        if (tid == 0) sh_nswap = 0;
+        __syncthreads();
+
+        int par = 0;
+        bool done = false;
+#pragma unroll
+        for (int kb = 0; kb < R; ++kb) {
+            for (int kt = 0; kt < 16 && !done; ++kt) {
+                const int k = 16 * kb + kt;
+                if (k >= m) {
+                    done = true;
+                    break;
+                }
+                if (tx == kt) {
+#pragma unroll
+                    for (int a = 0; a < R; ++a) colk[par][ty + 16 * a] = Mr[a][kb];
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    float best = -1.f;
+                    int bi = 0x7fffffff;
+                    for (int r = k + lane; r < m; r += 32) {
+                        const float v = fabsf(colk[par][r]);
+                        if (v > best) { best = v; bi = r; }
+                    }
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+                        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                    }
+                    if (lane == 0) {
+                        if (bi >= m || !(best > 0.f)) {
+                            sh_fail = 1;
+                        } else {
+                            sh_r[par] = bi;
+                            sh_piv[par] = colk[par][bi];
+                            pivr[k] = bi;
+                        }
+                    }
+                }
+                __syncthreads();
+                if (sh_fail) {
+                    done = true;
+                    break;
+                }
+                const int r = sh_r[par];
+                if (r != k) {
+                    const int tr = r & 15, ar = r >> 4;
+                    if (ty == kt) {
+#pragma unroll
+                        for (int b = 0; b < R; ++b) rowb[par][tx + 16 * b] = Mr[kb][b];
+                    }
+                    if (ty == tr) {
+#pragma unroll
+                        for (int a = 0; a < R; ++a)
+                            if (a == ar) {
+#pragma unroll
+                                for (int b = 0; b < R; ++b) swp[tx + 16 * b] = Mr[a][b];
+                            }
+                    }
+                    __syncthreads();
+                    if (ty == kt) {
+#pragma unroll
+                        for (int b = 0; b < R; ++b) Mr[kb][b] = swp[tx + 16 * b];
+                    }
+                    if (ty == tr) {
+#pragma unroll
+                        for (int a = 0; a < R; ++a)
+                            if (a == ar) {
+#pragma unroll
+                                for (int b = 0; b < R; ++b) Mr[a][b] = rowb[par][tx + 16 * b];
+                            }
+                    }
+                    if (tid == 0) {
+                        const float t = colk[par][k];
+                        colk[par][k] = colk[par][r];
+                        colk[par][r] = t;
+                        sh_nswap += 1;
+                    }
+                    __syncthreads();
+                }
+                const float inv = 1.f / sh_piv[par];
+                if (ty == kt) {
+#pragma unroll
+                    for (int b = 0; b < R; ++b) {
+                        const int c = tx + 16 * b;
+                        rowb[par][c] = (c == k) ? inv : Mr[kb][b] * inv;
+                    }
+                }
+                if (tid == 0) colk[par][k] = 0.f;
+                __syncthreads();
+                if (tx == kt) {
+#pragma unroll
+                    for (int a = 0; a < R; ++a) Mr[a][kb] = 0.f;
+                }
+                float ck[R];
+#pragma unroll
+                for (int a = 0; a < R; ++a) ck[a] = colk[par][ty + 16 * a];
+#pragma unroll
+                for (int b = 0; b < R; ++b) {
+                    const float rb = rowb[par][tx + 16 * b];
+#pragma unroll
+                    for (int a = 0; a < R; ++a) Mr[a][b] = fmaf(-ck[a], rb, Mr[a][b]);
+                }
+                if (ty == kt) {
+#pragma unroll
+                    for (int b = 0; b < R; ++b) Mr[kb][b] = rowb[par][tx + 16 * b];
+                }
+                par ^= 1;
+            }
+        }
+        if (sh_fail) break;
+        // column order of the inverse: undo the row interchanges in reverse
+        if (tid == 0) {
+            for (int c = 0; c < m; ++c) sinv[c] = c;
+            if (sh_nswap > 0) {
+                for (int c = 0; c < m; ++c) swp[c] = __int_as_float(c);   // sig, as bits
+                for (int k = m - 1; k >= 0; --k) {
+                    const int r = pivr[k];
+                    if (r != k) {
+                        const float t = swp[k];
+                        swp[k] = swp[r];
+                        swp[r] = t;
+                    }
+                }
+                for (int c = 0; c < m; ++c) sinv[__float_as_int(swp[c])] = c;
+            }
+        }
+        __syncthreads();
+        float* Gj = G + (long long)j * blk;
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            const int r = ty + 16 * a;
+#pragma unroll
+            for (int b = 0; b < R; ++b) {
+                const int c = tx + 16 * b;
+                if (r < mp && c < mp) {
+                    if (r < m && c < m) Gj[packed_index<float>(r, sinv[c], mp)] = Mr[a][b];
+                    else Gj[packed_index<float>(r, c, mp)] = 0.f;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (sh_fail && tid == 0) {
+        ls[i].status = ST_ESINGULAR;
+        ls[i].active = 0;
+    }
 }
 
 template <typename T>
@@ -615,28 +623,39 @@ cudaError_t launch_local_init(cudaStream_t st, int nsub, const SubDev* subs, con
     return cudaGetLastError();
 }
 
+template <int R>
+cudaError_t launch_factor_reg(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,
+                              const double* X, LocalState* ls, const double* cpool, double* coef,
+                              float* gpool, int only_active) {
+    count_launch();
+    k_local_factor_reg<R><<<nsub, FACT_THREADS, 0, st>>>(nsub, subs, probs, X, ls, cpool, coef, gpool,
+                                                         only_active);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_local_factor(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                                 const ProbDev* probs, const double* X, LocalState* ls,
                                 const double* cpool, double* coef, T* gpool, int only_active) {
+    if (sizeof(T) == sizeof(float)) {
+        // register tile covering the largest packed block (mp <= 16 R)
+        const int mpmax = ((maxm + 31) / 32) * 32;
+        float* g = reinterpret_cast<float*>(gpool);
+        switch (mpmax / 16) {
+            case 2: return launch_factor_reg<2>(st, nsub, subs, probs, X, ls, cpool, coef, g, only_active);
+            case 4: return launch_factor_reg<4>(st, nsub, subs, probs, X, ls, cpool, coef, g, only_active);
+            case 6: return launch_factor_reg<6>(st, nsub, subs, probs, X, ls, cpool, coef, g, only_active);
+            case 8: return launch_factor_reg<8>(st, nsub, subs, probs, X, ls, cpool, coef, g, only_active);
+            case 10: return launch_factor_reg<10>(st, nsub, subs, probs, X, ls, cpool, coef, g, only_active);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     const size_t sm = factor_smem<T>(maxm);
     cudaError_t e = cudaFuncSetAttribute(k_local_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     count_launch();
     k_local_factor<T><<<nsub, FACT_THREADS, sm, st>>>(nsub, maxm, subs, probs, X, ls, cpool, coef, gpool,
                                                       only_active);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_local_direction(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
-                                   const ProbDev* probs, LocalState* ls, NewtonParams np,
-                                   const double* coef, const T* gpool, const double* Kpool,
-                                   double* dpool, double* rpool, T* wpool) {
-    (void)maxm;
-    count_launch();
-    k_local_direction<T><<<nsub, NT, 0, st>>>(nsub, subs, probs, ls, np, coef, gpool, Kpool, dpool, rpool,
-                                              wpool);
     return cudaGetLastError();
 }
 
@@ -657,40 +676,10 @@ cudaError_t launch_local_prolong(cudaStream_t st, int nsub, const SubDev* subs, 
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_local_jvp(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
-                             const ProbDev* probs, const T* gpool, T* wpool, const double* coef,
-                             double* zpool, double* rpool, double* bpool, int nir, const double* D,
-                             double* O) {
-    (void)maxm;
-    count_launch();
-    k_local_jvp<T><<<nsub, NT, 0, st>>>(nsub, subs, probs, gpool, wpool, coef, zpool, rpool, bpool, nir, D, O);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_local_precond(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
-                                 const ProbDev* probs, const T* gpool, T* wpool, const double* R,
-                                 double* Z) {
-    (void)maxm;
-    count_launch();
-    k_local_precond<T><<<nsub, NT, 0, st>>>(nsub, subs, probs, gpool, wpool, R, Z);
-    return cudaGetLastError();
-}
-
 #define RAS_INSTANTIATE(T)                                                                            \
     template cudaError_t launch_local_factor<T>(cudaStream_t, int, int, const SubDev*, const ProbDev*,  \
                                                 const double*, LocalState*, const double*, double*, T*, \
-                                                int);                                                   \
-    template cudaError_t launch_local_direction<T>(cudaStream_t, int, int, const SubDev*,               \
-                                                   const ProbDev*, LocalState*, NewtonParams,           \
-                                                   const double*, const T*, const double*, double*,     \
-                                                   double*, T*);                                        \
-    template cudaError_t launch_local_jvp<T>(cudaStream_t, int, int, const SubDev*, const ProbDev*,     \
-                                             const T*, T*, const double*, double*, double*, double*,    \
-                                             int, const double*, double*);                              \
-    template cudaError_t launch_local_precond<T>(cudaStream_t, int, int, const SubDev*,                 \
-                                                 const ProbDev*, const T*, T*, const double*, double*);
+                                                int);
 RAS_INSTANTIATE(float)
 RAS_INSTANTIATE(double)
 #undef RAS_INSTANTIATE

@@ -7,9 +7,14 @@
 //      local vectors: 2*wx*wy FP64, interleaved (y, p) per node, nodes
 //                     lexicographic with the x1 index fastest, at voff;
 //      node arrays:   wx*wy FP64 (Jacobian coefficients), at noff;
-//      factors:       wy blocks G_j of (2wx)^2 T (row-major), at goff, where
-//                     G_j is the inverse of the j-th Schur complement of the
-//                     block-tridiagonal local Jacobian.
+//      factors:       wy blocks G_j of mp^2 T (mp = 2wx rounded up to 32, zero
+//                     padded) at goff, where G_j is the inverse of the j-th
+//                     Schur complement of the block-tridiagonal local Jacobian.
+//                     Each block is stored in the "packed" order of
+//                     packed_index(): the streaming solve reads it as mp/32
+//                     contiguous slabs, one per group of 32 rows, and thread t
+//                     of a 256-thread CTA finds its share of every slab as
+//                     contiguous 16-byte vectors.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -36,7 +41,9 @@ struct SubDev {
     int prob;
     int x0, y0, wx, wy;       // Omega_i
     int ox0, oy0, owx, owy;   // tilde Omega_i (owned nodes)
-    long long goff;           // factor offset (elements of T)
+    int mp;                   // 2*wx rounded up to a multiple of 32 (packed block size)
+    int pad_;
+    long long goff;           // factor offset (elements of T); wy blocks of mp*mp
     long long voff;           // local-vector offset (doubles), length 2*wx*wy
     long long noff;           // node-array offset (doubles), length wx*wy
 };
@@ -52,12 +59,29 @@ struct NewtonParams {
     int kmax, max_halvings, ir_max, pad;
 };
 
+// Packed position of element (r, c) of an mp x mp block of T. Thread
+// t = 8*rho + kappa (256 threads) owns rows rho + 32 s and the column chunk
+// kappa (mp/8 columns); within slab s its chunk is nv = mp/8/VE vectors of 16
+// bytes (VE = 16/sizeof(T)) at slab offsets (v*256 + t)*16.
+template <typename T>
+__host__ __device__ __forceinline__ long long packed_index(int r, int c, int mp) {
+    constexpr int VE = 16 / (int)sizeof(T);
+    const int cw = mp >> 3, nv = cw / VE;
+    const int rho = r & 31, s = r >> 5;
+    const int kappa = c / cw, cc = c - kappa * cw;
+    const int v = cc / VE, l = cc - v * VE;
+    const int t = (rho << 3) + kappa;
+    const long long e = (long long)s * nv + v;
+    return (e * 256 + t) * VE + l;
+}
+
 // Status values (same numbers as the public RAS_* codes).
 constexpr int ST_OK = 0;
 constexpr int ST_OK_FLOOR = 1;
 constexpr int ST_ENOCONV = -3;
 constexpr int ST_ESINGULAR = -5;
 constexpr int ST_ENONFINITE = -6;
+constexpr int ST_ETIMEOUT = -7;
 
 // ------------------------------------------------------------- pointwise math
 // Smoothed projection of Sec. 3.1 in the cancellation-free quotient form of
@@ -173,7 +197,7 @@ template <typename T>
 cudaError_t launch_local_direction(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                                    const ProbDev* probs, LocalState* ls, NewtonParams np,
                                    const double* coef, const T* gpool, const double* Kpool,
-                                   double* dpool, double* rpool, T* wpool);
+                                   double* dpool, double* rpool, T* wpool, int* err);
 cudaError_t launch_local_linesearch(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,
                                     const double* X, LocalState* ls, NewtonParams np, double* cpool,
                                     const double* dpool, double* Kpool, double* Ktpool,
@@ -184,9 +208,9 @@ template <typename T>
 cudaError_t launch_local_jvp(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                              const ProbDev* probs, const T* gpool, T* wpool, const double* coef,
                              double* zpool, double* rpool, double* bpool, int nir, const double* D,
-                             double* O);
+                             double* O, int* err);
 template <typename T>
 cudaError_t launch_local_precond(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                                  const ProbDev* probs, const T* gpool, T* wpool, const double* R,
-                                 double* Z);
+                                 double* Z, int* err);
 }  // namespace ras

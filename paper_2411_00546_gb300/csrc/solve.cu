@@ -1,0 +1,475 @@
+// Local block-tridiagonal solves J_i z = b with the stored factors G_j:
+//   w_0 = b_0, w_j = b_j + beta G_{j-1} w_{j-1};
+//   z_{W-1} = G_{W-1} w_{W-1},  z_j = G_j (w_j + beta z_{j+1}),
+// used by the Newton direction of the local solves (Alg. 1 inside Alg. 3),
+// the Jacobian action of the RASPEN function (Alg. 4) and the linear RAS
+// preconditioner. One CTA (256 threads) per subdomain.
+//
+// The solve is a chain of 2W-1 dependent matrix-vector products; each reads
+// one mp x mp block (100 KB in FP32 at mp = 160) that does not depend on the
+// chain. The blocks are therefore streamed ahead of the chain: every block is
+// stored as mp/32 contiguous slabs (packed_index), and a ring of DEPTH slab
+// buffers in shared memory is filled by TMA bulk copies (cp.async.bulk,
+// completion on an mbarrier) issued DEPTH slabs ahead of the slab being used.
+// Thread t = 8 rho + kappa multiplies its own contiguous part of a slab (row
+// rho + 32 s, column chunk kappa) with the vector and the 8 partial sums of a
+// row are added with warp shuffles. Every mbarrier wait is bounded; on timeout
+// the CTA waits (bounded) for its copies in flight, records ST_ETIMEOUT in
+// *err and returns.
+#include <stdint.h>
+
+#include "ras_internal.cuh"
+
+namespace ras {
+
+namespace {
+
+constexpr int NT = LOC_THREADS;
+static_assert(NT == 256, "packed layout assumes 256 threads");
+constexpr long long WAIT_LIMIT = 1LL << 22;   // try_wait rounds before giving up
+
+template <typename T>
+struct Ring {
+    static constexpr int DEPTH = (sizeof(T) == 4) ? 4 : 2;
+    static constexpr int SLAB_MAX = 256 * ((MAX_M / 8) / (16 / (int)sizeof(T))) * 16;  // bytes
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Arm `bar` for `bytes` and copy them from global `src` to shared `dst`.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait for phase `parity` of `bar`; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_x(T v, int m) {
+    return __shfl_xor_sync(0xffffffffu, v, m);
+}
+
+// Shared state of one CTA's slab stream. `seq` counts slabs over the CTA's
+// whole life, so ring slot and mbarrier parity stay consistent across solves.
+template <typename T>
+struct Stream {
+    unsigned char* ring;   // DEPTH slabs
+    uint64_t* full;        // DEPTH mbarriers
+    int* fail;             // shared flag
+    uint32_t seq;          // slabs consumed so far (uniform)
+};
+
+template <typename T>
+__device__ void stream_init(Stream<T>& S, unsigned char* smem) {
+    constexpr int D = Ring<T>::DEPTH;
+    S.ring = smem;
+    S.full = reinterpret_cast<uint64_t*>(smem + D * Ring<T>::SLAB_MAX);
+    S.fail = reinterpret_cast<int*>(S.full + D);
+    S.seq = 0;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < D; ++k) mbar_init(&S.full[k], 1);
+        *S.fail = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+}
+
+// On a timeout: wait (bounded) for the copies still in flight, then report.
+template <typename T>
+__device__ void stream_abort(Stream<T>& S, uint32_t first, uint32_t last, int* err) {
+    constexpr int D = Ring<T>::DEPTH;
+    if (threadIdx.x == 0) {
+        for (uint32_t g = first; g < last; ++g) mbar_wait(&S.full[g % D], (g / D) & 1u);
+        if (err) atomicExch(err, ST_ETIMEOUT);
+    }
+    __syncthreads();
+}
+
+// z = J_i^-1 b (see the file comment). rhs(j, t) -> T gives b; out(j, t, z)
+// consumes z. vec, tmp: shared arrays of mp T. w: global scratch, m*W T.
+// Returns false if a wait timed out (the CTA must then return).
+template <typename T, class Rhs, class Out>
+__device__ bool stream_solve(Stream<T>& S, const T* __restrict__ G, int m, int mp, int W, T beta, T* w, T* vec,
+                             T* tmp, Rhs rhs, Out out, int* err) {
+    constexpr int D = Ring<T>::DEPTH;
+    constexpr int VE = 16 / (int)sizeof(T);
+    const int tid = threadIdx.x, kappa = tid & 7, rho = tid >> 3;
+    const int cw = mp >> 3, nv = cw / VE, nslab = mp >> 5;
+    const uint32_t slab_elems = 256u * nv * VE;
+    const uint32_t slab_bytes = slab_elems * sizeof(T);
+    const long long blk = (long long)mp * mp;
+    const uint32_t total = (uint32_t)((2 * W - 1) * nslab);
+    const uint32_t base = S.seq;
+    // slab q of this solve: forward blocks 0..W-2, then backward W-1..0
+    auto src = [&](uint32_t q) -> const T* {
+        const int f = (W - 1) * nslab;
+        int jb, sl;
+        if ((int)q < f) {
+            jb = q / nslab;
+            sl = q % nslab;
+        } else {
+            const int r = q - f;
+            jb = W - 1 - r / nslab;
+            sl = r % nslab;
+        }
+        return G + jb * blk + (long long)sl * slab_elems;
+    };
+    if (tid == 0) {
+        fence_proxy_async();
+        for (uint32_t q = 0; q < total && q < (uint32_t)D; ++q) {
+            const uint32_t g = base + q;
+            tma_load_1d(S.ring + (g % D) * Ring<T>::SLAB_MAX, src(q), slab_bytes, &S.full[g % D]);
+        }
+    }
+    uint32_t q = 0;
+    // one mp x mp product from the stream: tmp = G_(next block) vec
+    auto matvec = [&]() -> bool {
+        for (int sl = 0; sl < nslab; ++sl, ++q) {
+            const uint32_t g = base + q;
+            const bool ok = mbar_wait(&S.full[g % D], (g / D) & 1u);
+            const T* slot = reinterpret_cast<const T*>(S.ring + (g % D) * Ring<T>::SLAB_MAX);
+            T acc = (T)0;
+            if (ok) {
+                const T* vk = vec + kappa * cw;
+                for (int v = 0; v < nv; ++v) {
+                    const T* gv = slot + ((long long)v * 256 + tid) * VE;
+#pragma unroll
+                    for (int l = 0; l < VE; ++l) acc += gv[l] * vk[v * VE + l];
+                }
+            }
+            if (__syncthreads_or(!ok)) {
+                // copies issued so far: relative slabs < min(total, q + D)
+                stream_abort(S, g, base + min(total, q + (uint32_t)D), err);
+                S.seq = base + total;
+                return false;
+            }
+            if (tid == 0 && q + D < total) {
+                fence_proxy_async();
+                const uint32_t gn = g + D;
+                tma_load_1d(S.ring + (gn % D) * Ring<T>::SLAB_MAX, src(q + D), slab_bytes, &S.full[gn % D]);
+            }
+            acc += shfl_x(acc, 1);
+            acc += shfl_x(acc, 2);
+            acc += shfl_x(acc, 4);
+            if (kappa == 0) tmp[rho + 32 * sl] = acc;
+        }
+        __syncthreads();
+        return true;
+    };
+    for (int t = m + tid; t < mp; t += NT) vec[t] = (T)0;
+    for (int j = 0; j < W; ++j) {
+        for (int t = tid; t < m; t += NT) {
+            T v = rhs(j, t);
+            if (j > 0) v += beta * tmp[t];
+            vec[t] = v;
+            w[j * m + t] = v;
+        }
+        __syncthreads();
+        if (j < W - 1 && !matvec()) return false;
+    }
+    for (int j = W - 1; j >= 0; --j) {
+        for (int t = tid; t < m; t += NT) {
+            T v = w[j * m + t];
+            if (j < W - 1) v += beta * tmp[t];
+            vec[t] = v;
+        }
+        __syncthreads();
+        if (!matvec()) return false;
+        for (int t = tid; t < m; t += NT) out(j, t, tmp[t]);
+    }
+    __syncthreads();
+    S.seq = base + total;
+    return true;
+}
+
+template <typename T>
+size_t solve_smem() {
+    return (size_t)Ring<T>::DEPTH * Ring<T>::SLAB_MAX + Ring<T>::DEPTH * sizeof(uint64_t) + 16;
+}
+
+// r = bsign * B - J_i z in FP64 with the Jacobian coefficients stored by the
+// factor kernel (5-point coupling inside Omega_i only); returns ||r||^2.
+__device__ double local_linear_residual(const SubDev& s, double beta, const double* coef, double bsign,
+                                        const double* B, const double* z, double* r, double* red) {
+    const int wx = s.wx, wy = s.wy, nn = wx * wy;
+    const double* ca = coef + 3 * s.noff;
+    const double* cb = ca + nn;
+    const double* cc = cb + nn;
+    double r2 = 0.0, dummy = 0.0;
+    for (int q = threadIdx.x; q < nn; q += NT) {
+        const int lx = q % wx, ly = q / wx;
+        const double zyc = z[2 * q], zpc = z[2 * q + 1];
+        double sy = 0.0, sp = 0.0;
+        if (lx > 0) { sy += z[2 * (q - 1)]; sp += z[2 * (q - 1) + 1]; }
+        if (lx < wx - 1) { sy += z[2 * (q + 1)]; sp += z[2 * (q + 1) + 1]; }
+        if (ly > 0) { sy += z[2 * (q - wx)]; sp += z[2 * (q - wx) + 1]; }
+        if (ly < wy - 1) { sy += z[2 * (q + wx)]; sp += z[2 * (q + wx) + 1]; }
+        const double Jy = beta * (4.0 * zyc - sy) + ca[q] * zyc + cb[q] * zpc;
+        const double Jp = beta * (4.0 * zpc - sp) + cc[q] * zyc + ca[q] * zpc;
+        const double ry = bsign * B[2 * q] - Jy, rp = bsign * B[2 * q + 1] - Jp;
+        r[2 * q] = ry;
+        r[2 * q + 1] = rp;
+        r2 += ry * ry + rp * rp;
+    }
+    block_sum2<NT>(r2, dummy, red);
+    return r2;
+}
+
+// Newton direction d = -J_i^-1 K_i. In mixed precision the FP32 solve is
+// followed by FP64 iterative refinement: r = -K - J d with the FP64 Jacobian
+// (matrix-free, from the coefficients the factor kernel stored), d += J^-1 r,
+// until ||r|| <= ir_rtol ||K|| or ir_max corrections.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_local_direction(int nsub, const SubDev* __restrict__ subs,
+                                                        const ProbDev* __restrict__ probs, LocalState* ls,
+                                                        NewtonParams np, const double* coef, const T* gpool,
+                                                        const double* Kpool, double* dpool, double* rpool,
+                                                        T* wpool, int* err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ T vec[MAX_M], tmp[MAX_M];
+    __shared__ double red[2 * NT];
+    const int i = blockIdx.x;
+    if (i >= nsub) return;
+    if (!ls[i].active) return;
+    const SubDev s = subs[i];
+    const ProbDev P = probs[s.prob];
+    const int m = 2 * s.wx, W = s.wy, L = m * W;
+    const double beta = P.beta;
+    const double* K = Kpool + s.voff;
+    double* d = dpool + s.voff;
+    double* r = rpool + s.voff;
+    T* w = wpool + s.voff;
+    const T* G = gpool + s.goff;
+    Stream<T> S;
+    stream_init(S, smem);
+    double b2 = 0.0, dummy = 0.0;
+    for (int q = threadIdx.x; q < L; q += NT) {
+        const double v = -K[q];
+        r[q] = v;
+        d[q] = 0.0;
+        b2 += v * v;
+    }
+    block_sum2<NT>(b2, dummy, red);
+    const double bnorm = sqrt(b2);
+    int nsolves = 0;
+    for (int it = 0;; ++it) {
+        ++nsolves;
+        if (!stream_solve<T>(
+                S, G, m, s.mp, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)r[j * m + t]; },
+                [=](int j, int t, T z) { d[j * m + t] += (double)z; }, err)) {
+            if (threadIdx.x == 0) {
+                ls[i].status = ST_ETIMEOUT;
+                ls[i].active = 0;
+            }
+            return;
+        }
+        if (it >= np.ir_max) break;
+        const double r2 = local_linear_residual(s, beta, coef, -1.0, K, d, r, red);
+        if (sqrt(r2) <= np.ir_rtol * bnorm) break;
+    }
+    if (threadIdx.x == 0) ls[i].solves += nsolves;
+}
+
+// Jacobian action of the RASPEN function (Alg. 4):
+//   O = -D - sum_i tilde P_i J_i(x^(i))^-1 B_i D,  B_i D = R_i A (I - P_i R_i) D,
+// i.e. b = -beta * (sum of D over the 5-point neighbours outside Omega_i).
+// With nir > 0 (mixed precision) the local solve is refined nir times in FP64:
+// z += J^-1 (b - J z), J from the coefficients at x^(i).
+template <typename T>
+__global__ void __launch_bounds__(NT) k_local_jvp(int nsub, const SubDev* __restrict__ subs,
+                                                  const ProbDev* __restrict__ probs, const T* gpool, T* wpool,
+                                                  const double* coef, double* zpool, double* rpool,
+                                                  double* bpool, int nir, const double* D, double* O,
+                                                  int* err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ T vec[MAX_M], tmp[MAX_M];
+    __shared__ double red[2 * NT];
+    const int i = blockIdx.x;
+    if (i >= nsub) return;
+    const SubDev s = subs[i];
+    const ProbDev P = probs[s.prob];
+    const int n = P.n, m = 2 * s.wx, W = s.wy;
+    const long long nn = (long long)n * n;
+    const double beta = P.beta;
+    const double* Dy = D + P.ofs;
+    double* Oy = O + P.ofs;
+    const T* G = gpool + s.goff;
+    T* w = wpool + s.voff;
+    Stream<T> S;
+    stream_init(S, smem);
+    auto bval = [=](int j, int t) -> double {
+        const int lx = t >> 1, f = t & 1;
+        const int gx = s.x0 + lx, gy = s.y0 + j;
+        const double* Df = Dy + f * nn;
+        double b = 0.0;
+        if (lx == 0 && gx > 0) b += Df[(long long)gy * n + gx - 1];
+        if (lx == s.wx - 1 && gx < n - 1) b += Df[(long long)gy * n + gx + 1];
+        if (j == 0 && gy > 0) b += Df[(long long)(gy - 1) * n + gx];
+        if (j == W - 1 && gy < n - 1) b += Df[(long long)(gy + 1) * n + gx];
+        return -beta * b;
+    };
+    auto owned_out = [=](int j, int t, double z) {
+        const int lx = t >> 1, f = t & 1;
+        const int gx = s.x0 + lx, gy = s.y0 + j;
+        if (gx >= s.ox0 && gx < s.ox0 + s.owx && gy >= s.oy0 && gy < s.oy0 + s.owy) {
+            const long long g = f * nn + (long long)gy * n + gx;
+            Oy[g] = -Dy[g] - z;
+        }
+    };
+    if (nir == 0) {
+        stream_solve<T>(
+            S, G, m, s.mp, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)bval(j, t); },
+            [=](int j, int t, T z) { owned_out(j, t, (double)z); }, err);
+        return;
+    }
+    const int L = m * W;
+    double* b = bpool + s.voff;
+    double* z = zpool + s.voff;
+    double* r = rpool + s.voff;
+    for (int q = threadIdx.x; q < L; q += NT) {
+        b[q] = bval(q / m, q % m);
+        z[q] = 0.0;
+    }
+    __syncthreads();
+    if (!stream_solve<T>(
+            S, G, m, s.mp, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)b[j * m + t]; },
+            [=](int j, int t, T zz) { z[j * m + t] += (double)zz; }, err))
+        return;
+    for (int it = 0; it < nir; ++it) {
+        local_linear_residual(s, beta, coef, 1.0, b, z, r, red);
+        if (!stream_solve<T>(
+                S, G, m, s.mp, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)r[j * m + t]; },
+                [=](int j, int t, T zz) { z[j * m + t] += (double)zz; }, err))
+            return;
+    }
+    for (int q = threadIdx.x; q < L; q += NT) owned_out(q / m, q % m, z[q]);
+}
+
+// Linear RAS preconditioner: Z = sum_i tilde P_i J_i^-1 R_i R.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_local_precond(int nsub, const SubDev* __restrict__ subs,
+                                                      const ProbDev* __restrict__ probs, const T* gpool,
+                                                      T* wpool, const double* R, double* Z, int* err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ T vec[MAX_M], tmp[MAX_M];
+    const int i = blockIdx.x;
+    if (i >= nsub) return;
+    const SubDev s = subs[i];
+    const ProbDev P = probs[s.prob];
+    const int n = P.n, m = 2 * s.wx, W = s.wy;
+    const long long nn = (long long)n * n;
+    const double* Ry = R + P.ofs;
+    double* Zy = Z + P.ofs;
+    Stream<T> S;
+    stream_init(S, smem);
+    auto rhs = [=](int j, int t) -> T {
+        const int lx = t >> 1, f = t & 1;
+        return (T)Ry[f * nn + (long long)(s.y0 + j) * n + s.x0 + lx];
+    };
+    auto out = [=](int j, int t, T z) {
+        const int lx = t >> 1, f = t & 1;
+        const int gx = s.x0 + lx, gy = s.y0 + j;
+        if (gx >= s.ox0 && gx < s.ox0 + s.owx && gy >= s.oy0 && gy < s.oy0 + s.owy)
+            Zy[f * nn + (long long)gy * n + gx] = (double)z;
+    };
+    stream_solve<T>(S, gpool + s.goff, m, s.mp, W, (T)P.beta, wpool + s.voff, vec, tmp, rhs, out, err);
+}
+
+template <class K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_local_direction(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
+                                   const ProbDev* probs, LocalState* ls, NewtonParams np,
+                                   const double* coef, const T* gpool, const double* Kpool,
+                                   double* dpool, double* rpool, T* wpool, int* err) {
+    (void)maxm;
+    const size_t sm = solve_smem<T>();
+    cudaError_t e = set_smem(k_local_direction<T>, sm);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_local_direction<T><<<nsub, NT, sm, st>>>(nsub, subs, probs, ls, np, coef, gpool, Kpool, dpool, rpool,
+                                               wpool, err);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_local_jvp(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
+                             const ProbDev* probs, const T* gpool, T* wpool, const double* coef,
+                             double* zpool, double* rpool, double* bpool, int nir, const double* D,
+                             double* O, int* err) {
+    (void)maxm;
+    const size_t sm = solve_smem<T>();
+    cudaError_t e = set_smem(k_local_jvp<T>, sm);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_local_jvp<T><<<nsub, NT, sm, st>>>(nsub, subs, probs, gpool, wpool, coef, zpool, rpool, bpool, nir, D, O,
+                                         err);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_local_precond(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
+                                 const ProbDev* probs, const T* gpool, T* wpool, const double* R,
+                                 double* Z, int* err) {
+    (void)maxm;
+    const size_t sm = solve_smem<T>();
+    cudaError_t e = set_smem(k_local_precond<T>, sm);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_local_precond<T><<<nsub, NT, sm, st>>>(nsub, subs, probs, gpool, wpool, R, Z, err);
+    return cudaGetLastError();
+}
+
+#define RAS_INSTANTIATE(T)                                                                                   \
+    template cudaError_t launch_local_direction<T>(cudaStream_t, int, int, const SubDev*, const ProbDev*,      \
+                                                   LocalState*, NewtonParams, const double*, const T*,          \
+                                                   const double*, double*, double*, T*, int*);                 \
+    template cudaError_t launch_local_jvp<T>(cudaStream_t, int, int, const SubDev*, const ProbDev*, const T*,  \
+                                             T*, const double*, double*, double*, double*, int,                \
+                                             const double*, double*, int*);                                    \
+    template cudaError_t launch_local_precond<T>(cudaStream_t, int, int, const SubDev*, const ProbDev*,        \
+                                                 const T*, T*, const double*, double*, int*);
+RAS_INSTANTIATE(float)
+RAS_INSTANTIATE(double)
+#undef RAS_INSTANTIATE
+
+}  // namespace ras

@@ -19,6 +19,7 @@ RAS_ENOMEM = -2
 RAS_ENOCONV = -3
 RAS_ESINGULAR = -5
 RAS_ENONFINITE = -6
+RAS_ETIMEOUT = -7
 RAS_ENOTIMPL = -8
 RAS_ECUDA = -9
 RAS_ESTATE = -10
