@@ -307,6 +307,17 @@ def main():
                 "frac": achieved / peak, "traffic": None, "peak_source": src,
                 "avg_launch_ms": dms / max(dn, 1), "launches": dn}
     kernel_share = {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items()}
+    kernels = {}
+    for k, (kms, kn, kw) in prof.items():
+        if kn == 0:
+            continue
+        e = {"ms_total": round(kms, 3), "launches": kn, "avg_ms": round(kms / kn, 4)}
+        if kw > 0 and kms > 0:
+            if k == "factor":
+                e["tflops"] = round(kw / (kms / 1e3) / 1e12, 3)
+            else:
+                e["gbs"] = round(kw / (kms / 1e3) / 1e9, 1)
+        kernels[k] = e
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -339,7 +350,9 @@ def main():
                           "method": "RASPEN_eps (Alg. 2), mixed precision", "parallelism": "replicas",
                           "l2": "no flush: device working set %.2f GB (local factors, Krylov basis) far "
                                 "above the 129 MB L2" % (dev_bytes / 1e9),
-                          "solve_stats": stats[-1], "fp64": fp64, "kernel_share": kernel_share},
+                          "solve_stats": stats[-1], "fp64": fp64, "kernel_share": kernel_share,
+                          "kernels": kernels, "y_max": float(np.abs(y_mixed).max()),
+                          "p_max": float(np.abs(p_mixed).max())},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clocks.summary()}
         print(json.dumps(out))

@@ -375,14 +375,48 @@ __global__ void __launch_bounds__(NT) k_local_prolong(int nsub, const SubDev* __
     }
 }
 
+// R consecutive floats of shared memory (16-byte aligned) <-> registers, in
+// 16-, 8- and 4-byte pieces.
+template <int R>
+__device__ __forceinline__ void load_vec(const float* src, float* v) {
+#pragma unroll
+    for (int q = 0; q + 4 <= R; q += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(src + q);
+        v[q] = t.x; v[q + 1] = t.y; v[q + 2] = t.z; v[q + 3] = t.w;
+    }
+    if (R % 4 >= 2) {
+        const float2 t = *reinterpret_cast<const float2*>(src + (R / 4) * 4);
+        v[(R / 4) * 4] = t.x;
+        v[(R / 4) * 4 + 1] = t.y;
+    }
+    if (R % 2) v[R - 1] = src[R - 1];
+}
+
+template <int R>
+__device__ __forceinline__ void store_vec(float* dst, const float* v) {
+#pragma unroll
+    for (int q = 0; q + 4 <= R; q += 4)
+        *reinterpret_cast<float4*>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+    if (R % 4 >= 2) *reinterpret_cast<float2*>(dst + (R / 4) * 4) = make_float2(v[(R / 4) * 4], v[(R / 4) * 4 + 1]);
+    if (R % 2) dst[R - 1] = v[R - 1];
+}
+
 // FP32 factorisation with the block held in registers. Thread (ty, tx) of a
-// 16 x 16 CTA owns rows ty + 16a and columns tx + 16b (a, b < R) of the
-// 16R x 16R block, so every elimination step updates registers only; the
-// pivot column and the scaled pivot row are broadcast through shared memory
-// (double-buffered, three barriers per step). Partial pivoting as in the
-// generic kernel (max |.| among the not yet eliminated rows, ties to the
-// lowest row); an off-diagonal pivot row is swapped in physically and the
-// column order of the inverse is restored when G_j is written.
+// 16 x 16 CTA owns the R x R tile of rows ty*R + a and columns tx*R + b of the
+// 16R x 16R block, so every elimination step updates registers only. Step k
+// (k = kt*R + kb: owner kt, register index kb) publishes column k (owners
+// tx == kt) and row k (owners ty == kt) in shared memory as 16-byte vectors
+// (double-buffered), then one barrier, then the rank-1 update.
+//
+// Partial pivoting (max |.| in the column among the rows not yet eliminated,
+// ties to the lowest row) is applied optimistically: every step each warp
+// checks 20 candidate rows against the diagonal and raises a flag when one is
+// larger. A block row that raised the flag is redone from its Schur complement
+// by a shared-memory Gauss-Jordan elimination with full partial pivoting; a
+// block row that did not is exactly what partial pivoting computes.
+//
+// G_{j-1} stays in shared memory (natural order) as the source of the next
+// Schur complement and of the coalesced write-out in packed order.
 template <int R>
 __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_reg(int nsub, const SubDev* __restrict__ subs,
                                                                       const ProbDev* __restrict__ probs,
@@ -390,14 +424,18 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_reg(int nsub, 
                                                                       const double* cpool, double* coef,
                                                                       float* gpool, int only_active) {
     constexpr int MM = 16 * R;
+    constexpr int PAD = ((R + 3) / 4) * 4;   // owner stride in the broadcast buffers
     static_assert(FACT_THREADS == 256, "16 x 16 thread tile");
-    __shared__ float colk[2][MM];
-    __shared__ float rowb[2][MM];
-    __shared__ float swp[MM];
+    static_assert(16 * PAD >= MM, "broadcast buffers hold a full column");
+    __shared__ __align__(16) float colk[2][16 * PAD];
+    __shared__ __align__(16) float rowb[2][16 * PAD];
     __shared__ int pivr[MM];
     __shared__ int sinv[MM];
-    __shared__ int sh_r[2], sh_fail, sh_nswap;
-    __shared__ float sh_piv[2];
+    __shared__ int used[MM];
+    __shared__ int sh_viol, sh_r, sh_fail;
+    __shared__ float sh_piv;
+    extern __shared__ __align__(16) float Ms[];
+    constexpr int LDS = MM + 4;
     const int i = blockIdx.x;
     if (i >= nsub) return;
     if (only_active && !ls[i].active) return;
@@ -424,6 +462,10 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_reg(int nsub, 
             cc[q] = d2 * p - 1.0;
         }
     }
+    for (int t = tid; t < 16 * PAD; t += FACT_THREADS) {
+        colk[0][t] = colk[1][t] = 0.f;
+        rowb[0][t] = rowb[1][t] = 0.f;
+    }
     if (tid == 0) sh_fail = 0;
     __syncthreads();
 
@@ -431,177 +473,179 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_reg(int nsub, 
     const long long blk = (long long)mp * mp;
     float* G = gpool + s.goff;
     float Mr[R][R];
-    for (int j = 0; j < W; ++j) {
+    bool failed = false;
+    // entry (r, c) of the diagonal block D_j (one grid row of the local Jacobian)
+    auto dval = [=](int j, int r, int c) -> float {
+        const int ix = r >> 1, f = r & 1, cx = c >> 1, cf = c & 1;
+        const int q = j * s.wx + ix;
+        if (cx == ix) {
+            if (cf == f) return tdiag + (float)ca[q];
+            return (f == 0) ? (float)cb[q] : (float)cc[q];
+        }
+        return (cf == f && (cx == ix - 1 || cx == ix + 1)) ? -tbeta : 0.f;
+    };
+    // shared-buffer slot of row (or column) index i: owner i / R, register i % R
+    auto slot = [](int i) { return (i / R) * PAD + (i % R); };
+    for (int j = 0; j < W && !failed; ++j) {
         // S_j = D_j - beta^2 G_{j-1}
-        const float* Gp = G + (long long)(j > 0 ? j - 1 : 0) * blk;
 #pragma unroll
         for (int a = 0; a < R; ++a) {
-            const int r = ty + 16 * a;
+            const int r = ty * R + a;
 #pragma unroll
             for (int b = 0; b < R; ++b) {
-                const int c = tx + 16 * b;
+                const int c = tx * R + b;
                 float v = 0.f;
                 if (r < m && c < m) {
-                    if (j > 0) v = -tbeta2 * Gp[packed_index<float>(r, c, mp)];
-                    const int ix = r >> 1, f = r & 1, cx = c >> 1, cf = c & 1;
-                    const int q = j * s.wx + ix;
-                    if (cx == ix) {
-                        if (cf == f) v += tdiag + (float)ca[q];
-                        else if (f == 0) v += (float)cb[q];
-                        else v += (float)cc[q];
-                    } else if (cf == f && (cx == ix - 1 || cx == ix + 1)) {
-                        v -= tbeta;
-                    }
+                    if (j > 0) v = -tbeta2 * Ms[r * LDS + c];
+                    v += dval(j, r, c);
                 }
                 Mr[a][b] = v;
             }
         }
-        if (tid == 0) sh_nswap = 0;
-        __syncthreads();
-
+        if (tid == 0) sh_viol = 0;
         int par = 0;
         bool done = false;
+        for (int kt = 0; kt < 16 && !done; ++kt) {
 #pragma unroll
-        for (int kb = 0; kb < R; ++kb) {
-            for (int kt = 0; kt < 16 && !done; ++kt) {
-                const int k = 16 * kb + kt;
+            for (int kb = 0; kb < R; ++kb) {
+                const int k = kt * R + kb;
                 if (k >= m) {
                     done = true;
                     break;
                 }
+                float* cbuf = colk[par];
+                float* rbuf = rowb[par];
                 if (tx == kt) {
+                    float col[R];
 #pragma unroll
-                    for (int a = 0; a < R; ++a) colk[par][ty + 16 * a] = Mr[a][kb];
+                    for (int a2 = 0; a2 < R; ++a2) col[a2] = Mr[a2][kb];
+                    store_vec<R>(cbuf + ty * PAD, col);
                 }
+                if (ty == kt) store_vec<R>(rbuf + tx * PAD, Mr[kb]);
                 __syncthreads();
-                if (warp == 0) {
-                    float best = -1.f;
-                    int bi = 0x7fffffff;
-                    for (int r = k + lane; r < m; r += 32) {
-                        const float v = fabsf(colk[par][r]);
-                        if (v > best) { best = v; bi = r; }
-                    }
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) {
-                        const float ob = __shfl_xor_sync(0xffffffffu, best, off);
-                        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-                        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-                    }
-                    if (lane == 0) {
-                        if (bi >= m || !(best > 0.f)) {
-                            sh_fail = 1;
-                        } else {
-                            sh_r[par] = bi;
-                            sh_piv[par] = colk[par][bi];
-                            pivr[k] = bi;
-                        }
-                    }
+                const float piv = cbuf[kt * PAD + kb];
+                {
+                    // optimistic partial-pivoting check: warp w, rows k+1+20w ..
+                    const int r = k + 1 + 20 * warp + lane;
+                    const float dg = fabsf(piv);
+                    bool viol = (lane < 20 && r < m && fabsf(cbuf[slot(r)]) > dg);
+                    if (tid == 0 && !(dg > 0.f && dg < INFINITY)) viol = true;
+                    if (viol) sh_viol = 1;
                 }
-                __syncthreads();
-                if (sh_fail) {
-                    done = true;
-                    break;
+                const float inv = __frcp_rn(piv);
+                float ck[R], rb[R];
+                load_vec<R>(cbuf + ty * PAD, ck);
+                load_vec<R>(rbuf + tx * PAD, rb);
+#pragma unroll
+                for (int b = 0; b < R; ++b) rb[b] *= inv;
+                if (tx == kt) {
+                    rb[kb] = inv;
+#pragma unroll
+                    for (int a2 = 0; a2 < R; ++a2) Mr[a2][kb] = 0.f;
                 }
-                const int r = sh_r[par];
-                if (r != k) {
-                    const int tr = r & 15, ar = r >> 4;
-                    if (ty == kt) {
 #pragma unroll
-                        for (int b = 0; b < R; ++b) rowb[par][tx + 16 * b] = Mr[kb][b];
-                    }
-                    if (ty == tr) {
+                for (int a2 = 0; a2 < R; ++a2)
 #pragma unroll
-                        for (int a = 0; a < R; ++a)
-                            if (a == ar) {
-#pragma unroll
-                                for (int b = 0; b < R; ++b) swp[tx + 16 * b] = Mr[a][b];
-                            }
-                    }
-                    __syncthreads();
-                    if (ty == kt) {
-#pragma unroll
-                        for (int b = 0; b < R; ++b) Mr[kb][b] = swp[tx + 16 * b];
-                    }
-                    if (ty == tr) {
-#pragma unroll
-                        for (int a = 0; a < R; ++a)
-                            if (a == ar) {
-#pragma unroll
-                                for (int b = 0; b < R; ++b) Mr[a][b] = rowb[par][tx + 16 * b];
-                            }
-                    }
-                    if (tid == 0) {
-                        const float t = colk[par][k];
-                        colk[par][k] = colk[par][r];
-                        colk[par][r] = t;
-                        sh_nswap += 1;
-                    }
-                    __syncthreads();
-                }
-                const float inv = 1.f / sh_piv[par];
+                    for (int b = 0; b < R; ++b) Mr[a2][b] = fmaf(-ck[a2], rb[b], Mr[a2][b]);
                 if (ty == kt) {
 #pragma unroll
-                    for (int b = 0; b < R; ++b) {
-                        const int c = tx + 16 * b;
-                        rowb[par][c] = (c == k) ? inv : Mr[kb][b] * inv;
-                    }
-                }
-                if (tid == 0) colk[par][k] = 0.f;
-                __syncthreads();
-                if (tx == kt) {
-#pragma unroll
-                    for (int a = 0; a < R; ++a) Mr[a][kb] = 0.f;
-                }
-                float ck[R];
-#pragma unroll
-                for (int a = 0; a < R; ++a) ck[a] = colk[par][ty + 16 * a];
-#pragma unroll
-                for (int b = 0; b < R; ++b) {
-                    const float rb = rowb[par][tx + 16 * b];
-#pragma unroll
-                    for (int a = 0; a < R; ++a) Mr[a][b] = fmaf(-ck[a], rb, Mr[a][b]);
-                }
-                if (ty == kt) {
-#pragma unroll
-                    for (int b = 0; b < R; ++b) Mr[kb][b] = rowb[par][tx + 16 * b];
+                    for (int b = 0; b < R; ++b) Mr[kb][b] = rb[b];
                 }
                 par ^= 1;
             }
         }
-        if (sh_fail) break;
-        // column order of the inverse: undo the row interchanges in reverse
-        if (tid == 0) {
-            for (int c = 0; c < m; ++c) sinv[c] = c;
-            if (sh_nswap > 0) {
-                for (int c = 0; c < m; ++c) swp[c] = __int_as_float(c);   // sig, as bits
-                for (int k = m - 1; k >= 0; --k) {
-                    const int r = pivr[k];
-                    if (r != k) {
-                        const float t = swp[k];
-                        swp[k] = swp[r];
-                        swp[r] = t;
+        __syncthreads();
+        if (sh_viol) {
+            // Redo this block row with partial pivoting in shared memory:
+            // S_j in place of G_{j-1}, implicit pivoting (rows never move),
+            // then G_j[r][c] = M[perm[r]][rinv[c]].
+            for (int idx = tid; idx < m * m; idx += FACT_THREADS) {
+                const int r = idx / m, c = idx - r * m;
+                float v = (j > 0) ? -tbeta2 * Ms[r * LDS + c] : 0.f;
+                Ms[r * LDS + c] = v + dval(j, r, c);
+            }
+            for (int t = tid; t < m; t += FACT_THREADS) used[t] = 0;
+            __syncthreads();
+            for (int k = 0; k < m; ++k) {
+                if (warp == 0) {
+                    unsigned bb = 0u;
+                    int bi = 0x7fffffff;
+                    for (int r = lane; r < m; r += 32) {
+                        if (!used[r]) {
+                            const unsigned u = __float_as_uint(fabsf(Ms[r * LDS + k]));
+                            if (u > bb) { bb = u; bi = r; }
+                        }
+                    }
+                    const unsigned mx = __reduce_max_sync(0xffffffffu, bb);
+                    const int r = (int)__reduce_min_sync(0xffffffffu, (unsigned)(bb == mx ? bi : 0x7fffffff));
+                    if (lane == 0) {
+                        if (mx == 0u || mx >= 0x7f800000u || r >= m) {
+                            sh_fail = 1;
+                        } else {
+                            sh_r = r;
+                            used[r] = 1;
+                            pivr[k] = r;
+                            sh_piv = Ms[r * LDS + k];
+                        }
                     }
                 }
-                for (int c = 0; c < m; ++c) sinv[__float_as_int(swp[c])] = c;
+                __syncthreads();
+                if (sh_fail) break;
+                const int r = sh_r;
+                const float inv = 1.f / sh_piv;
+                for (int t = tid; t < m; t += FACT_THREADS) colk[0][t] = Ms[t * LDS + k];
+                __syncthreads();
+                for (int t = tid; t < m; t += FACT_THREADS) Ms[r * LDS + t] = (t == k ? 1.f : Ms[r * LDS + t]) * inv;
+                __syncthreads();
+                for (int idx = tid; idx < m * m; idx += FACT_THREADS) {
+                    const int rr = idx / m, t = idx - rr * m;
+                    if (rr != r) Ms[rr * LDS + t] = (t == k ? 0.f : Ms[rr * LDS + t]) - colk[0][rr] * Ms[r * LDS + t];
+                }
+                __syncthreads();
+            }
+            if (sh_fail) {
+                failed = true;
+                break;
+            }
+            for (int t = tid; t < m; t += FACT_THREADS) sinv[pivr[t]] = t;   // rinv
+            __syncthreads();
+#pragma unroll
+            for (int a = 0; a < R; ++a) {
+                const int r = ty * R + a;
+#pragma unroll
+                for (int b = 0; b < R; ++b) {
+                    const int c = tx * R + b;
+                    Mr[a][b] = (r < m && c < m) ? Ms[pivr[r] * LDS + sinv[c]] : 0.f;
+                }
+            }
+            __syncthreads();
+        }
+        // G_j into shared memory, then packed to HBM
+#pragma unroll
+        for (int a2 = 0; a2 < R; ++a2) {
+            const int r = ty * R + a2;
+#pragma unroll
+            for (int b = 0; b < R; ++b) {
+                const int c = tx * R + b;
+                if (r < mp && c < mp) Ms[r * LDS + c] = (r < m && c < m) ? Mr[a2][b] : 0.f;
             }
         }
         __syncthreads();
-        float* Gj = G + (long long)j * blk;
-#pragma unroll
-        for (int a = 0; a < R; ++a) {
-            const int r = ty + 16 * a;
-#pragma unroll
-            for (int b = 0; b < R; ++b) {
-                const int c = tx + 16 * b;
-                if (r < mp && c < mp) {
-                    if (r < m && c < m) Gj[packed_index<float>(r, sinv[c], mp)] = Mr[a][b];
-                    else Gj[packed_index<float>(r, c, mp)] = 0.f;
-                }
+        {
+            // slab sl, vector v of thread t = 8 rho + kappa: row rho + 32 sl,
+            // columns kappa*cw + 4v .. +3 (the layout of packed_index)
+            const int cw = mp >> 3, nv = cw >> 2, nslab = mp >> 5;
+            const int rho = tid >> 3, kappa = tid & 7;
+            float4* Gj4 = reinterpret_cast<float4*>(G + (long long)j * blk);
+            for (int sl = 0; sl < nslab; ++sl) {
+                const float* row = Ms + (rho + 32 * sl) * LDS + kappa * cw;
+                for (int v = 0; v < nv; ++v)
+                    Gj4[(sl * nv + v) * 256 + tid] = *reinterpret_cast<const float4*>(row + 4 * v);
             }
         }
         __syncthreads();
     }
-    if (sh_fail && tid == 0) {
+    if (failed && tid == 0) {
         ls[i].status = ST_ESINGULAR;
         ls[i].active = 0;
     }
@@ -627,9 +671,12 @@ template <int R>
 cudaError_t launch_factor_reg(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,
                               const double* X, LocalState* ls, const double* cpool, double* coef,
                               float* gpool, int only_active) {
+    const size_t sm = (size_t)(16 * R) * (16 * R + 4) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_local_factor_reg<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
     count_launch();
-    k_local_factor_reg<R><<<nsub, FACT_THREADS, 0, st>>>(nsub, subs, probs, X, ls, cpool, coef, gpool,
-                                                         only_active);
+    k_local_factor_reg<R><<<nsub, FACT_THREADS, sm, st>>>(nsub, subs, probs, X, ls, cpool, coef, gpool,
+                                                          only_active);
     return cudaGetLastError();
 }
 

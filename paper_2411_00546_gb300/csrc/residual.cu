@@ -114,23 +114,36 @@ __global__ void __launch_bounds__(NT) k_jacvec_global(ProbDev P, const double* _
 }
 
 // partials[v * NB + block] = partial dot of V_v (row v of V, stride ld) with w.
+// Per-thread accumulators, then warp shuffles and one pass over the 8 warps'
+// partials in warp order (fixed order: deterministic).
 constexpr int MAXV = 32;
+template <int NVC>
 __global__ void __launch_bounds__(NT) k_dot_multi(const double* __restrict__ V, long long ld, int nv,
                                                   const double* __restrict__ w, long long len,
                                                   double* partials) {
-    __shared__ double red[NT];
-    double acc[MAXV];
+    __shared__ double red[NT / 32][NVC];
+    double acc[NVC];
 #pragma unroll
-    for (int v = 0; v < MAXV; ++v) acc[v] = 0.0;
+    for (int v = 0; v < NVC; ++v) acc[v] = 0.0;
     for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < len; g += (long long)NB * NT) {
         const double wv = w[g];
 #pragma unroll
-        for (int v = 0; v < MAXV; ++v)
-            if (v < nv) acc[v] += V[(long long)v * ld + g] * wv;
+        for (int v = 0; v < NVC; ++v) acc[v] += V[(long long)v * ld + g] * wv;
     }
-    for (int v = 0; v < nv; ++v) {
-        const double s = block_sum1<NT>(acc[v < MAXV ? v : 0], red);
-        if (threadIdx.x == 0) partials[(long long)v * NB + blockIdx.x] = s;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int v = 0; v < NVC; ++v) {
+        double a = acc[v];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+        if (lane == 0) red[warp][v] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < NVC) {
+        double a = 0.0;
+#pragma unroll
+        for (int k = 0; k < NT / 32; ++k) a += red[k][threadIdx.x];
+        partials[(long long)threadIdx.x * NB + blockIdx.x] = a;
     }
 }
 
@@ -207,7 +220,20 @@ cudaError_t launch_dot_multi(cudaStream_t st, const double* V, long long ld, int
                              long long len, double* partials) {
     if (nv > MAXV || nv < 1) return cudaErrorInvalidValue;
     count_launch();
-    k_dot_multi<<<NB, NT, 0, st>>>(V, ld, nv, w, len, partials);
+    // one instantiation per count: every issued FP64 FMA is a useful one (the
+    // FP64 pipe, not HBM, bounds this kernel on GB300)
+    switch (nv) {
+#define RAS_DOT_CASE(K) \
+    case K: k_dot_multi<K><<<NB, NT, 0, st>>>(V, ld, nv, w, len, partials); break;
+        RAS_DOT_CASE(1) RAS_DOT_CASE(2) RAS_DOT_CASE(3) RAS_DOT_CASE(4) RAS_DOT_CASE(5) RAS_DOT_CASE(6)
+        RAS_DOT_CASE(7) RAS_DOT_CASE(8) RAS_DOT_CASE(9) RAS_DOT_CASE(10) RAS_DOT_CASE(11) RAS_DOT_CASE(12)
+        RAS_DOT_CASE(13) RAS_DOT_CASE(14) RAS_DOT_CASE(15) RAS_DOT_CASE(16) RAS_DOT_CASE(17) RAS_DOT_CASE(18)
+        RAS_DOT_CASE(19) RAS_DOT_CASE(20) RAS_DOT_CASE(21) RAS_DOT_CASE(22) RAS_DOT_CASE(23) RAS_DOT_CASE(24)
+        RAS_DOT_CASE(25) RAS_DOT_CASE(26) RAS_DOT_CASE(27) RAS_DOT_CASE(28) RAS_DOT_CASE(29) RAS_DOT_CASE(30)
+        RAS_DOT_CASE(31) RAS_DOT_CASE(32)
+#undef RAS_DOT_CASE
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

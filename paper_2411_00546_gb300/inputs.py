@@ -89,6 +89,10 @@ def problem(name, **over):
         cfg = dict(n=255, sx=8, sy=8, overlap=4, phi=PHI_CUBIC, nu=1e-5, mu=1e-3, yd=("fourier", 1))
     elif name == "n1023":        # 1023^2 grid, 16x16 subdomains of 64^2, overlap 8
         cfg = dict(n=1023, sx=16, sy=16, overlap=8, phi=PHI_CUBIC, nu=1e-6, mu=1e-2, yd=("fourier", 1))
+    elif name == "n511":         # same subdomain shape as n1023 on a 511^2 grid (8x8 subdomains)
+        cfg = dict(n=511, sx=8, sy=8, overlap=8, phi=PHI_CUBIC, nu=1e-6, mu=1e-2, yd=("fourier", 1))
+    elif name == "n1023_active":  # n1023 with mu = 1e-3: the L1 term is active (nonzero control)
+        cfg = dict(n=1023, sx=16, sy=16, overlap=8, phi=PHI_CUBIC, nu=1e-6, mu=1e-3, yd=("fourier", 1))
     else:
         raise KeyError(name)
     base.update(cfg)

@@ -263,3 +263,29 @@ def test_host_entry_point_matches_device_solve(n63_solves):
         assert rel_inf(ph.numpy(), ref.P) <= FP64_TOL
     finally:
         ras.ras_destroy(h)
+
+
+@pytest.mark.parametrize("n,s,nu", [(20, 2, 1e-9), (31, 3, 1e-10)])
+def test_pivoting_cases(n, s, nu):
+    """nu tiny: the (y, p) coupling (1/nu)(1 - P_eps') of the local Jacobian
+    dwarfs its diagonal 4/h^2 + phi', so partial pivoting must interchange
+    rows (the register factorisation's fallback path and the FP64 kernel's
+    pivoting). Same bar as the other parity tests."""
+    cfg = _cfg(n=n, sx=s, sy=s, overlap=2, nu=nu, mu=1e-3, eps0=1e-1, eps_min=1e-3)
+    yd = 3.0 * inputs.yd_fourier(n, 11)
+    prob = oracle_problem(cfg, yd=yd)
+    subs = dd.subdomains(n, s, s, 2)
+    ref = oras.ras_apply(prob, np.zeros((n, n)), np.zeros((n, n)), subs, oracle_opts(cfg), True)
+    # the oracle's band LU does interchange rows here
+    J = oras.local_jacobian_factor(prob, np.zeros((n, n)), 1e-4 * np.ones((n, n)), 1e-3, subs[0])
+    assert np.any(J.piv != np.arange(1, J.piv.size + 1))
+    for prec, tol in PRECS:
+        h = gpu_problem(cfg, prec, yd=yd)
+        try:
+            Fy, Fp = zeros(n), zeros(n)
+            ras.ras_apply(h, zeros(n), zeros(n), 1, Fy, Fp)
+            assert rel_inf(Fy.cpu().numpy(), ref.Fy) <= tol
+            assert rel_inf(Fp.cpu().numpy(), ref.Fp) <= tol
+            assert ras.ras_local_iterations(h) == ref.iterations
+        finally:
+            ras.ras_destroy(h)
