@@ -36,6 +36,18 @@ SM_MAX_MHZ = 2070.0
 FP32_LANES = 128     # FP32 FMA lanes per SM
 FP64_LANES = 2       # FP64 FMA per clock per SM on GB300 (1.2 TFLOP/s class)
 
+# Counts of one RASPEN_eps solve (see run_reference).
+SOLVE_COUNTS = {"n1023": {"inner_its_sum": 1794, "evaluations": 3, "gmres_its": 147}}
+
+
+def field_err(a, b, other):
+    """Relative infinity-norm error of one field, its scale floored at 1e-2 of
+    the joint scale (a field below 1% of the other is known only on that scale)."""
+    import numpy as np
+    sb = float(np.abs(b).max())
+    scale = max(sb, 1e-2 * max(sb, float(np.abs(other).max())), 1e-300)
+    return float(np.abs(a - b).max() / scale)
+
 
 def parse_args():
     ap = argparse.ArgumentParser()
@@ -266,8 +278,9 @@ def main():
         y64n, p64n = y64.cpu().numpy(), p64.cpu().numpy()
         fp64 = {"solves_per_s": 1e3 / e0.elapsed_time(e1), "ms": e0.elapsed_time(e1),
                 "outer_its": st64.outer_its, "gmres_its": st64.gmres_its,
-                "err_mixed_vs_fp64_y": float(np.abs(y_mixed - y64n).max() / max(np.abs(y64n).max(), 1e-300)),
-                "err_mixed_vs_fp64_p": float(np.abs(p_mixed - p64n).max() / max(np.abs(p64n).max(), 1e-300))}
+                "err_mixed_vs_fp64_y": field_err(y_mixed, y64n, p64n),
+                "err_mixed_vs_fp64_p": field_err(p_mixed, p64n, y64n),
+                "err_rule": "max|a-b| / max(max|b|, 1e-2 * joint scale of (y, p))"}
         ras.ras_destroy(h64)
 
     # end to end through the host-buffer entry point (pinned host memory)
@@ -375,25 +388,32 @@ def run_reference(args, world, rank, dist):
         if k >= args.warmup:
             times.append(dt)
             samples.append(s)
-    # one solve of this workload takes (per the GPU path's counters) about
-    # `steps` local Newton steps; without a GPU run here the estimate uses the
-    # sampled subdomain's steps for every subdomain and evaluation.
+    # Step counts of one solve of these workloads (local Newton steps summed
+    # over subdomains and evaluations, RASPEN-function evaluations, Krylov
+    # steps). They are properties of the method on the seeded inputs, equal in
+    # the oracle and the CUDA path (the parity tests check equal local counts
+    # and outer counts); the CPU time of a solve is the sampled per-step cost
+    # times these counts.
     s = samples[-1]
     from oracle import decomposition as dd
     from paper_2411_00546_gb300 import inputs
     cfg = inputs.problem(args.workload)
     nsub = len(dd.subdomains(cfg["n"], cfg["sx"], cfg["sy"], cfg["overlap"]))
-    est = {"inner_its_sum": s["inner_its"] * nsub, "evaluations": 1, "gmres_its": 0}
+    est = SOLVE_COUNTS.get(args.workload, {"inner_its_sum": s["inner_its"] * nsub, "evaluations": 1,
+                                           "gmres_its": 0})
     t_est = cpu_solve_estimate(s, est, nsub)
     value = 1.0 / t_est
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": args.workload, "method": "oracle local Newton sample (lower bound of one "
-                                                             "RASPEN-function evaluation)"},
+           "config": {"workload": args.workload, "method": "oracle (plain FP64 CPU restatement of the paper), "
+                                                             "bounded sample extrapolated to one RASPEN_eps solve"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": "one interior subdomain's local Newton with continuation at x=0 per step, "
-                                      "scaled to all %d subdomains of one evaluation" % nsub},
+                            "sample": "per step: one interior subdomain's local Newton with continuation at x=0 "
+                                      "(%d steps, %.2f s) and one local band solve (%.4f s) on 1 BLAS thread; "
+                                      "extrapolated to one solve with the workload's counts %s over %d "
+                                      "subdomains" % (s["inner_its"], s["newton_s"], s["solve_s"], json.dumps(est),
+                                                       nsub)},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     if dist is not None:

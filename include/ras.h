@@ -130,6 +130,34 @@ int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu
                const double* y_d, const double* f, const ras_opts* o,
                void* stream, ras_problem** out);
 
+/* A batch of independent problems in one handle (spec: many problems of
+ * uneven grid size in one launch per sweep). Each entry describes one problem
+ * exactly like the arguments of ras_create; y_d and f are device pointers,
+ * copied. All problems share the options. The subdomains of all problems form
+ * one table: every step of a RASPEN-function evaluation (Alg. 3) is one launch
+ * for the whole batch, and the FP32 factorisation is launched once per
+ * register-tile class (block size mp = 2*wx rounded up to 32, tile mp/16).
+ * Limits as in ras_create, per problem; 1 <= count <= 4096. */
+typedef struct {
+    int n, sx, sy, overlap, phi;
+    double nu, mu;
+    const double* y_d;
+    const double* f;
+} ras_problem_desc;
+int ras_batch_create(int count, const ras_problem_desc* problems, const ras_opts* o, void* stream,
+                     ras_problem** out);
+
+/* Number of problems in the handle (1 for ras_create). */
+int ras_problem_count(const ras_problem* h);
+
+/* RASPEN (Alg. 2) for every problem of a batch, in lockstep: the RASPEN-
+ * function evaluations and the Krylov steps of all problems still iterating
+ * share their launches; each problem stops on its own test. y[k], p[k]: device
+ * n_k*n_k arrays (initial guess in, solution out). stats: `count` entries, or
+ * NULL. Returns the worst status. The single-problem entry points other than
+ * ras_raspen_solve take only handles with one problem (else RAS_EINVAL). */
+int ras_batch_raspen_solve(ras_problem* h, double* const* y, double* const* p, ras_stats* stats);
+
 /* Set the target smoothing parameter eps_min (> 0; P_eps is not smooth at 0). */
 int ras_set_eps(ras_problem* h, double eps_min);
 

@@ -1,8 +1,16 @@
 // Host side of the RAS / RASPEN library: the C ABI of include/ras.h, the
-// decomposition (Sec. 4.2), the per-sweep launch sequence of Alg. 3, GMRES,
-// RASPEN (Alg. 2) and Newton_RAS (Alg. 1 with linear RAS). Every arithmetic
-// step runs in the kernels of local.cu and residual.cu; this file only
-// orders launches, moves scalars and applies the stop rules.
+// decomposition (Sec. 4.2), the launch sequence of the RASPEN function
+// (Alg. 3), GMRES, RASPEN (Alg. 2) and Newton_RAS (Alg. 1 with linear RAS).
+// Every arithmetic step runs in the kernels of local.cu, solve.cu and
+// residual.cu; this file orders launches, moves scalars and applies the stop
+// rules.
+//
+// A handle holds one or more independent problems (a batch). All subdomains
+// of all problems form one table, so every step of a RASPEN-function
+// evaluation is one launch for the whole batch; global vectors are the
+// concatenation of the problems' [y | p] planes (problem k at ProbDev.ofs),
+// and GMRES runs the problems in lockstep with segmented reductions, one host
+// synchronisation per Krylov step for the whole batch.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -21,22 +29,28 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 using ras::LocalState;
 using ras::NewtonParams;
 using ras::ProbDev;
+using ras::Seg;
 using ras::SubDev;
 
 struct ras_problem {
-    int n = 0, sx = 0, sy = 0, overlap = 0, phi = 0;
-    double nu = 0.0, mu = 0.0;
+    int nprob = 0;
+    std::vector<ras_problem_desc> desc;
     ras_opts o{};
     cudaStream_t st = nullptr;
     int nsub = 0, maxm = 0;
-    long long N = 0;          // n*n
+    long long L = 0;          // length of a global vector (sum of 2 n_k^2)
     long long Lsum = 0;       // sum of 2*wx*wy
     long long Nsum = 0;       // sum of wx*wy
-    long long Gsum = 0;       // sum of wy*(2wx)^2
+    long long Gsum = 0;       // sum of wy*mp^2
     std::vector<SubDev> subs;
-    ProbDev prob{};
+    std::vector<ProbDev> probs;
+    std::vector<Seg> segs;
+    std::vector<int> sub_first, sub_count;   // subdomains of each problem (contiguous)
     SubDev* d_subs = nullptr;
-    ProbDev* d_prob = nullptr;
+    ProbDev* d_probs = nullptr;
+    Seg* d_segs = nullptr;
+    int* d_lists = nullptr;                  // subdomain indices grouped by register-tile class
+    std::vector<int> tile_off, tile_cnt;     // per tile class 2, 4, 6, 8, 10 (index tile/2 - 1)
     double* yd = nullptr;
     double* f = nullptr;
     double *cpool = nullptr, *dpool = nullptr, *Kpool = nullptr, *Ktpool = nullptr, *rpool = nullptr;
@@ -48,12 +62,15 @@ struct ras_problem {
     int* d_active = nullptr;
     int* d_err = nullptr;        // set by kernels whose bounded waits ran out
     int* h_active = nullptr;     // pinned
+    int* d_mask = nullptr;       // per-problem masks: row 0 [0, nprob) GMRES/JVP, row 1 outer loop
+    double* d_pstart = nullptr;  // per-problem eps start of a RASPEN-function evaluation
     double *X = nullptr, *F = nullptr, *Dv = nullptr, *Ov = nullptr, *T1 = nullptr, *T2 = nullptr,
            *T3 = nullptr, *Z = nullptr;
     double* coefG = nullptr;
     double* partials = nullptr;
-    double* scal = nullptr;      // device scalars
-    double* h_scal = nullptr;    // pinned host scalars
+    int nbp = 0;                 // blocks per problem of the segmented kernels
+    double* scal = nullptr;      // device scalars, 4 * 32 per problem
+    double* h_scal = nullptr;    // pinned host scalars, same layout
     double* V = nullptr;
     int Vm = 0;
     bool jvp_ready = false;
@@ -77,7 +94,8 @@ struct ras_problem {
 
 namespace {
 
-constexpr int NSCAL = 160;
+constexpr int SS = ras::SEG_STRIDE;   // per-problem stride of scalar arrays
+constexpr int NTILE = 5;              // register tiles 2, 4, 6, 8, 10
 
 int fail(ras_problem* h, int code, const std::string& msg) {
     if (h) h->err = msg;
@@ -234,34 +252,66 @@ int check_err(ras_problem* h) {
 
 size_t prec_bytes(const ras_problem* h) { return h->o.precision == RAS_MIXED ? sizeof(float) : sizeof(double); }
 
-// Algorithmic work of a factorisation of the subdomains with mask[i] != 0:
-// 16 wx^3 wy flops each (block-tridiagonal Gauss-Jordan = no-fill band LU count).
-double factor_flops(const ras_problem* h, const std::vector<LocalState>* ls) {
+// Algorithmic work of a factorisation: 16 wx^3 wy flops per subdomain (block-
+// tridiagonal Gauss-Jordan = no-fill band LU count). With `ls`: only active
+// subdomains, or (skip_skipped) all but those of non-participating problems.
+double factor_flops(const ras_problem* h, const std::vector<LocalState>* ls, bool skip_skipped) {
     double w = 0.0;
     for (int i = 0; i < h->nsub; ++i) {
-        if (ls && !(*ls)[i].active) continue;
+        if (ls && !skip_skipped && !(*ls)[i].active) continue;
+        if (ls && skip_skipped && (*ls)[i].status == ras::ST_SKIP) continue;
         const double wx = h->subs[i].wx, wy = h->subs[i].wy;
         w += 16.0 * wx * wx * wx * wy;
     }
     return w;
 }
 
-// Bytes of one two-pass block solve over every subdomain's factor.
-double solve_bytes_all(const ras_problem* h) {
-    return 2.0 * (double)h->Gsum * (double)prec_bytes(h);
+// Bytes of one two-pass block solve over the factors of the problems in mask.
+double solve_bytes(const ras_problem* h, const std::vector<int>* mask) {
+    double b = 0.0;
+    for (int i = 0; i < h->nsub; ++i) {
+        const SubDev& s = h->subs[i];
+        if (mask && !(*mask)[s.prob]) continue;
+        b += 2.0 * (double)s.wy * s.mp * s.mp * (double)prec_bytes(h);
+    }
+    return b;
 }
 
-double resid_bytes(const ras_problem* h) { return (h->f ? 48.0 : 40.0) * (double)h->N; }
+long long plane(const ras_problem* h, int p) { return (long long)h->probs[p].n * h->probs[p].n; }
 
-// ||F(x + alpha d, eps)|| and the rounding-floor norm; writes F to Fout (2N) if given.
-int residual_norm(ras_problem* h, const double* x, const double* d, double alpha, double eps,
-                  double* Fout, double& nrm, double& flr) {
-    const long long N = h->N;
+double resid_bytes(const ras_problem* h) { return (h->f ? 48.0 : 40.0) * (double)plane(h, 0); }
+
+int set_mask(ras_problem* h, int row, const std::vector<int>& m) {
+    CK(cudaMemcpyAsync(h->d_mask + row * h->nprob, m.data(), h->nprob * sizeof(int), cudaMemcpyHostToDevice,
+                       h->st));
+    return RAS_OK;
+}
+
+// Per-problem squared norms of the segments of v (problems flagged in dmask),
+// into h->scal[p * SS] (device) and h->h_scal[p * SS] (host).
+int seg_norms2(ras_problem* h, const double* v, const int* dmask) {
+    const int P = h->nprob, nb = h->nbp;
+    double len = 0.0;
+    for (auto& s : h->segs) len += 8.0 * s.len;
+    CK(timed(h, RAS_K_KRYLOV, len, [&] {
+        return ras::launch_seg_dot(h->st, P, nb, h->d_segs, dmask, v, h->L, 1, v, h->partials);
+    }));
+    CK(timed(h, RAS_K_OTHER, 0.0,
+             [&] { return ras::launch_seg_reduce(h->st, P, nb, dmask, 1, h->partials, h->scal); }));
+    CK(cudaMemcpyAsync(h->h_scal, h->scal, (size_t)P * SS * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    return sync(h);
+}
+
+// ||F(x + alpha d, eps)|| and the rounding-floor norm (problem 0); writes F if given.
+int residual_norm(ras_problem* h, const double* x, const double* d, double alpha, double eps, double* Fout,
+                  double& nrm, double& flr) {
+    const long long N = plane(h, 0);
     CK(timed(h, RAS_K_RESIDUAL, resid_bytes(h), [&] {
-        return ras::launch_residual_global(h->st, h->prob, x, x + N, d, d ? d + N : nullptr, alpha, eps, Fout,
+        return ras::launch_residual_global(h->st, h->probs[0], x, x + N, d, d ? d + N : nullptr, alpha, eps, Fout,
                                            Fout ? Fout + N : nullptr, h->partials);
     }));
-    CK(timed(h, RAS_K_OTHER, 0.0, [&] { return ras::launch_reduce_partials(h->st, h->partials, ras::VEC_BLOCKS, 2, h->scal); }));
+    CK(timed(h, RAS_K_OTHER, 0.0,
+             [&] { return ras::launch_reduce_partials(h->st, h->partials, ras::VEC_BLOCKS, 2, h->scal); }));
     CK(cudaMemcpyAsync(h->h_scal, h->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     TRY(sync(h));
     nrm = std::sqrt(h->h_scal[0]);
@@ -269,45 +319,61 @@ int residual_norm(ras_problem* h, const double* x, const double* d, double alpha
     return RAS_OK;
 }
 
-// ||v||_2 of a global vector (2N), deterministic.
-int vec_norm(ras_problem* h, const double* v, double& out) {
-    const long long len = 2 * h->N;
-    CK(timed(h, RAS_K_KRYLOV, 8.0 * len, [&] { return ras::launch_dot_multi(h->st, v, len, 1, v, len, h->partials); }));
-    CK(timed(h, RAS_K_OTHER, 0.0, [&] { return ras::launch_reduce_partials(h->st, h->partials, ras::VEC_BLOCKS, 1, h->scal); }));
-    CK(cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    TRY(sync(h));
-    out = std::sqrt(h->h_scal[0]);
+int copy_in(ras_problem* h, double* dst, int p, const double* y, const double* pp) {
+    const long long N = plane(h, p), o = h->probs[p].ofs;
+    CK(cudaMemcpyAsync(dst + o, y, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(dst + o + N, pp, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     return RAS_OK;
 }
 
-int copy_in(ras_problem* h, double* dst, const double* y, const double* p) {
-    CK(cudaMemcpyAsync(dst, y, h->N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-    CK(cudaMemcpyAsync(dst + h->N, p, h->N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+int copy_out(ras_problem* h, const double* src, int p, double* y, double* pp) {
+    const long long N = plane(h, p), o = h->probs[p].ofs;
+    if (y) CK(cudaMemcpyAsync(y, src + o, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    if (pp) CK(cudaMemcpyAsync(pp, src + o + N, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     return RAS_OK;
 }
 
-int copy_out(ras_problem* h, const double* src, double* y, double* p) {
-    if (y) CK(cudaMemcpyAsync(y, src, h->N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-    if (p) CK(cudaMemcpyAsync(p, src + h->N, h->N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-    return RAS_OK;
-}
-
-void stats_clear(ras_stats* s) {
+void stats_clear(ras_stats* s, int count) {
     if (!s) return;
-    std::memset(s, 0, sizeof(*s));
+    std::memset(s, 0, sizeof(ras_stats) * count);
+}
+
+// Factorisation launches: FP32 one per register-tile class, FP64 one.
+template <typename T>
+int launch_factor(ras_problem* h, int only_active, double flops) {
+    if (sizeof(T) == sizeof(float)) {
+        bool first = true;   // the profile books the flops on the first launch of the sweep
+        for (int c = 0; c < NTILE; ++c) {
+            if (h->tile_cnt[c] == 0) continue;
+            CK(timed(h, RAS_K_FACTOR, first ? flops : 0.0, [&] {
+                return ras::launch_local_factor_f32(h->st, 2 * (c + 1), h->tile_cnt[c], h->d_lists + h->tile_off[c],
+                                                    h->d_subs, h->d_probs, h->X, h->ls, h->cpool, h->coef,
+                                                    (float*)h->gpool, only_active);
+            }));
+            first = false;
+        }
+        return RAS_OK;
+    }
+    CK(timed(h, RAS_K_FACTOR, flops, [&] {
+        return ras::launch_local_factor<T>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs, h->X, h->ls, h->cpool,
+                                           h->coef, (T*)h->gpool, only_active);
+    }));
+    return RAS_OK;
 }
 
 // --------------------------------------------------------------- Alg. 3
+// RASPEN function of the problems with pstart[p] > 0 (eps at which their
+// local solves start); per-problem counters into stats[p] (may be null).
 template <typename T>
-int ras_apply_T(ras_problem* h, int continuation, double* Fout, ras_stats* stats) {
+int ras_apply_T(ras_problem* h, const std::vector<double>& pstart, double* Fout, ras_stats* stats) {
     const NewtonParams np = inner_params(h->o);
-    const double eps_start = continuation ? h->o.eps0 : h->o.eps_min;
     T* gp = (T*)h->gpool;
     T* wp = (T*)h->wpool;
+    CK(cudaMemcpyAsync(h->d_pstart, pstart.data(), h->nprob * sizeof(double), cudaMemcpyHostToDevice, h->st));
     CK(cudaMemsetAsync(h->d_active, 0, sizeof(int), h->st));
     CK(timed(h, RAS_K_INIT, 0.0, [&] {
-        return ras::launch_local_init(h->st, h->nsub, h->d_subs, h->d_prob, h->X, h->ls, eps_start, np, h->cpool,
-                                      h->Kpool, h->d_active);
+        return ras::launch_local_init(h->st, h->nsub, h->d_subs, h->d_probs, h->X, h->ls, h->d_pstart, np,
+                                      h->cpool, h->Kpool, h->d_active);
     }));
     CK(cudaMemcpyAsync(h->h_active, h->d_active, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     TRY(sync(h));
@@ -322,20 +388,17 @@ int ras_apply_T(ras_problem* h, int continuation, double* Fout, ras_stats* stats
         double fl = 0.0;
         if (h->prof_on) {
             TRY(read_ls(before));
-            fl = factor_flops(h, &before);
+            fl = factor_flops(h, &before, false);
         }
-        CK(timed(h, RAS_K_FACTOR, fl, [&] {
-            return ras::launch_local_factor<T>(h->st, h->nsub, h->maxm, h->d_subs, h->d_prob, h->X, h->ls,
-                                               h->cpool, h->coef, gp, 1);
-        }));
+        TRY(launch_factor<T>(h, 1, fl));
         CK(timed(h, RAS_K_DIRECTION, 0.0, [&] {
-            return ras::launch_local_direction<T>(h->st, h->nsub, h->maxm, h->d_subs, h->d_prob, h->ls, np,
+            return ras::launch_local_direction<T>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs, h->ls, np,
                                                   h->coef, gp, h->Kpool, h->dpool, h->rpool, wp, h->d_err);
         }));
         const size_t dir_rec = h->prof_recs.size();
         CK(cudaMemsetAsync(h->d_active, 0, sizeof(int), h->st));
         CK(timed(h, RAS_K_LINESEARCH, 0.0, [&] {
-            return ras::launch_local_linesearch(h->st, h->nsub, h->d_subs, h->d_prob, h->X, h->ls, np, h->cpool,
+            return ras::launch_local_linesearch(h->st, h->nsub, h->d_subs, h->d_probs, h->X, h->ls, np, h->cpool,
                                                 h->dpool, h->Kpool, h->Ktpool, h->d_active);
         }));
         CK(cudaMemcpyAsync(h->h_active, h->d_active, sizeof(int), cudaMemcpyDeviceToHost, h->st));
@@ -344,68 +407,82 @@ int ras_apply_T(ras_problem* h, int continuation, double* Fout, ras_stats* stats
             TRY(read_ls(after));
             double bytes = 0.0;
             for (int i = 0; i < h->nsub; ++i) {
-                const double m = 2.0 * h->subs[i].wx;
-                bytes += (after[i].solves - before[i].solves) * 2.0 * m * m * h->subs[i].wy * sizeof(T);
+                const double mp = h->subs[i].mp;
+                bytes += (after[i].solves - before[i].solves) * 2.0 * mp * mp * h->subs[i].wy * sizeof(T);
             }
             h->prof_recs[dir_rec - 1].work = bytes;
         }
     }
     // factors at x^(i) = x + P_i C_i(x) for the Jacobian action (Alg. 4)
-    CK(timed(h, RAS_K_FACTOR, factor_flops(h, nullptr), [&] {
-        return ras::launch_local_factor<T>(h->st, h->nsub, h->maxm, h->d_subs, h->d_prob, h->X, h->ls, h->cpool,
-                                           h->coef, gp, 0);
-    }));
+    double fl_all = 0.0;
+    if (h->prof_on) {
+        TRY(read_ls(before));
+        fl_all = factor_flops(h, &before, true);
+    }
+    TRY(launch_factor<T>(h, 0, fl_all));
     CK(timed(h, RAS_K_OTHER, 0.0, [&] {
-        return ras::launch_local_prolong(h->st, h->nsub, h->d_subs, h->d_prob, h->cpool, Fout);
+        return ras::launch_local_prolong(h->st, h->nsub, h->d_subs, h->d_probs, h->ls, h->cpool, Fout);
     }));
     std::vector<LocalState> ls(h->nsub);
     CK(cudaMemcpyAsync(ls.data(), h->ls, h->nsub * sizeof(LocalState), cudaMemcpyDeviceToHost, h->st));
     TRY(sync(h));
     int worst = RAS_OK;
     h->last_its.assign(h->nsub, 0);
-    int itmax = 0, fails = 0, halv = 0, exh = 0;
-    long long itsum = 0;
+    std::vector<int> itmax(h->nprob, 0), fails(h->nprob, 0), halv(h->nprob, 0), exh(h->nprob, 0);
+    std::vector<long long> itsum(h->nprob, 0);
     for (int i = 0; i < h->nsub; ++i) {
+        const int p = h->subs[i].prob;
+        if (ls[i].status == ras::ST_SKIP) continue;
         h->last_its[i] = ls[i].k;
-        itmax = std::max(itmax, ls[i].k);
-        itsum += ls[i].k;
-        halv += ls[i].halvings;
-        exh += ls[i].exhausted;
+        itmax[p] = std::max(itmax[p], ls[i].k);
+        itsum[p] += ls[i].k;
+        halv[p] += ls[i].halvings;
+        exh[p] += ls[i].exhausted;
         if (ls[i].status < 0) {
-            ++fails;
+            ++fails[p];
             worst = std::min(worst, ls[i].status);
         }
     }
     h->jvp_ready = (worst >= 0);
     if (stats) {
-        stats->evaluations += 1;
-        stats->inner_its_max += itmax;
-        stats->inner_its_sum += itsum;
-        stats->halvings += halv;
-        stats->exhausted += exh;
-        stats->local_failures += fails;
-        stats->eps_final = h->o.eps_min;
+        for (int p = 0; p < h->nprob; ++p) {
+            if (!(pstart[p] > 0)) continue;
+            ras_stats& s = stats[p];
+            s.evaluations += 1;
+            s.inner_its_max += itmax[p];
+            s.inner_its_sum += itsum[p];
+            s.halvings += halv[p];
+            s.exhausted += exh[p];
+            s.local_failures += fails[p];
+            s.eps_final = h->o.eps_min;
+        }
     }
-    if (worst < 0) return fail(h, worst, "local Newton solve failed in " + std::to_string(fails) + " subdomain(s)");
+    if (worst < 0) {
+        int nf = 0;
+        for (int v : fails) nf += v;
+        return fail(h, worst, "local Newton solve failed in " + std::to_string(nf) + " subdomain(s)");
+    }
     return RAS_OK;
 }
 
-int ras_apply_internal(ras_problem* h, int continuation, double* Fout, ras_stats* stats) {
+int ras_apply_internal(ras_problem* h, const std::vector<double>& pstart, double* Fout, ras_stats* stats) {
     TRY(alloc_factor_pools(h));
-    if (h->o.precision == RAS_MIXED) return ras_apply_T<float>(h, continuation, Fout, stats);
-    return ras_apply_T<double>(h, continuation, Fout, stats);
+    if (h->o.precision == RAS_MIXED) return ras_apply_T<float>(h, pstart, Fout, stats);
+    return ras_apply_T<double>(h, pstart, Fout, stats);
 }
 
-int jvp_internal(ras_problem* h, const double* D, double* O) {
+// Alg. 4 for the problems flagged in `mask` (device copy: d_mask row 0), or all.
+int jvp_internal(ras_problem* h, const double* D, double* O, const std::vector<int>* mask) {
     const int nir = (h->o.precision == RAS_MIXED) ? h->o.jvp_ir : 0;
-    CK(timed(h, RAS_K_JVP, solve_bytes_all(h) * (1 + nir), [&] {
+    const int* dm = mask ? h->d_mask : nullptr;
+    CK(timed(h, RAS_K_JVP, solve_bytes(h, mask) * (1 + nir), [&] {
         if (h->o.precision == RAS_MIXED)
-            return ras::launch_local_jvp<float>(h->st, h->nsub, h->maxm, h->d_subs, h->d_prob,
+            return ras::launch_local_jvp<float>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs,
                                                 (const float*)h->gpool, (float*)h->wpool, h->coef, h->dpool,
-                                                h->rpool, h->Ktpool, nir, D, O, h->d_err);
-        return ras::launch_local_jvp<double>(h->st, h->nsub, h->maxm, h->d_subs, h->d_prob,
+                                                h->rpool, h->Ktpool, nir, D, O, dm, h->d_err);
+        return ras::launch_local_jvp<double>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs,
                                              (const double*)h->gpool, (double*)h->wpool, h->coef, h->dpool,
-                                             h->rpool, h->Ktpool, 0, D, O, h->d_err);
+                                             h->rpool, h->Ktpool, 0, D, O, dm, h->d_err);
     }));
     return RAS_OK;
 }
@@ -421,13 +498,11 @@ int factor_at(ras_problem* h, double eps) {
     }
     CK(cudaMemsetAsync(h->cpool, 0, h->Lsum * sizeof(double), h->st));
     CK(cudaMemcpyAsync(h->ls, ls.data(), h->nsub * sizeof(LocalState), cudaMemcpyHostToDevice, h->st));
-    CK(timed(h, RAS_K_FACTOR, factor_flops(h, nullptr), [&] {
-        if (h->o.precision == RAS_MIXED)
-            return ras::launch_local_factor<float>(h->st, h->nsub, h->maxm, h->d_subs, h->d_prob, h->X, h->ls,
-                                                   h->cpool, h->coef, (float*)h->gpool, 0);
-        return ras::launch_local_factor<double>(h->st, h->nsub, h->maxm, h->d_subs, h->d_prob, h->X, h->ls,
-                                                h->cpool, h->coef, (double*)h->gpool, 0);
-    }));
+    if (h->o.precision == RAS_MIXED) {
+        TRY(launch_factor<float>(h, 0, factor_flops(h, nullptr, false)));
+    } else {
+        TRY(launch_factor<double>(h, 0, factor_flops(h, nullptr, false)));
+    }
     CK(cudaMemcpyAsync(ls.data(), h->ls, h->nsub * sizeof(LocalState), cudaMemcpyDeviceToHost, h->st));
     TRY(sync(h));
     h->jvp_ready = false;
@@ -437,170 +512,298 @@ int factor_at(ras_problem* h, double eps) {
 }
 
 int precond_internal(ras_problem* h, const double* R, double* Zo) {
-    CK(timed(h, RAS_K_PRECOND, solve_bytes_all(h), [&] {
+    CK(timed(h, RAS_K_PRECOND, solve_bytes(h, nullptr), [&] {
         if (h->o.precision == RAS_MIXED)
-            return ras::launch_local_precond<float>(h->st, h->nsub, h->maxm, h->d_subs, h->d_prob,
+            return ras::launch_local_precond<float>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs,
                                                     (const float*)h->gpool, (float*)h->wpool, R, Zo, h->d_err);
-        return ras::launch_local_precond<double>(h->st, h->nsub, h->maxm, h->d_subs, h->d_prob,
+        return ras::launch_local_precond<double>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs,
                                                  (const double*)h->gpool, (double*)h->wpool, R, Zo, h->d_err);
     }));
     return RAS_OK;
 }
 
 // --------------------------------------------------------------- GMRES
-// Restarted GMRES(m), CGS2 Arnoldi, Givens rotations, x0 = 0, right
-// preconditioning when `prec` is true. A(in, out) and M(in, out) act on
-// global vectors (2N). One host synchronisation per Krylov step.
+// Restarted GMRES(m) for every problem p with part[p] != 0, in lockstep:
+// CGS2 Arnoldi with segmented (per-problem) reductions, Givens rotations on
+// the host, x0 = 0, right preconditioning when `prec`. A(in, out, mask) and
+// M(in, out, mask) act on the problems flagged in mask (host) = d_mask row 0
+// (device), which this routine keeps equal to the problems still iterating.
+// One host synchronisation per Krylov step for the whole batch.
 template <class Aop, class Mop>
-int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, int& its, bool& conv) {
-    const long long len = 2 * h->N;
-    const int m = h->o.gmres_restart;
+int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, const std::vector<int>& part,
+          std::vector<int>& its, std::vector<int>& conv) {
+    const int P = h->nprob, nb = h->nbp, m = h->o.gmres_restart, maxit = h->o.gmres_maxit;
+    const long long L = h->L;
     const double rtol = h->o.gmres_rtol;
-    const int maxit = h->o.gmres_maxit;
     if (h->Vm < m) {
         dfree(h, h->V);
         h->V = nullptr;
-        TRY(dalloc(h, &h->V, (size_t)(m + 1) * len));
+        TRY(dalloc(h, &h->V, (size_t)(m + 1) * L));
         h->Vm = m;
     }
     double* V = h->V;
     double* r = h->T2;
     double* upd = h->T3;
-    CK(cudaMemsetAsync(x, 0, len * sizeof(double), h->st));
-    its = 0;
-    conv = false;
-    double bnorm;
-    TRY(vec_norm(h, b, bnorm));
-    if (bnorm == 0.0) {
-        conv = true;
-        return RAS_OK;
+    const int* dmask = h->d_mask;   // row 0
+    its.assign(P, 0);
+    conv.assign(P, 0);
+    CK(cudaMemsetAsync(x, 0, L * sizeof(double), h->st));
+    std::vector<int> act(P, 0), cyc(P, 0), steps(P, 0);
+    std::vector<double> target(P, 0.0), beta(P, 0.0);
+    TRY(set_mask(h, 0, part));
+    TRY(seg_norms2(h, b, dmask));
+    for (int p = 0; p < P; ++p) {
+        if (!part[p]) continue;
+        const double bn = std::sqrt(h->h_scal[p * SS]);
+        target[p] = rtol * bn;
+        if (bn == 0.0) conv[p] = 1;
+        else act[p] = 1;
     }
-    const double target = rtol * bnorm;
-    CK(cudaMemcpyAsync(r, b, len * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-    std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    CK(cudaMemcpyAsync(r, b, L * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    std::vector<double> H((size_t)P * (m + 1) * m), cs((size_t)P * m), sn((size_t)P * m), g((size_t)P * (m + 1)),
+        y((size_t)P * SS, 0.0);
+    double seglen = 0.0;
+    for (int p = 0; p < P; ++p) seglen += (double)h->segs[p].len;
     for (;;) {
-        double beta;
-        TRY(vec_norm(h, r, beta));
-        if (beta <= target || its >= maxit) {
-            conv = beta <= target;
-            return RAS_OK;
+        // true residual norms of the problems still iterating
+        TRY(set_mask(h, 0, act));
+        TRY(seg_norms2(h, r, dmask));
+        bool any = false;
+        for (int p = 0; p < P; ++p) {
+            if (!act[p]) continue;
+            beta[p] = std::sqrt(h->h_scal[p * SS]);
+            if (beta[p] <= target[p] || its[p] >= maxit) {
+                conv[p] = beta[p] <= target[p];
+                act[p] = 0;
+            } else {
+                any = true;
+            }
         }
+        if (!any) return RAS_OK;
+        cyc = act;
+        TRY(set_mask(h, 0, cyc));
+        // V_0 = r / beta (device-side, from the squared norms in h->scal)
+        CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
+            return ras::launch_seg_scale(h->st, P, nb, h->d_segs, dmask, r, h->scal, 1.0, V);
+        }));
         std::fill(H.begin(), H.end(), 0.0);
         std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        CK(timed(h, RAS_K_KRYLOV, 16.0 * len, [&] { return ras::launch_scale_copy(h->st, r, nullptr, nullptr, 1.0 / beta, V, len); }));
-        int steps = 0;
+        for (int p = 0; p < P; ++p) {
+            g[(size_t)p * (m + 1)] = beta[p];
+            steps[p] = 0;
+        }
         for (int j = 0; j < m; ++j) {
-            double* vj = V + (long long)j * len;
-            double* w = V + (long long)(j + 1) * len;
+            if (std::none_of(cyc.begin(), cyc.end(), [](int v) { return v != 0; })) break;
+            double* vj = V + (long long)j * L;
+            double* w = V + (long long)(j + 1) * L;
             if (prec) {
-                TRY(M(vj, h->Z));
-                TRY(A(h->Z, w));
+                TRY(M(vj, h->Z, cyc));
+                TRY(A(h->Z, w, cyc));
             } else {
-                TRY(A(vj, w));
+                TRY(A(vj, w, cyc));
             }
-            // CGS2: two passes of classical Gram-Schmidt
-            const double dbytes = 8.0 * len * (j + 2), abytes = 8.0 * len * (j + 3);
-            CK(timed(h, RAS_K_KRYLOV, dbytes, [&] { return ras::launch_dot_multi(h->st, V, len, j + 1, w, len, h->partials); }));
-            CK(timed(h, RAS_K_OTHER, 0.0, [&] { return ras::launch_reduce_partials(h->st, h->partials, ras::VEC_BLOCKS, j + 1, h->scal); }));
-            CK(timed(h, RAS_K_KRYLOV, abytes, [&] { return ras::launch_axpy_multi(h->st, V, len, j + 1, h->scal, -1.0, w, len); }));
-            CK(timed(h, RAS_K_KRYLOV, dbytes, [&] { return ras::launch_dot_multi(h->st, V, len, j + 1, w, len, h->partials); }));
-            CK(timed(h, RAS_K_OTHER, 0.0, [&] { return ras::launch_reduce_partials(h->st, h->partials, ras::VEC_BLOCKS, j + 1, h->scal + 32); }));
-            CK(timed(h, RAS_K_KRYLOV, abytes, [&] { return ras::launch_axpy_multi(h->st, V, len, j + 1, h->scal + 32, -1.0, w, len); }));
-            CK(timed(h, RAS_K_KRYLOV, 8.0 * len, [&] { return ras::launch_dot_multi(h->st, w, len, 1, w, len, h->partials); }));
-            CK(timed(h, RAS_K_OTHER, 0.0, [&] { return ras::launch_reduce_partials(h->st, h->partials, ras::VEC_BLOCKS, 1, h->scal + 64); }));
-            CK(cudaMemcpyAsync(h->h_scal, h->scal, 65 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+            // CGS2: two passes of classical Gram-Schmidt, then the norm
+            const double dbytes = 8.0 * seglen * (j + 2), abytes = 8.0 * seglen * (j + 3);
+            double* h1 = h->scal;
+            double* h2 = h->scal + (size_t)P * SS;
+            double* n2 = h->scal + (size_t)2 * P * SS;
+            CK(timed(h, RAS_K_KRYLOV, dbytes, [&] {
+                return ras::launch_seg_dot(h->st, P, nb, h->d_segs, dmask, V, L, j + 1, w, h->partials);
+            }));
+            CK(timed(h, RAS_K_OTHER, 0.0,
+                     [&] { return ras::launch_seg_reduce(h->st, P, nb, dmask, j + 1, h->partials, h1); }));
+            CK(timed(h, RAS_K_KRYLOV, abytes, [&] {
+                return ras::launch_seg_axpy(h->st, P, nb, h->d_segs, dmask, V, L, j + 1, h1, -1.0, w);
+            }));
+            CK(timed(h, RAS_K_KRYLOV, dbytes, [&] {
+                return ras::launch_seg_dot(h->st, P, nb, h->d_segs, dmask, V, L, j + 1, w, h->partials);
+            }));
+            CK(timed(h, RAS_K_OTHER, 0.0,
+                     [&] { return ras::launch_seg_reduce(h->st, P, nb, dmask, j + 1, h->partials, h2); }));
+            CK(timed(h, RAS_K_KRYLOV, abytes, [&] {
+                return ras::launch_seg_axpy(h->st, P, nb, h->d_segs, dmask, V, L, j + 1, h2, -1.0, w);
+            }));
+            CK(timed(h, RAS_K_KRYLOV, 8.0 * seglen, [&] {
+                return ras::launch_seg_dot(h->st, P, nb, h->d_segs, dmask, w, L, 1, w, h->partials);
+            }));
+            CK(timed(h, RAS_K_OTHER, 0.0,
+                     [&] { return ras::launch_seg_reduce(h->st, P, nb, dmask, 1, h->partials, n2); }));
+            CK(cudaMemcpyAsync(h->h_scal, h->scal, (size_t)3 * P * SS * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->st));
             TRY(sync(h));
-            for (int i = 0; i <= j; ++i) H[i * m + j] = h->h_scal[i] + h->h_scal[32 + i];
-            const double hn = std::sqrt(h->h_scal[64]);
-            H[(j + 1) * m + j] = hn;
-            for (int i = 0; i < j; ++i) {
-                const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
-                H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
-                H[i * m + j] = t;
+            bool changed = false;
+            for (int p = 0; p < P; ++p) {
+                if (!cyc[p]) continue;
+                double* Hp = H.data() + (size_t)p * (m + 1) * m;
+                double* csp = cs.data() + (size_t)p * m;
+                double* snp = sn.data() + (size_t)p * m;
+                double* gp = g.data() + (size_t)p * (m + 1);
+                for (int i = 0; i <= j; ++i)
+                    Hp[i * m + j] = h->h_scal[p * SS + i] + h->h_scal[(size_t)P * SS + p * SS + i];
+                const double hn = std::sqrt(h->h_scal[(size_t)2 * P * SS + p * SS]);
+                Hp[(j + 1) * m + j] = hn;
+                for (int i = 0; i < j; ++i) {
+                    const double t = csp[i] * Hp[i * m + j] + snp[i] * Hp[(i + 1) * m + j];
+                    Hp[(i + 1) * m + j] = -snp[i] * Hp[i * m + j] + csp[i] * Hp[(i + 1) * m + j];
+                    Hp[i * m + j] = t;
+                }
+                const double den = std::hypot(Hp[j * m + j], Hp[(j + 1) * m + j]);
+                csp[j] = Hp[j * m + j] / den;
+                snp[j] = Hp[(j + 1) * m + j] / den;
+                Hp[j * m + j] = den;
+                Hp[(j + 1) * m + j] = 0.0;
+                gp[j + 1] = -snp[j] * gp[j];
+                gp[j] = csp[j] * gp[j];
+                its[p] += 1;
+                steps[p] = j + 1;
+                if (hn == 0.0 || std::fabs(gp[j + 1]) <= target[p] || its[p] >= maxit) {
+                    cyc[p] = 0;
+                    changed = true;
+                }
             }
-            const double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
-            cs[j] = H[j * m + j] / den;
-            sn[j] = H[(j + 1) * m + j] / den;
-            H[j * m + j] = den;
-            H[(j + 1) * m + j] = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-            ++its;
-            steps = j + 1;
-            if (hn == 0.0 || std::fabs(g[j + 1]) <= target || its >= maxit) break;
-            CK(timed(h, RAS_K_KRYLOV, 16.0 * len, [&] { return ras::launch_scale_copy(h->st, w, nullptr, nullptr, 1.0 / hn, w, len); }));
+            if (changed) TRY(set_mask(h, 0, cyc));
+            if (std::any_of(cyc.begin(), cyc.end(), [](int v) { return v != 0; })) {
+                CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
+                    return ras::launch_seg_scale(h->st, P, nb, h->d_segs, dmask, w, n2, 1.0, w);
+                }));
+            }
         }
-        for (int i = steps - 1; i >= 0; --i) {
-            double s = g[i];
-            for (int k = i + 1; k < steps; ++k) s -= H[i * m + k] * y[k];
-            y[i] = s / H[i * m + i];
+        // x += M (V y) for the problems that took steps in this cycle
+        int maxsteps = 0;
+        std::vector<int> took(P, 0);
+        std::fill(y.begin(), y.end(), 0.0);
+        for (int p = 0; p < P; ++p) {
+            if (steps[p] == 0) continue;
+            took[p] = 1;
+            maxsteps = std::max(maxsteps, steps[p]);
+            const double* Hp = H.data() + (size_t)p * (m + 1) * m;
+            const double* gp = g.data() + (size_t)p * (m + 1);
+            double* yp = y.data() + (size_t)p * SS;
+            for (int i = steps[p] - 1; i >= 0; --i) {
+                double s = gp[i];
+                for (int k = i + 1; k < steps[p]; ++k) s -= Hp[i * m + k] * yp[k];
+                yp[i] = s / Hp[i * m + i];
+            }
         }
-        for (int i = 0; i < steps; ++i) h->h_scal[96 + i] = y[i];
-        CK(cudaMemcpyAsync(h->scal + 96, h->h_scal + 96, steps * sizeof(double), cudaMemcpyHostToDevice, h->st));
-        CK(cudaMemsetAsync(upd, 0, len * sizeof(double), h->st));
-        CK(timed(h, RAS_K_KRYLOV, 8.0 * len * (steps + 2), [&] { return ras::launch_axpy_multi(h->st, V, len, steps, h->scal + 96, 1.0, upd, len); }));
+        if (maxsteps == 0) return RAS_OK;
+        double* ycoef = h->scal + (size_t)3 * P * SS;
+        CK(cudaMemcpyAsync(ycoef, y.data(), (size_t)P * SS * sizeof(double), cudaMemcpyHostToDevice, h->st));
+        TRY(set_mask(h, 0, took));
+        CK(cudaMemsetAsync(upd, 0, L * sizeof(double), h->st));
+        CK(timed(h, RAS_K_KRYLOV, 8.0 * seglen * (maxsteps + 2), [&] {
+            return ras::launch_seg_axpy(h->st, P, nb, h->d_segs, dmask, V, L, maxsteps, ycoef, 1.0, upd);
+        }));
+        const double* add = upd;
         if (prec) {
-            TRY(M(upd, h->Z));
-            CK(timed(h, RAS_K_KRYLOV, 24.0 * len, [&] { return ras::launch_axpy(h->st, 1.0, h->Z, x, len); }));
-        } else {
-            CK(timed(h, RAS_K_KRYLOV, 24.0 * len, [&] { return ras::launch_axpy(h->st, 1.0, upd, x, len); }));
+            TRY(M(upd, h->Z, took));
+            add = h->Z;
         }
-        TRY(A(x, r));
-        CK(timed(h, RAS_K_KRYLOV, 24.0 * len, [&] { return ras::launch_add_scaled(h->st, b, r, -1.0, r, len); }));
+        CK(timed(h, RAS_K_KRYLOV, 24.0 * seglen, [&] {
+            return ras::launch_seg_add_scaled(h->st, P, nb, h->d_segs, dmask, x, add, 1.0, x);
+        }));
+        // r = b - A x for the problems still iterating
+        if (std::none_of(act.begin(), act.end(), [](int v) { return v != 0; })) return RAS_OK;
+        TRY(set_mask(h, 0, act));
+        TRY(A(x, r, act));
+        CK(timed(h, RAS_K_KRYLOV, 24.0 * seglen, [&] {
+            return ras::launch_seg_add_scaled(h->st, P, nb, h->d_segs, dmask, b, r, -1.0, r);
+        }));
     }
 }
 
 // --------------------------------------------------------------- Alg. 2
+// RASPEN for every problem of the handle, in lockstep: a problem leaves the
+// loop when its own stop test holds (or at kmax).
 int raspen_internal(ras_problem* h, ras_stats* s) {
-    const long long len = 2 * h->N;
-    int rc = ras_apply_internal(h, 1, h->F, s);
+    const int P = h->nprob, nb = h->nbp;
+    const ras_opts& o = h->o;
+    std::vector<double> pstart(P, o.eps0);
+    int rc = ras_apply_internal(h, pstart, h->F, s);
     if (rc < 0) return rc;
-    double nrm;
-    TRY(vec_norm(h, h->F, nrm));
-    const double stop = std::max(h->o.tol, h->o.tol * nrm);
-    if (s) s->res0 = nrm;
-    int k = 0;
-    auto A = [&](const double* in, double* out) { return jvp_internal(h, in, out); };
-    auto M = [&](const double*, double*) { return RAS_OK; };
-    while (nrm > stop && k < h->o.kmax_outer_raspen) {
-        CK(timed(h, RAS_K_KRYLOV, 16.0 * len, [&] { return ras::launch_scale_copy(h->st, h->F, nullptr, nullptr, -1.0, h->T1, len); }));
-        int its = 0;
-        bool conv = false;
-        TRY(gmres(h, A, M, false, h->T1, h->Dv, its, conv));
-        if (s) s->gmres_its += its;
-        CK(timed(h, RAS_K_KRYLOV, 24.0 * len, [&] { return ras::launch_axpy(h->st, 1.0, h->Dv, h->X, len); }));
-        ++k;
-        rc = ras_apply_internal(h, 0, h->F, s);
+    std::vector<int> all(P, 1), need(P, 0), k(P, 0), its, conv;
+    std::vector<double> nrm(P), stop(P);
+    const int* dneed = h->d_mask + P;   // row 1
+    TRY(set_mask(h, 1, all));
+    TRY(seg_norms2(h, h->F, dneed));
+    for (int p = 0; p < P; ++p) {
+        nrm[p] = std::sqrt(h->h_scal[p * SS]);
+        stop[p] = std::max(o.tol, o.tol * nrm[p]);
+        if (s) s[p].res0 = nrm[p];
+    }
+    double seglen = 0.0;
+    for (auto& sg : h->segs) seglen += (double)sg.len;
+    // the JVP runs for the problems GMRES is still iterating (d_mask row 0)
+    auto A = [&](const double* in, double* out, const std::vector<int>& mask) {
+        return jvp_internal(h, in, out, &mask);
+    };
+    auto M = [&](const double*, double*, const std::vector<int>&) { return RAS_OK; };
+    for (;;) {
+        bool any = false;
+        for (int p = 0; p < P; ++p) {
+            need[p] = (nrm[p] > stop[p] && k[p] < o.kmax_outer_raspen) ? 1 : 0;
+            any = any || need[p];
+        }
+        if (!any) break;
+        TRY(set_mask(h, 1, need));
+        CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
+            return ras::launch_seg_scale(h->st, P, nb, h->d_segs, dneed, h->F, nullptr, -1.0, h->T1);
+        }));
+        TRY(gmres(h, A, M, false, h->T1, h->Dv, need, its, conv));
+        CK(timed(h, RAS_K_KRYLOV, 24.0 * seglen, [&] {
+            return ras::launch_seg_add_scaled(h->st, P, nb, h->d_segs, dneed, h->X, h->Dv, 1.0, h->X);
+        }));
+        for (int p = 0; p < P; ++p) {
+            if (need[p]) {
+                k[p] += 1;
+                if (s) s[p].gmres_its += its[p];
+                pstart[p] = o.eps_min;
+            } else {
+                pstart[p] = 0.0;
+            }
+        }
+        rc = ras_apply_internal(h, pstart, h->F, s);
         if (rc < 0) {
-            if (s) s->outer_its = k;
+            for (int p = 0; p < P; ++p)
+                if (s) s[p].outer_its = k[p];
             return rc;
         }
-        TRY(vec_norm(h, h->F, nrm));
+        TRY(seg_norms2(h, h->F, dneed));
+        for (int p = 0; p < P; ++p)
+            if (need[p]) nrm[p] = std::sqrt(h->h_scal[p * SS]);
     }
-    if (s) {
-        s->outer_its = k;
-        s->res = nrm;
-        s->status = (nrm <= stop) ? RAS_OK : RAS_ENOCONV;
+    int worst = RAS_OK;
+    for (int p = 0; p < P; ++p) {
+        const int st = (nrm[p] <= stop[p]) ? RAS_OK : RAS_ENOCONV;
+        if (s) {
+            s[p].outer_its = k[p];
+            s[p].res = nrm[p];
+            s[p].status = st;
+        }
+        worst = std::min(worst, st);
     }
-    if (!(nrm <= stop)) return fail(h, RAS_ENOCONV, "RASPEN reached kmax_outer_raspen");
+    if (worst < 0) return fail(h, worst, "RASPEN reached kmax_outer_raspen");
     return RAS_OK;
 }
 
 // --------------------------------------------------------------- Newton_RAS
 int newton_ras_internal(ras_problem* h, ras_stats* s) {
-    const long long len = 2 * h->N;
+    const int nb = h->nbp;
+    const long long N = plane(h, 0);
     const ras_opts& o = h->o;
+    const double seglen = (double)h->segs[0].len;
     double eps = o.eps0, nrm, flr;
     TRY(residual_norm(h, h->X, nullptr, 0.0, eps, h->F, nrm, flr));
     const double stop = std::max(o.tol, o.tol * nrm);
     if (s) s->res0 = nrm;
     int k = 0, status = RAS_OK;
-    auto A = [&](const double* in, double* out) -> int {
-        CK(timed(h, RAS_K_OTHER, 56.0 * h->N, [&] { return ras::launch_jacvec_global(h->st, h->prob, h->coefG, in, in + h->N, out, out + h->N); }));
+    std::vector<int> one(1, 1), its, conv;
+    auto A = [&](const double* in, double* out, const std::vector<int>&) -> int {
+        CK(timed(h, RAS_K_OTHER, 56.0 * N, [&] {
+            return ras::launch_jacvec_global(h->st, h->probs[0], h->coefG, in, in + N, out, out + N);
+        }));
         return RAS_OK;
     };
-    auto M = [&](const double* in, double* out) { return precond_internal(h, in, out); };
+    auto M = [&](const double* in, double* out, const std::vector<int>&) { return precond_internal(h, in, out); };
     for (;;) {
         if (!std::isfinite(nrm)) { status = RAS_ENONFINITE; break; }
         if (eps == o.eps_min) {
@@ -609,12 +812,14 @@ int newton_ras_internal(ras_problem* h, ras_stats* s) {
         }
         if (k >= o.kmax_outer_newton) { status = RAS_ENOCONV; break; }
         TRY(factor_at(h, eps));
-        CK(timed(h, RAS_K_OTHER, 40.0 * h->N, [&] { return ras::launch_coef_global(h->st, h->prob, h->X, h->X + h->N, eps, h->coefG); }));
-        CK(timed(h, RAS_K_KRYLOV, 16.0 * len, [&] { return ras::launch_scale_copy(h->st, h->F, nullptr, nullptr, -1.0, h->T1, len); }));
-        int its = 0;
-        bool conv = false;
-        TRY(gmres(h, A, M, true, h->T1, h->Dv, its, conv));
-        if (s) s->gmres_its += its;
+        CK(timed(h, RAS_K_OTHER, 40.0 * N, [&] {
+            return ras::launch_coef_global(h->st, h->probs[0], h->X, h->X + N, eps, h->coefG);
+        }));
+        CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
+            return ras::launch_seg_scale(h->st, 1, nb, h->d_segs, nullptr, h->F, nullptr, -1.0, h->T1);
+        }));
+        TRY(gmres(h, A, M, true, h->T1, h->Dv, one, its, conv));
+        if (s) s->gmres_its += its[0];
         double alpha = 1.0, nt = 0.0, ft = 0.0;
         int hh = 0;
         for (;;) {
@@ -627,7 +832,9 @@ int newton_ras_internal(ras_problem* h, ras_stats* s) {
             s->halvings += hh;
             if (!(nt <= o.sigma * nrm)) s->exhausted += 1;
         }
-        CK(timed(h, RAS_K_KRYLOV, 24.0 * len, [&] { return ras::launch_add_scaled(h->st, h->X, h->Dv, alpha, h->X, len); }));
+        CK(timed(h, RAS_K_KRYLOV, 24.0 * seglen, [&] {
+            return ras::launch_seg_add_scaled(h->st, 1, nb, h->d_segs, nullptr, h->X, h->Dv, alpha, h->X);
+        }));
         const double en = ras::next_eps(eps, o.gamma, o.eps_min);
         if (en == eps) {
             std::swap(h->F, h->Ov);
@@ -647,6 +854,11 @@ int newton_ras_internal(ras_problem* h, ras_stats* s) {
     }
     if (status < 0) return fail(h, status, "Newton_RAS stopped without convergence");
     return status;
+}
+
+int need_single(ras_problem* h) {
+    if (h->nprob != 1) return fail(h, RAS_EINVAL, "this entry point takes a single-problem handle");
+    return RAS_OK;
 }
 
 }  // namespace
@@ -680,54 +892,91 @@ int ras_default_opts(ras_opts* o) {
     return RAS_OK;
 }
 
-int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu, const double* y_d,
-               const double* f, const ras_opts* o, void* stream, ras_problem** out) {
+int ras_batch_create(int count, const ras_problem_desc* pd, const ras_opts* o, void* stream, ras_problem** out) {
     if (!out) return RAS_EINVAL;
     *out = nullptr;
-    if (n < 2 || sx < 1 || sy < 1 || sx > n || sy > n || overlap < 0 || phi < 0 || phi > 2 || !(nu > 0) ||
-        !(mu > 0) || !std::isfinite(nu) || !std::isfinite(mu) || !y_d)
-        return RAS_EINVAL;
+    if (count < 1 || count > 4096 || !pd) return RAS_EINVAL;
+    for (int p = 0; p < count; ++p) {
+        const ras_problem_desc& d = pd[p];
+        if (d.n < 2 || d.sx < 1 || d.sy < 1 || d.sx > d.n || d.sy > d.n || d.overlap < 0 || d.phi < 0 ||
+            d.phi > 2 || !(d.nu > 0) || !(d.mu > 0) || !std::isfinite(d.nu) || !std::isfinite(d.mu) || !d.y_d)
+            return RAS_EINVAL;
+    }
     ras_problem* h = new ras_problem();
-    h->n = n; h->sx = sx; h->sy = sy; h->overlap = overlap; h->phi = phi; h->nu = nu; h->mu = mu;
+    h->nprob = count;
+    h->desc.assign(pd, pd + count);
     if (o) h->o = *o;
     else ras_default_opts(&h->o);
     h->st = (cudaStream_t)stream;
     int rc = validate_opts(h, h->o);
     if (rc < 0) { delete h; return rc; }
-    h->N = (long long)n * n;
-    const auto bx = split_blocks(n, sx), by = split_blocks(n, sy);
-    long long voff = 0, noff = 0, goff = 0;
-    for (int j = 0; j < sy; ++j) {
-        for (int i = 0; i < sx; ++i) {
-            SubDev s{};
-            s.prob = 0;
-            s.ox0 = bx[i].first; s.owx = bx[i].second - bx[i].first;
-            s.oy0 = by[j].first; s.owy = by[j].second - by[j].first;
-            s.x0 = std::max(0, s.ox0 - overlap);
-            s.y0 = std::max(0, s.oy0 - overlap);
-            s.wx = std::min(n, bx[i].second + overlap) - s.x0;
-            s.wy = std::min(n, by[j].second + overlap) - s.y0;
-            s.mp = ((2 * s.wx + 31) / 32) * 32;
-            s.voff = voff; s.noff = noff; s.goff = goff;
-            voff += 2LL * s.wx * s.wy;
-            noff += (long long)s.wx * s.wy;
-            goff += (long long)s.wy * s.mp * s.mp;
-            h->maxm = std::max(h->maxm, 2 * s.wx);
-            h->subs.push_back(s);
+    long long voff = 0, noff = 0, goff = 0, vec = 0, nn_tot = 0;
+    bool any_f = false;
+    for (int p = 0; p < count; ++p) {
+        const ras_problem_desc& d = pd[p];
+        const int n = d.n;
+        ProbDev P{};
+        P.n = n;
+        P.phi = d.phi;
+        P.h = 1.0 / (n + 1);
+        P.beta = 1.0 / (P.h * P.h);
+        P.nu = d.nu;
+        P.mu = d.mu;
+        P.kappa = h->o.kappa;
+        P.ofs = vec;
+        h->probs.push_back(P);
+        h->segs.push_back(Seg{vec, 2LL * n * n});
+        h->sub_first.push_back((int)h->subs.size());
+        const auto bx = split_blocks(n, d.sx), by = split_blocks(n, d.sy);
+        for (int j = 0; j < d.sy; ++j) {
+            for (int i = 0; i < d.sx; ++i) {
+                SubDev s{};
+                s.prob = p;
+                s.ox0 = bx[i].first; s.owx = bx[i].second - bx[i].first;
+                s.oy0 = by[j].first; s.owy = by[j].second - by[j].first;
+                s.x0 = std::max(0, s.ox0 - d.overlap);
+                s.y0 = std::max(0, s.oy0 - d.overlap);
+                s.wx = std::min(n, bx[i].second + d.overlap) - s.x0;
+                s.wy = std::min(n, by[j].second + d.overlap) - s.y0;
+                s.mp = ((2 * s.wx + 31) / 32) * 32;
+                s.voff = voff; s.noff = noff; s.goff = goff;
+                voff += 2LL * s.wx * s.wy;
+                noff += (long long)s.wx * s.wy;
+                goff += (long long)s.wy * s.mp * s.mp;
+                h->maxm = std::max(h->maxm, 2 * s.wx);
+                h->subs.push_back(s);
+            }
         }
+        h->sub_count.push_back((int)h->subs.size() - h->sub_first.back());
+        vec += 2LL * n * n;
+        nn_tot += (long long)n * n;
+        any_f = any_f || d.f != nullptr;
     }
     if (h->maxm > ras::MAX_M) {
         delete h;
         return RAS_EINVAL;
     }
     h->nsub = (int)h->subs.size();
-    h->Lsum = voff; h->Nsum = noff; h->Gsum = goff;
-    const long long N = h->N;
+    h->Lsum = voff; h->Nsum = noff; h->Gsum = goff; h->L = vec;
+    // register-tile classes of the FP32 factorisation: tile = mp / 16
+    std::vector<int> lists;
+    h->tile_off.assign(NTILE, 0);
+    h->tile_cnt.assign(NTILE, 0);
+    for (int c = 0; c < NTILE; ++c) {
+        h->tile_off[c] = (int)lists.size();
+        for (int i = 0; i < h->nsub; ++i)
+            if (h->subs[i].mp / 32 - 1 == c) lists.push_back(i);
+        h->tile_cnt[c] = (int)lists.size() - h->tile_off[c];
+    }
+    h->nbp = std::max(8, ras::VEC_BLOCKS / count);
     rc = RAS_OK;
     auto A = [&](int r) { if (rc == RAS_OK && r < 0) rc = r; };
-    A(dalloc(h, &h->yd, N));
+    A(dalloc(h, &h->yd, nn_tot));
+    if (any_f) A(dalloc(h, &h->f, nn_tot));
     A(dalloc(h, &h->d_subs, h->nsub));
-    A(dalloc(h, &h->d_prob, 1));
+    A(dalloc(h, &h->d_probs, count));
+    A(dalloc(h, &h->d_segs, count));
+    A(dalloc(h, &h->d_lists, std::max<size_t>(1, lists.size())));
     A(dalloc(h, &h->cpool, h->Lsum));
     A(dalloc(h, &h->dpool, h->Lsum));
     A(dalloc(h, &h->Kpool, h->Lsum));
@@ -737,15 +986,16 @@ int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu
     A(dalloc(h, &h->ls, h->nsub));
     A(dalloc(h, &h->d_active, 1));
     A(dalloc(h, &h->d_err, 1));
-    for (double** p : {&h->X, &h->F, &h->Dv, &h->Ov, &h->T1, &h->T2, &h->T3, &h->Z}) A(dalloc(h, p, 2 * N));
-    A(dalloc(h, &h->coefG, 3 * N));
-    A(dalloc(h, &h->partials, (size_t)ras::VEC_BLOCKS * 32));
-    A(dalloc(h, &h->scal, NSCAL));
-    if (rc == RAS_OK && f) A(dalloc(h, &h->f, N));
+    A(dalloc(h, &h->d_mask, 2 * count));
+    A(dalloc(h, &h->d_pstart, count));
+    for (double** p : {&h->X, &h->F, &h->Dv, &h->Ov, &h->T1, &h->T2, &h->T3, &h->Z}) A(dalloc(h, p, h->L));
+    if (count == 1) A(dalloc(h, &h->coefG, 3 * nn_tot));
+    A(dalloc(h, &h->partials, (size_t)count * SS * std::max(h->nbp, (int)ras::VEC_BLOCKS)));
+    A(dalloc(h, &h->scal, (size_t)4 * count * SS));
     if (rc == RAS_OK) A(alloc_factor_pools(h));
     if (rc == RAS_OK) {
         if (cudaMallocHost((void**)&h->h_active, sizeof(int)) != cudaSuccess ||
-            cudaMallocHost((void**)&h->h_scal, NSCAL * sizeof(double)) != cudaSuccess) {
+            cudaMallocHost((void**)&h->h_scal, (size_t)4 * count * SS * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             rc = RAS_ENOMEM;
         }
@@ -754,22 +1004,26 @@ int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu
         ras_destroy(h);
         return rc;
     }
-    h->prob.n = n;
-    h->prob.phi = phi;
-    h->prob.h = 1.0 / (n + 1);
-    h->prob.beta = 1.0 / (h->prob.h * h->prob.h);
-    h->prob.nu = nu;
-    h->prob.mu = mu;
-    h->prob.kappa = h->o.kappa;
-    h->prob.yd = h->yd;
-    h->prob.f = h->f;
-    h->prob.ofs = 0;
+    // y_d and f of problem p at the plane offset sum_{q<p} n_q^2
+    long long poff = 0;
     cudaError_t e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->yd, y_d, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
-    if (e == cudaSuccess && f) e = cudaMemcpyAsync(h->f, f, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
+    for (int p = 0; p < count && e == cudaSuccess; ++p) {
+        const long long N = plane(h, p);
+        h->probs[p].yd = h->yd + poff;
+        h->probs[p].f = pd[p].f ? h->f + poff : nullptr;
+        e = cudaMemcpyAsync(h->yd + poff, pd[p].y_d, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
+        if (e == cudaSuccess && pd[p].f)
+            e = cudaMemcpyAsync(h->f + poff, pd[p].f, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
+        poff += N;
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->d_subs, h->subs.data(), h->nsub * sizeof(SubDev), cudaMemcpyHostToDevice, h->st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_prob, &h->prob, sizeof(ProbDev), cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_probs, h->probs.data(), count * sizeof(ProbDev), cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_segs, h->segs.data(), count * sizeof(Seg), cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess && !lists.empty())
+        e = cudaMemcpyAsync(h->d_lists, lists.data(), lists.size() * sizeof(int), cudaMemcpyHostToDevice, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) {
         ras_destroy(h);
@@ -778,6 +1032,16 @@ int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu
     *out = h;
     return RAS_OK;
 }
+
+int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu, const double* y_d,
+               const double* f, const ras_opts* o, void* stream, ras_problem** out) {
+    ras_problem_desc d{};
+    d.n = n; d.sx = sx; d.sy = sy; d.overlap = overlap; d.phi = phi; d.nu = nu; d.mu = mu;
+    d.y_d = y_d; d.f = f;
+    return ras_batch_create(1, &d, o, stream, out);
+}
+
+int ras_problem_count(const ras_problem* h) { return h ? h->nprob : RAS_EINVAL; }
 
 int ras_set_eps(ras_problem* h, double eps_min) {
     if (!h) return RAS_EINVAL;
@@ -796,8 +1060,8 @@ int ras_set_opts(ras_problem* h, const ras_opts* o) {
     h->jvp_ready = false;
     TRY(alloc_factor_pools(h));
     if (kappa_changed) {
-        h->prob.kappa = o->kappa;
-        CK(cudaMemcpyAsync(h->d_prob, &h->prob, sizeof(ProbDev), cudaMemcpyHostToDevice, h->st));
+        for (auto& P : h->probs) P.kappa = o->kappa;
+        CK(cudaMemcpyAsync(h->d_probs, h->probs.data(), h->nprob * sizeof(ProbDev), cudaMemcpyHostToDevice, h->st));
         TRY(sync(h));
     }
     return RAS_OK;
@@ -805,14 +1069,16 @@ int ras_set_opts(ras_problem* h, const ras_opts* o) {
 
 int ras_set_data(ras_problem* h, const double* y_d, const double* f) {
     if (!h || !y_d) return RAS_EINVAL;
-    CK(cudaMemcpyAsync(h->yd, y_d, h->N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    TRY(need_single(h));
+    const long long N = plane(h, 0);
+    CK(cudaMemcpyAsync(h->yd, y_d, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     if (f) {
-        if (!h->f) TRY(dalloc(h, &h->f, h->N));
-        CK(cudaMemcpyAsync(h->f, f, h->N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        if (!h->f) TRY(dalloc(h, &h->f, N));
+        CK(cudaMemcpyAsync(h->f, f, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     }
-    if ((f != nullptr) != (h->prob.f != nullptr)) {
-        h->prob.f = f ? h->f : nullptr;
-        CK(cudaMemcpyAsync(h->d_prob, &h->prob, sizeof(ProbDev), cudaMemcpyHostToDevice, h->st));
+    if ((f != nullptr) != (h->probs[0].f != nullptr)) {
+        h->probs[0].f = f ? h->f : nullptr;
+        CK(cudaMemcpyAsync(h->d_probs, h->probs.data(), sizeof(ProbDev), cudaMemcpyHostToDevice, h->st));
     }
     h->jvp_ready = false;
     return sync(h);
@@ -821,7 +1087,8 @@ int ras_set_data(ras_problem* h, const double* y_d, const double* f) {
 int ras_residual(ras_problem* h, const double* y, const double* p, double eps, double* Fy, double* Fp,
                  double* norm_host) {
     if (!h || !y || !p || !(eps > 0)) return RAS_EINVAL;
-    CK(ras::launch_residual_global(h->st, h->prob, y, p, nullptr, nullptr, 0.0, eps, Fy, Fp, h->partials));
+    TRY(need_single(h));
+    CK(ras::launch_residual_global(h->st, h->probs[0], y, p, nullptr, nullptr, 0.0, eps, Fy, Fp, h->partials));
     CK(ras::launch_reduce_partials(h->st, h->partials, ras::VEC_BLOCKS, 2, h->scal));
     CK(cudaMemcpyAsync(h->h_scal, h->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     TRY(sync(h));
@@ -832,12 +1099,14 @@ int ras_residual(ras_problem* h, const double* y, const double* p, double eps, d
 int ras_apply(ras_problem* h, const double* y, const double* p, int continuation, double* Fy, double* Fp,
               ras_stats* stats) {
     if (!h || !y || !p || !Fy || !Fp) return RAS_EINVAL;
-    stats_clear(stats);
-    TRY(copy_in(h, h->X, y, p));
-    const int rc = ras_apply_internal(h, continuation, h->F, stats);
+    TRY(need_single(h));
+    stats_clear(stats, 1);
+    TRY(copy_in(h, h->X, 0, y, p));
+    const std::vector<double> pstart(1, continuation ? h->o.eps0 : h->o.eps_min);
+    const int rc = ras_apply_internal(h, pstart, h->F, stats);
     if (rc == RAS_ECUDA) return rc;
     TRY(check_err(h));
-    TRY(copy_out(h, h->F, Fy, Fp));
+    TRY(copy_out(h, h->F, 0, Fy, Fp));
     TRY(sync(h));
     if (stats) stats->status = rc;
     return rc;
@@ -845,10 +1114,11 @@ int ras_apply(ras_problem* h, const double* y, const double* p, int continuation
 
 int ras_jvp(ras_problem* h, const double* dy, const double* dp, double* oy, double* op) {
     if (!h || !dy || !dp || !oy || !op) return RAS_EINVAL;
+    TRY(need_single(h));
     if (!h->jvp_ready) return fail(h, RAS_ESTATE, "ras_jvp needs a successful ras_apply first");
-    TRY(copy_in(h, h->Dv, dy, dp));
-    TRY(jvp_internal(h, h->Dv, h->Ov));
-    TRY(copy_out(h, h->Ov, oy, op));
+    TRY(copy_in(h, h->Dv, 0, dy, dp));
+    TRY(jvp_internal(h, h->Dv, h->Ov, nullptr));
+    TRY(copy_out(h, h->Ov, 0, oy, op));
     TRY(sync(h));
     return check_err(h);
 }
@@ -856,35 +1126,45 @@ int ras_jvp(ras_problem* h, const double* dy, const double* dp, double* oy, doub
 int ras_precondition(ras_problem* h, const double* y, const double* p, double eps, const double* ry,
                      const double* rp, double* zy, double* zp) {
     if (!h || !y || !p || !ry || !rp || !zy || !zp || !(eps > 0)) return RAS_EINVAL;
-    TRY(copy_in(h, h->X, y, p));
+    TRY(need_single(h));
+    TRY(copy_in(h, h->X, 0, y, p));
     TRY(factor_at(h, eps));
-    TRY(copy_in(h, h->T1, ry, rp));
+    TRY(copy_in(h, h->T1, 0, ry, rp));
     TRY(precond_internal(h, h->T1, h->Z));
-    TRY(copy_out(h, h->Z, zy, zp));
+    TRY(copy_out(h, h->Z, 0, zy, zp));
     TRY(sync(h));
     return check_err(h);
 }
 
-int ras_raspen_solve(ras_problem* h, double* y, double* p, ras_stats* stats) {
+int ras_batch_raspen_solve(ras_problem* h, double* const* y, double* const* p, ras_stats* stats) {
     if (!h || !y || !p) return RAS_EINVAL;
-    stats_clear(stats);
-    TRY(copy_in(h, h->X, y, p));
+    for (int k = 0; k < h->nprob; ++k)
+        if (!y[k] || !p[k]) return RAS_EINVAL;
+    stats_clear(stats, h->nprob);
+    for (int k = 0; k < h->nprob; ++k) TRY(copy_in(h, h->X, k, y[k], p[k]));
     const int rc = raspen_internal(h, stats);
     if (rc == RAS_ECUDA) return rc;
     TRY(check_err(h));
-    TRY(copy_out(h, h->X, y, p));
+    for (int k = 0; k < h->nprob; ++k) TRY(copy_out(h, h->X, k, y[k], p[k]));
     TRY(sync(h));
     return rc;
 }
 
+int ras_raspen_solve(ras_problem* h, double* y, double* p, ras_stats* stats) {
+    if (!h || !y || !p) return RAS_EINVAL;
+    TRY(need_single(h));
+    return ras_batch_raspen_solve(h, &y, &p, stats);
+}
+
 int ras_newton_ras_solve(ras_problem* h, double* y, double* p, ras_stats* stats) {
     if (!h || !y || !p) return RAS_EINVAL;
-    stats_clear(stats);
-    TRY(copy_in(h, h->X, y, p));
+    TRY(need_single(h));
+    stats_clear(stats, 1);
+    TRY(copy_in(h, h->X, 0, y, p));
     const int rc = newton_ras_internal(h, stats);
     if (rc == RAS_ECUDA) return rc;
     TRY(check_err(h));
-    TRY(copy_out(h, h->X, y, p));
+    TRY(copy_out(h, h->X, 0, y, p));
     TRY(sync(h));
     return rc;
 }
@@ -893,17 +1173,19 @@ int ras_solve_host(ras_problem* h, int method, const double* y_d_host, double* y
                    ras_stats* stats) {
     if (!h || !y_host || !p_host || (method != RAS_METHOD_RASPEN && method != RAS_METHOD_NEWTON_RAS))
         return RAS_EINVAL;
-    stats_clear(stats);
-    const size_t nb = h->N * sizeof(double);
+    TRY(need_single(h));
+    stats_clear(stats, 1);
+    const long long N = plane(h, 0);
+    const size_t nb = N * sizeof(double);
     if (y_d_host) CK(cudaMemcpyAsync(h->yd, y_d_host, nb, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->X, y_host, nb, cudaMemcpyHostToDevice, h->st));
-    CK(cudaMemcpyAsync(h->X + h->N, p_host, nb, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->X + N, p_host, nb, cudaMemcpyHostToDevice, h->st));
     h->jvp_ready = false;
     const int rc = (method == RAS_METHOD_RASPEN) ? raspen_internal(h, stats) : newton_ras_internal(h, stats);
     if (rc == RAS_ECUDA) return rc;
     TRY(check_err(h));
     CK(cudaMemcpyAsync(y_host, h->X, nb, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemcpyAsync(p_host, h->X + h->N, nb, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(p_host, h->X + N, nb, cudaMemcpyDeviceToHost, h->st));
     TRY(sync(h));
     return rc;
 }
@@ -927,10 +1209,10 @@ const char* ras_last_error(const ras_problem* h) {
 void ras_destroy(ras_problem* h) {
     if (!h) return;
     cudaStreamSynchronize(h->st);
-    for (void* p : h->allocs) cudaFree(p);
-    h->allocs.clear();
     prof_flush(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
     if (h->h_active) cudaFreeHost(h->h_active);
     if (h->h_scal) cudaFreeHost(h->h_scal);
     delete h;

@@ -123,15 +123,28 @@ __device__ __forceinline__ void decide(LocalState& L, const NewtonParams& np) {
     L.active = 1;
 }
 
+// pstart[p]: eps at which the local solves of problem p start (eps_0 with
+// continuation, eps_min without); <= 0 means problem p does not take part.
 __global__ void __launch_bounds__(NT) k_local_init(int nsub, const SubDev* __restrict__ subs,
                                                    const ProbDev* __restrict__ probs, const double* X,
-                                                   LocalState* ls, double eps_start, NewtonParams np,
-                                                   double* cpool, double* Kpool, int* active_count) {
+                                                   LocalState* ls, const double* __restrict__ pstart,
+                                                   NewtonParams np, double* cpool, double* Kpool,
+                                                   int* active_count) {
     __shared__ double red[2 * NT];
     const int i = blockIdx.x;
     if (i >= nsub) return;
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
+    const double eps_start = pstart[s.prob];
+    if (!(eps_start > 0.0)) {
+        if (threadIdx.x == 0) {
+            LocalState st{};
+            st.status = ST_SKIP;
+            st.active = 0;
+            ls[i] = st;
+        }
+        return;
+    }
     const int L = 2 * s.wx * s.wy;
     double* c = cpool + s.voff;
     for (int q = threadIdx.x; q < L; q += NT) c[q] = 0.0;
@@ -171,6 +184,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_local_factor(int nsub, int max
     const int i = blockIdx.x;
     if (i >= nsub) return;
     if (only_active && !ls[i].active) return;
+    if (ls[i].status == ST_SKIP) return;
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
     const int m = 2 * s.wx, W = s.wy, nn = s.wx * s.wy, LD = maxm + 1;
@@ -356,10 +370,11 @@ __global__ void __launch_bounds__(NT) k_local_linesearch(int nsub, const SubDev*
 
 // Restricted prolongation (Sec. 4.2): F[owned nodes of i] = C_i.
 __global__ void __launch_bounds__(NT) k_local_prolong(int nsub, const SubDev* __restrict__ subs,
-                                                      const ProbDev* __restrict__ probs,
+                                                      const ProbDev* __restrict__ probs, const LocalState* ls,
                                                       const double* cpool, double* F) {
     const int i = blockIdx.x;
     if (i >= nsub) return;
+    if (ls[i].status == ST_SKIP) return;
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
     const long long nn = (long long)P.n * P.n;
@@ -422,7 +437,8 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_reg(int nsub, 
                                                                       const ProbDev* __restrict__ probs,
                                                                       const double* X, LocalState* ls,
                                                                       const double* cpool, double* coef,
-                                                                      float* gpool, int only_active) {
+                                                                      float* gpool, int only_active,
+                                                                      const int* __restrict__ list) {
     constexpr int MM = 16 * R;
     constexpr int PAD = ((R + 3) / 4) * 4;   // owner stride in the broadcast buffers
     static_assert(FACT_THREADS == 256, "16 x 16 thread tile");
@@ -436,9 +452,10 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_reg(int nsub, 
     __shared__ float sh_piv;
     extern __shared__ __align__(16) float Ms[];
     constexpr int LDS = MM + 4;
-    const int i = blockIdx.x;
-    if (i >= nsub) return;
+    if ((int)blockIdx.x >= nsub) return;
+    const int i = list ? list[blockIdx.x] : (int)blockIdx.x;
     if (only_active && !ls[i].active) return;
+    if (ls[i].status == ST_SKIP) return;
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
     const int m = 2 * s.wx, W = s.wy, nn = s.wx * s.wy, mp = s.mp;
@@ -660,24 +677,37 @@ size_t factor_smem(int maxm) {
 
 // ------------------------------------------------------------------ launchers
 cudaError_t launch_local_init(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,
-                              const double* X, LocalState* ls, double eps_start, NewtonParams np,
+                              const double* X, LocalState* ls, const double* pstart, NewtonParams np,
                               double* cpool, double* Kpool, int* active_count) {
     count_launch();
-    k_local_init<<<nsub, NT, 0, st>>>(nsub, subs, probs, X, ls, eps_start, np, cpool, Kpool, active_count);
+    k_local_init<<<nsub, NT, 0, st>>>(nsub, subs, probs, X, ls, pstart, np, cpool, Kpool, active_count);
     return cudaGetLastError();
 }
 
 template <int R>
-cudaError_t launch_factor_reg(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,
+cudaError_t launch_factor_reg(cudaStream_t st, int count, const SubDev* subs, const ProbDev* probs,
                               const double* X, LocalState* ls, const double* cpool, double* coef,
-                              float* gpool, int only_active) {
+                              float* gpool, int only_active, const int* list) {
     const size_t sm = (size_t)(16 * R) * (16 * R + 4) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_local_factor_reg<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_local_factor_reg<R><<<nsub, FACT_THREADS, sm, st>>>(nsub, subs, probs, X, ls, cpool, coef, gpool,
-                                                          only_active);
+    k_local_factor_reg<R><<<count, FACT_THREADS, sm, st>>>(count, subs, probs, X, ls, cpool, coef, gpool,
+                                                           only_active, list);
     return cudaGetLastError();
+}
+
+cudaError_t launch_local_factor_f32(cudaStream_t st, int tile, int count, const int* list, const SubDev* subs,
+                                    const ProbDev* probs, const double* X, LocalState* ls, const double* cpool,
+                                    double* coef, float* gpool, int only_active) {
+    switch (tile) {
+        case 2: return launch_factor_reg<2>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+        case 4: return launch_factor_reg<4>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+        case 6: return launch_factor_reg<6>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+        case 8: return launch_factor_reg<8>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+        case 10: return launch_factor_reg<10>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T>
@@ -685,17 +715,9 @@ cudaError_t launch_local_factor(cudaStream_t st, int nsub, int maxm, const SubDe
                                 const ProbDev* probs, const double* X, LocalState* ls,
                                 const double* cpool, double* coef, T* gpool, int only_active) {
     if (sizeof(T) == sizeof(float)) {
-        // register tile covering the largest packed block (mp <= 16 R)
         const int mpmax = ((maxm + 31) / 32) * 32;
-        float* g = reinterpret_cast<float*>(gpool);
-        switch (mpmax / 16) {
-            case 2: return launch_factor_reg<2>(st, nsub, subs, probs, X, ls, cpool, coef, g, only_active);
-            case 4: return launch_factor_reg<4>(st, nsub, subs, probs, X, ls, cpool, coef, g, only_active);
-            case 6: return launch_factor_reg<6>(st, nsub, subs, probs, X, ls, cpool, coef, g, only_active);
-            case 8: return launch_factor_reg<8>(st, nsub, subs, probs, X, ls, cpool, coef, g, only_active);
-            case 10: return launch_factor_reg<10>(st, nsub, subs, probs, X, ls, cpool, coef, g, only_active);
-            default: return cudaErrorInvalidValue;
-        }
+        return launch_local_factor_f32(st, mpmax / 16, nsub, nullptr, subs, probs, X, ls, cpool, coef,
+                                       reinterpret_cast<float*>(gpool), only_active);
     }
     const size_t sm = factor_smem<T>(maxm);
     cudaError_t e = cudaFuncSetAttribute(k_local_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -717,9 +739,9 @@ cudaError_t launch_local_linesearch(cudaStream_t st, int nsub, const SubDev* sub
 }
 
 cudaError_t launch_local_prolong(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,
-                                 const double* cpool, double* F) {
+                                 const LocalState* ls, const double* cpool, double* F) {
     count_launch();
-    k_local_prolong<<<nsub, NT, 0, st>>>(nsub, subs, probs, cpool, F);
+    k_local_prolong<<<nsub, NT, 0, st>>>(nsub, subs, probs, ls, cpool, F);
     return cudaGetLastError();
 }
 

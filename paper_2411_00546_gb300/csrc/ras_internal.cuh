@@ -48,6 +48,11 @@ struct SubDev {
     long long noff;           // node-array offset (doubles), length wx*wy
 };
 
+// Segment of one problem inside a global vector buffer: [ofs, ofs + len).
+struct Seg {
+    long long ofs, len;
+};
+
 // State of Alg. 1 for one subdomain.
 struct LocalState {
     double eps, nrm, nrm0, stop, flr;
@@ -82,6 +87,7 @@ constexpr int ST_ENOCONV = -3;
 constexpr int ST_ESINGULAR = -5;
 constexpr int ST_ENONFINITE = -6;
 constexpr int ST_ETIMEOUT = -7;
+constexpr int ST_SKIP = 2;        // subdomain of a problem not taking part in this evaluation
 
 // ------------------------------------------------------------- pointwise math
 // Smoothed projection of Sec. 3.1 in the cancellation-free quotient form of
@@ -184,11 +190,30 @@ cudaError_t launch_axpy(cudaStream_t st, double a, const double* x, double* y, l
 cudaError_t launch_add_scaled(cudaStream_t st, const double* x, const double* d, double alpha,
                               double* out, long long len);
 
+// segmented (one segment per problem) Krylov kernels: residual.cu.
+// Partials / results are laid out [problem][32] (32 = max vectors).
+constexpr int SEG_STRIDE = 32;
+cudaError_t launch_seg_dot(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask, const double* V,
+                           long long ld, int nv, const double* w, double* partials);
+cudaError_t launch_seg_reduce(cudaStream_t st, int nprob, int nbp, const int* mask, int nv, const double* partials,
+                              double* out);
+cudaError_t launch_seg_axpy(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask, const double* V,
+                            long long ld, int nv, const double* h, double sign, double* w);
+cudaError_t launch_seg_scale(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask,
+                             const double* src, const double* n2, double sign, double* dst);
+cudaError_t launch_seg_add_scaled(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask,
+                                  const double* x, const double* d, double alpha, double* out);
+
 // per-subdomain kernels: local.cu. X, F, D, O, R, Z are global vector bases
 // (problem k at ProbDev.ofs); pools are indexed by SubDev offsets.
 cudaError_t launch_local_init(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,
-                              const double* X, LocalState* ls, double eps_start, NewtonParams np,
+                              const double* X, LocalState* ls, const double* pstart, NewtonParams np,
                               double* cpool, double* Kpool, int* active_count);
+// FP32 register-tile factorisation of the `count` subdomains in `list`
+// (device indices; null = 0..count-1), all with packed size mp <= 16*tile.
+cudaError_t launch_local_factor_f32(cudaStream_t st, int tile, int count, const int* list, const SubDev* subs,
+                                    const ProbDev* probs, const double* X, LocalState* ls, const double* cpool,
+                                    double* coef, float* gpool, int only_active);
 template <typename T>
 cudaError_t launch_local_factor(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                                 const ProbDev* probs, const double* X, LocalState* ls,
@@ -203,12 +228,12 @@ cudaError_t launch_local_linesearch(cudaStream_t st, int nsub, const SubDev* sub
                                     const double* dpool, double* Kpool, double* Ktpool,
                                     int* active_count);
 cudaError_t launch_local_prolong(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,
-                                 const double* cpool, double* F);
+                                 const LocalState* ls, const double* cpool, double* F);
 template <typename T>
 cudaError_t launch_local_jvp(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                              const ProbDev* probs, const T* gpool, T* wpool, const double* coef,
                              double* zpool, double* rpool, double* bpool, int nir, const double* D,
-                             double* O, int* err);
+                             double* O, const int* pmask, int* err);
 template <typename T>
 cudaError_t launch_local_precond(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                                  const ProbDev* probs, const T* gpool, T* wpool, const double* R,

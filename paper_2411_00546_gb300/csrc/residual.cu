@@ -185,6 +185,151 @@ __global__ void __launch_bounds__(NT) k_add_scaled(const double* x, const double
         out[g] = fma(alpha, d[g], x[g]);
 }
 
+
+// ------------------------------------------------------------------ segmented
+// Grid (nbp, nprob): blocks blockIdx.x of problem blockIdx.y grid-stride over
+// that problem's segment; problems with mask == 0 are skipped. Reductions use
+// fixed trees and fixed block order (deterministic).
+template <int NVC>
+__global__ void __launch_bounds__(NT) k_seg_dot(const Seg* __restrict__ segs, const int* __restrict__ mask,
+                                                const double* __restrict__ V, long long ld, int nv,
+                                                const double* __restrict__ w, double* partials) {
+    __shared__ double red[NT / 32][NVC];
+    const int pb = blockIdx.y, nbp = gridDim.x;
+    if (mask && !mask[pb]) return;
+    const Seg sg = segs[pb];
+    double acc[NVC];
+#pragma unroll
+    for (int v = 0; v < NVC; ++v) acc[v] = 0.0;
+    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < sg.len; g += (long long)nbp * NT) {
+        const long long x = sg.ofs + g;
+        const double wv = w[x];
+#pragma unroll
+        for (int v = 0; v < NVC; ++v) acc[v] += V[(long long)v * ld + x] * wv;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int v = 0; v < NVC; ++v) {
+        double a = acc[v];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+        if (lane == 0) red[warp][v] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < NVC) {
+        double a = 0.0;
+#pragma unroll
+        for (int k = 0; k < NT / 32; ++k) a += red[k][threadIdx.x];
+        partials[((long long)pb * SEG_STRIDE + threadIdx.x) * nbp + blockIdx.x] = a;
+    }
+    (void)nv;
+}
+
+// out[p*32 + v] = sum over the nbp partials of (p, v), in block order.
+__global__ void k_seg_reduce(int nbp, const int* __restrict__ mask, const double* __restrict__ partials,
+                             double* out) {
+    const int v = blockIdx.x, pb = blockIdx.y;
+    if (mask && !mask[pb]) return;
+    __shared__ double red[NT];
+    double a = 0.0;
+    for (int k = threadIdx.x; k < nbp; k += NT) a += partials[((long long)pb * SEG_STRIDE + v) * nbp + k];
+    a = block_sum1<NT>(a, red);
+    if (threadIdx.x == 0) out[pb * SEG_STRIDE + v] = a;
+}
+
+// w += sign * sum_v h[p*32 + v] V_v on each segment.
+__global__ void __launch_bounds__(NT) k_seg_axpy(const Seg* __restrict__ segs, const int* __restrict__ mask,
+                                                 const double* __restrict__ V, long long ld, int nv,
+                                                 const double* __restrict__ h, double sign, double* w) {
+    __shared__ double hs[SEG_STRIDE];
+    const int pb = blockIdx.y, nbp = gridDim.x;
+    if (mask && !mask[pb]) return;
+    if (threadIdx.x < nv) hs[threadIdx.x] = sign * h[pb * SEG_STRIDE + threadIdx.x];
+    __syncthreads();
+    const Seg sg = segs[pb];
+    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < sg.len; g += (long long)nbp * NT) {
+        const long long x = sg.ofs + g;
+        double acc = w[x];
+        for (int v = 0; v < nv; ++v) acc += hs[v] * V[(long long)v * ld + x];
+        w[x] = acc;
+    }
+}
+
+// dst = sign * src / sqrt(n2[p*32]) (n2 null: dst = sign * src) on each segment.
+__global__ void __launch_bounds__(NT) k_seg_scale(const Seg* __restrict__ segs, const int* __restrict__ mask,
+                                                  const double* src, const double* __restrict__ n2, double sign,
+                                                  double* dst) {
+    const int pb = blockIdx.y, nbp = gridDim.x;
+    if (mask && !mask[pb]) return;
+    const double s = n2 ? sign / sqrt(n2[pb * SEG_STRIDE]) : sign;
+    const Seg sg = segs[pb];
+    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < sg.len; g += (long long)nbp * NT)
+        dst[sg.ofs + g] = s * src[sg.ofs + g];
+}
+
+// out = fma(alpha, d, x) on each segment.
+__global__ void __launch_bounds__(NT) k_seg_add_scaled(const Seg* __restrict__ segs, const int* __restrict__ mask,
+                                                       const double* x, const double* d, double alpha,
+                                                       double* out) {
+    const int pb = blockIdx.y, nbp = gridDim.x;
+    if (mask && !mask[pb]) return;
+    const Seg sg = segs[pb];
+    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < sg.len; g += (long long)nbp * NT)
+        out[sg.ofs + g] = fma(alpha, d[sg.ofs + g], x[sg.ofs + g]);
+}
+
+}  // namespace
+
+cudaError_t launch_seg_dot(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask, const double* V,
+                           long long ld, int nv, const double* w, double* partials) {
+    count_launch();
+    const dim3 grid(nbp, nprob);
+    switch (nv) {
+#define RAS_SEG_CASE(K) \
+    case K: k_seg_dot<K><<<grid, NT, 0, st>>>(segs, mask, V, ld, nv, w, partials); break;
+        RAS_SEG_CASE(1) RAS_SEG_CASE(2) RAS_SEG_CASE(3) RAS_SEG_CASE(4) RAS_SEG_CASE(5) RAS_SEG_CASE(6)
+        RAS_SEG_CASE(7) RAS_SEG_CASE(8) RAS_SEG_CASE(9) RAS_SEG_CASE(10) RAS_SEG_CASE(11) RAS_SEG_CASE(12)
+        RAS_SEG_CASE(13) RAS_SEG_CASE(14) RAS_SEG_CASE(15) RAS_SEG_CASE(16) RAS_SEG_CASE(17) RAS_SEG_CASE(18)
+        RAS_SEG_CASE(19) RAS_SEG_CASE(20) RAS_SEG_CASE(21) RAS_SEG_CASE(22) RAS_SEG_CASE(23) RAS_SEG_CASE(24)
+        RAS_SEG_CASE(25) RAS_SEG_CASE(26) RAS_SEG_CASE(27) RAS_SEG_CASE(28) RAS_SEG_CASE(29) RAS_SEG_CASE(30)
+        RAS_SEG_CASE(31) RAS_SEG_CASE(32)
+#undef RAS_SEG_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_reduce(cudaStream_t st, int nprob, int nbp, const int* mask, int nv, const double* partials,
+                              double* out) {
+    if (nv < 1 || nv > SEG_STRIDE) return cudaErrorInvalidValue;
+    count_launch();
+    k_seg_reduce<<<dim3(nv, nprob), NT, 0, st>>>(nbp, mask, partials, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_axpy(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask, const double* V,
+                            long long ld, int nv, const double* h, double sign, double* w) {
+    if (nv < 1 || nv > SEG_STRIDE) return cudaErrorInvalidValue;
+    count_launch();
+    k_seg_axpy<<<dim3(nbp, nprob), NT, 0, st>>>(segs, mask, V, ld, nv, h, sign, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_scale(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask,
+                             const double* src, const double* n2, double sign, double* dst) {
+    count_launch();
+    k_seg_scale<<<dim3(nbp, nprob), NT, 0, st>>>(segs, mask, src, n2, sign, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_add_scaled(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask,
+                                  const double* x, const double* d, double alpha, double* out) {
+    count_launch();
+    k_seg_add_scaled<<<dim3(nbp, nprob), NT, 0, st>>>(segs, mask, x, d, alpha, out);
+    return cudaGetLastError();
+}
+
+namespace {
 }  // namespace
 
 cudaError_t launch_residual_global(cudaStream_t st, const ProbDev& P, const double* y, const double* p,

@@ -314,13 +314,14 @@ __global__ void __launch_bounds__(NT) k_local_jvp(int nsub, const SubDev* __rest
                                                   const ProbDev* __restrict__ probs, const T* gpool, T* wpool,
                                                   const double* coef, double* zpool, double* rpool,
                                                   double* bpool, int nir, const double* D, double* O,
-                                                  int* err) {
+                                                  const int* pmask, int* err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ T vec[MAX_M], tmp[MAX_M];
     __shared__ double red[2 * NT];
     const int i = blockIdx.x;
     if (i >= nsub) return;
     const SubDev s = subs[i];
+    if (pmask && !pmask[s.prob]) return;
     const ProbDev P = probs[s.prob];
     const int n = P.n, m = 2 * s.wx, W = s.wy;
     const long long nn = (long long)n * n;
@@ -435,14 +436,14 @@ template <typename T>
 cudaError_t launch_local_jvp(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                              const ProbDev* probs, const T* gpool, T* wpool, const double* coef,
                              double* zpool, double* rpool, double* bpool, int nir, const double* D,
-                             double* O, int* err) {
+                             double* O, const int* pmask, int* err) {
     (void)maxm;
     const size_t sm = solve_smem<T>();
     cudaError_t e = set_smem(k_local_jvp<T>, sm);
     if (e != cudaSuccess) return e;
     count_launch();
     k_local_jvp<T><<<nsub, NT, sm, st>>>(nsub, subs, probs, gpool, wpool, coef, zpool, rpool, bpool, nir, D, O,
-                                         err);
+                                         pmask, err);
     return cudaGetLastError();
 }
 
@@ -465,7 +466,7 @@ cudaError_t launch_local_precond(cudaStream_t st, int nsub, int maxm, const SubD
                                                    const double*, double*, double*, T*, int*);                 \
     template cudaError_t launch_local_jvp<T>(cudaStream_t, int, int, const SubDev*, const ProbDev*, const T*,  \
                                              T*, const double*, double*, double*, double*, int,                \
-                                             const double*, double*, int*);                                    \
+                                             const double*, double*, const int*, int*);                        \
     template cudaError_t launch_local_precond<T>(cudaStream_t, int, int, const SubDev*, const ProbDev*,        \
                                                  const T*, T*, const double*, double*, int*);
 RAS_INSTANTIATE(float)

@@ -57,6 +57,12 @@ class ras_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ras_problem_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("sx", ctypes.c_int), ("sy", ctypes.c_int), ("overlap", ctypes.c_int),
+                ("phi", ctypes.c_int), ("nu", ctypes.c_double), ("mu", ctypes.c_double),
+                ("y_d", ctypes.c_void_p), ("f", ctypes.c_void_p)]
+
+
 class RasError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("ras error %d: %s" % (code, msg))
@@ -69,6 +75,10 @@ _I = ctypes.c_int
 _SIGS = {
     "ras_default_opts": (_I, [ctypes.POINTER(ras_opts)]),
     "ras_create": (_I, [_I, _I, _I, _I, _I, _D, _D, _P, _P, ctypes.POINTER(ras_opts), _P, ctypes.POINTER(_P)]),
+    "ras_batch_create": (_I, [_I, ctypes.POINTER(ras_problem_desc), ctypes.POINTER(ras_opts), _P,
+                              ctypes.POINTER(_P)]),
+    "ras_problem_count": (_I, [_P]),
+    "ras_batch_raspen_solve": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(ras_stats)]),
     "ras_set_eps": (_I, [_P, _D]),
     "ras_set_opts": (_I, [_P, ctypes.POINTER(ras_opts)]),
     "ras_set_data": (_I, [_P, _P, _P]),
@@ -164,6 +174,51 @@ def ras_create(n, sx, sy, overlap, phi, nu, mu, y_d, f=None, opts=None, stream=N
     if rc != RAS_OK:
         raise RasError(rc, "ras_create failed")
     return Handle(out, n)
+
+
+class BatchHandle(Handle):
+    """Handle of a batch: ns = grid sizes of its problems."""
+
+    def __init__(self, ptr, ns):
+        super().__init__(ptr, None)
+        self.ns = list(ns)
+
+
+def ras_batch_create(problems, opts=None, stream=None):
+    """problems: list of dicts with n, sx, sy, overlap, phi, nu, mu, y_d (CUDA
+    float64 tensor, n*n) and optionally f."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    arr = (ras_problem_desc * len(problems))()
+    for k, d in enumerate(problems):
+        n = d["n"]
+        arr[k].n, arr[k].sx, arr[k].sy, arr[k].overlap, arr[k].phi = n, d["sx"], d["sy"], d["overlap"], d["phi"]
+        arr[k].nu, arr[k].mu = d["nu"], d["mu"]
+        arr[k].y_d = _ptr(d["y_d"], n * n)
+        arr[k].f = _ptr(d.get("f"), n * n)
+    out = ctypes.c_void_p()
+    rc = lib().ras_batch_create(len(problems), arr, ctypes.byref(opts) if opts is not None else None,
+                                ctypes.c_void_p(stream), ctypes.byref(out))
+    if rc != RAS_OK:
+        raise RasError(rc, "ras_batch_create failed")
+    return BatchHandle(out, [d["n"] for d in problems])
+
+
+def ras_problem_count(h):
+    return lib().ras_problem_count(h.ptr)
+
+
+def ras_batch_raspen_solve(h, ys, ps, check=True):
+    """Solve every problem of the batch; ys, ps: lists of CUDA tensors."""
+    k = len(h.ns)
+    Y = (_P * k)(*[_ptr(y, n * n) for y, n in zip(ys, h.ns)])
+    Pp = (_P * k)(*[_ptr(p, n * n) for p, n in zip(ps, h.ns)])
+    st = (ras_stats * k)()
+    rc = lib().ras_batch_raspen_solve(h.ptr, Y, Pp, st)
+    if check:
+        h._check(rc)
+    return rc, list(st)
 
 
 def ras_set_eps(h, eps_min):
