@@ -416,42 +416,132 @@ __device__ __forceinline__ void store_vec(float* dst, const float* v) {
     if (R % 2) dst[R - 1] = v[R - 1];
 }
 
-// FP32 factorisation with the block held in registers. Thread (ty, tx) of a
-// 16 x 16 CTA owns the R x R tile of rows ty*R + a and columns tx*R + b of the
-// 16R x 16R block, so every elimination step updates registers only. Step k
-// (k = kt*R + kb: owner kt, register index kb) publishes column k (owners
-// tx == kt) and row k (owners ty == kt) in shared memory as 16-byte vectors
-// (double-buffered), then one barrier, then the rank-1 update.
+// Entries of D_j (grid row j of the local Jacobian) inside the tile of
+// thread (ty, ty + DT): the 2 x 2 node blocks on the diagonal (4 beta + phi',
+// the control coupling (1/nu)(1 - P_eps'(-p/mu)) in the y-row and
+// phi'' p - 1 in the p-row) and -beta two places off it (the x-neighbours of
+// the same field). R is even, so a row's field is a & 1.
+template <int R, int DT>
+__device__ __forceinline__ void add_band(float (&Mr)[R][R], int ty, int m, int wx, int j, float tdiag,
+                                         float tbeta, const double* ca, const double* cb, const double* cc) {
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+#pragma unroll
+        for (int b = 0; b < R; ++b) {
+            const int off = DT * R + b - a;
+            if (off < -2 || off > 2) continue;
+            const int r = ty * R + a, c = r + off;
+            if (r >= m || c < 0 || c >= m) continue;
+            const int q = j * wx + (r >> 1);
+            if (off == 0) Mr[a][b] += tdiag + (float)ca[q];
+            else if (off == 1 && (a & 1) == 0) Mr[a][b] += (float)cb[q];
+            else if (off == -1 && (a & 1) == 1) Mr[a][b] += (float)cc[q];
+            else if (off == 2 || off == -2) Mr[a][b] -= tbeta;
+        }
+    }
+}
+
+// The single-pivot Gauss-Jordan sweeps k = kt*R .. kt*R+R-1 restricted to the
+// column panel M[:, K], run by its 16 owners (thread column kt: one half of a
+// warp, lanes in the mask hm) on their own tiles, so the panel never leaves
+// registers. The pivot rows sit in thread (kt, kt) = lane src. Partial
+// pivoting is checked, not applied: every lane notes a row not yet
+// eliminated (rows of thread rows > kt, and rows after the pivot in thread
+// row kt) whose entry in the pivot column is larger than the diagonal, or a
+// diagonal that is 0 or not finite; the owners vote once at the end, and
+// false means the caller redoes the block row with pivoting.
+template <int R>
+__device__ __forceinline__ bool panel_sweep(float (&Mr)[R][R], int ty, int kt, int m, unsigned hm, int src) {
+    const int nk = min(R, m - kt * R);
+    bool bad = false;
+#pragma unroll
+    for (int kl = 0; kl < R; ++kl) {
+        if (kl >= nk) break;
+        float t[R];
+#pragma unroll
+        for (int c = 0; c < R; ++c) t[c] = __shfl_sync(hm, Mr[kl][c], src);
+        const float d = t[kl], ad = fabsf(d);
+        bad |= !(ad > 0.f && ad < INFINITY);
+        {
+            // largest candidate of this lane: all its rows below thread row
+            // kt, the rows after the pivot in thread row kt, none above
+            float mpart = 0.f;
+#pragma unroll
+            for (int a = kl + 1; a < R; ++a) mpart = fmaxf(mpart, fabsf(Mr[a][kl]));
+            float mall = mpart;
+#pragma unroll
+            for (int a = 0; a <= kl; ++a) mall = fmaxf(mall, fabsf(Mr[a][kl]));
+            const float cand = (ty > kt) ? mall : ((ty == kt) ? mpart : 0.f);
+            bad |= cand > ad;
+        }
+        const float inv = __frcp_rn(d);
+#pragma unroll
+        for (int c = 0; c < R; ++c) t[c] = (c == kl) ? inv : t[c] * inv;
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            const float f = Mr[a][kl];
+            Mr[a][kl] = 0.f;
+#pragma unroll
+            for (int c = 0; c < R; ++c) Mr[a][c] = fmaf(-f, t[c], Mr[a][c]);
+        }
+        if (ty == kt) {
+#pragma unroll
+            for (int c = 0; c < R; ++c) Mr[kl][c] = t[c];
+        }
+    }
+    return !__any_sync(hm, bad);
+}
+
+// FP32 factorisation, one CTA per subdomain. Thread (ty, tx) of the 16 x 16
+// CTA (tid = 16 tx + ty: a thread column is one half of a warp) holds the
+// R x R tile (rows ty*R + a, columns tx*R + b) of the block row matrix in
+// registers for the whole launch: S_j = D_j - beta^2 G_{j-1} is formed in
+// place from G_{j-1} (the same tile), inverted in place and written out
+// (staged through shared memory in the packed order).
+//
+// The inverse is the Gauss-Jordan sweep over the pivots k = 0 .. m-1, taken
+// R at a time: panel K = kt*R .. kt*R+R-1 holds the columns of thread column
+// kt and the rows of thread row kt. With A = M[K,K], sweeping the pivots of K
+// gives M[:,K] <- C' = [A^-1; -M[I,K] A^-1] (the column panel after its R
+// single-pivot sweeps) and, for every other column J,
+//   M[K,J] <- C'[K,K] M[K,J],   M[I,J] <- M[I,J] + C'[I,K] M[K,J].
+// Per panel: the 16 owners of column kt sweep it in their registers
+// (panel_sweep) and publish C'; the owners of row kt publish M[K,:] with
+// zeros in place of M[K,K] and clear their tiles; after one barrier every
+// thread adds the rank-R product of the two, which leaves the column panel
+// at C' and turns rows K into C'[K,K] M[K,J]. The panel buffers alternate
+// between two copies, so one barrier per panel suffices.
 //
 // Partial pivoting (max |.| in the column among the rows not yet eliminated,
-// ties to the lowest row) is applied optimistically: every step each warp
-// checks 20 candidate rows against the diagonal and raises a flag when one is
-// larger. A block row that raised the flag is redone from its Schur complement
-// by a shared-memory Gauss-Jordan elimination with full partial pivoting; a
-// block row that did not is exactly what partial pivoting computes.
-//
-// G_{j-1} stays in shared memory (natural order) as the source of the next
-// Schur complement and of the coalesced write-out in packed order.
+// ties to the lowest row) is optimistic: a block row whose diagonal pivots
+// all pass the check is exactly what partial pivoting computes; one that
+// fails is redone from S_j (G_{j-1} read back from the factor pool) by a
+// shared-memory Gauss-Jordan elimination with partial pivoting.
 template <int R>
-__global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_reg(int nsub, const SubDev* __restrict__ subs,
-                                                                      const ProbDev* __restrict__ probs,
-                                                                      const double* X, LocalState* ls,
-                                                                      const double* cpool, double* coef,
-                                                                      float* gpool, int only_active,
-                                                                      const int* __restrict__ list) {
+__global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub, const SubDev* __restrict__ subs,
+                                                                        const ProbDev* __restrict__ probs,
+                                                                        const double* X, LocalState* ls,
+                                                                        const double* cpool, double* coef,
+                                                                        float* gpool, int only_active,
+                                                                        const int* __restrict__ list) {
     constexpr int MM = 16 * R;
-    constexpr int PAD = ((R + 3) / 4) * 4;   // owner stride in the broadcast buffers
+    constexpr int PAD = ((R + 3) / 4) * 4;   // owner stride in the panel buffers
+    constexpr int LDC = 16 * PAD;            // one panel column (or row) of 16 owners
+    constexpr int LDS = MM + 4;              // staging stride of the full block
     static_assert(FACT_THREADS == 256, "16 x 16 thread tile");
-    static_assert(16 * PAD >= MM, "broadcast buffers hold a full column");
-    __shared__ __align__(16) float colk[2][16 * PAD];
-    __shared__ __align__(16) float rowb[2][16 * PAD];
+    static_assert(R % 2 == 0, "one field per row parity");
+    // panel buffers inside the staging area (dead while the panels run):
+    // two copies each of the swept column panel (transposed) and the row panel
+    constexpr int OFF_CT = 0;
+    constexpr int OFF_RW = OFF_CT + 2 * R * LDC;
+    static_assert(OFF_RW + 2 * R * LDC <= MM * LDS, "panel buffers fit in the staging area");
+    __shared__ float fcol[MM];
     __shared__ int pivr[MM];
     __shared__ int sinv[MM];
     __shared__ int used[MM];
     __shared__ int sh_viol, sh_r, sh_fail;
     __shared__ float sh_piv;
     extern __shared__ __align__(16) float Ms[];
-    constexpr int LDS = MM + 4;
     if ((int)blockIdx.x >= nsub) return;
     const int i = list ? list[blockIdx.x] : (int)blockIdx.x;
     if (only_active && !ls[i].active) return;
@@ -459,7 +549,7 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_reg(int nsub, 
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
     const int m = 2 * s.wx, W = s.wy, nn = s.wx * s.wy, mp = s.mp;
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, ty = tid & 15, tx = tid >> 4, warp = tid >> 5, lane = tid & 31;
 
     const double eps = ls[i].eps;
     const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu;
@@ -479,19 +569,18 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_reg(int nsub, 
             cc[q] = d2 * p - 1.0;
         }
     }
-    for (int t = tid; t < 16 * PAD; t += FACT_THREADS) {
-        colk[0][t] = colk[1][t] = 0.f;
-        rowb[0][t] = rowb[1][t] = 0.f;
-    }
     if (tid == 0) sh_fail = 0;
-    __syncthreads();
+    __syncthreads();   // coefficients visible to the whole CTA
 
     const float tbeta = (float)beta, tbeta2 = (float)(beta * beta), tdiag = (float)(4.0 * beta);
     const long long blk = (long long)mp * mp;
     float* G = gpool + s.goff;
     float Mr[R][R];
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int b = 0; b < R; ++b) Mr[a][b] = 0.f;
     bool failed = false;
-    // entry (r, c) of the diagonal block D_j (one grid row of the local Jacobian)
     auto dval = [=](int j, int r, int c) -> float {
         const int ix = r >> 1, f = r & 1, cx = c >> 1, cf = c & 1;
         const int q = j * s.wx + ix;
@@ -501,84 +590,91 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_reg(int nsub, 
         }
         return (cf == f && (cx == ix - 1 || cx == ix + 1)) ? -tbeta : 0.f;
     };
-    // shared-buffer slot of row (or column) index i: owner i / R, register i % R
-    auto slot = [](int i) { return (i / R) * PAD + (i % R); };
     for (int j = 0; j < W && !failed; ++j) {
-        // S_j = D_j - beta^2 G_{j-1}
+        // S_j = D_j - beta^2 G_{j-1}: the tile holds G_{j-1} (zero for j = 0)
 #pragma unroll
-        for (int a = 0; a < R; ++a) {
-            const int r = ty * R + a;
+        for (int a = 0; a < R; ++a)
 #pragma unroll
-            for (int b = 0; b < R; ++b) {
-                const int c = tx * R + b;
-                float v = 0.f;
-                if (r < m && c < m) {
-                    if (j > 0) v = -tbeta2 * Ms[r * LDS + c];
-                    v += dval(j, r, c);
-                }
-                Mr[a][b] = v;
-            }
-        }
+            for (int b = 0; b < R; ++b) Mr[a][b] = -tbeta2 * Mr[a][b];
+        if (tx == ty) add_band<R, 0>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
+        else if (tx == ty + 1) add_band<R, 1>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
+        else if (tx == ty - 1) add_band<R, -1>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
         if (tid == 0) sh_viol = 0;
-        int par = 0;
-        bool done = false;
-        for (int kt = 0; kt < 16 && !done; ++kt) {
-#pragma unroll
-            for (int kb = 0; kb < R; ++kb) {
-                const int k = kt * R + kb;
-                if (k >= m) {
-                    done = true;
-                    break;
-                }
-                float* cbuf = colk[par];
-                float* rbuf = rowb[par];
+
+        for (int kt = 0; kt < 16 && kt * R < m; ++kt) {
+            float* CsT = Ms + OFF_CT + (kt & 1) * (R * LDC);
+            float* Rw = Ms + OFF_RW + (kt & 1) * (R * LDC);
+            if (ty == kt) {
                 if (tx == kt) {
+#pragma unroll
+                    for (int c = 0; c < R; ++c) {
+                        float z[R];
+#pragma unroll
+                        for (int b = 0; b < R; ++b) z[b] = 0.f;
+                        store_vec<R>(Rw + c * LDC + tx * PAD, z);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < R; ++c) store_vec<R>(Rw + c * LDC + tx * PAD, Mr[c]);
+                }
+                // rows K restart from 0: the update below leaves C'[K,K] M[K,J]
+                // there (forming it as M[K,J] + (C'[K,K] - I) M[K,J] would
+                // cancel catastrophically, since C'[K,K] ~ 1/(4 beta))
+                if (tx != kt) {
+#pragma unroll
+                    for (int a = 0; a < R; ++a)
+#pragma unroll
+                        for (int b = 0; b < R; ++b) Mr[a][b] = 0.f;
+                }
+            }
+            if (tx == kt) {
+                const int half = kt & 1;
+                const unsigned hm = 0xffffu << (16 * half);
+                const bool ok = panel_sweep<R>(Mr, ty, kt, m, hm, 16 * half + kt);
+                if (!ok && ty == 0) sh_viol = 1;
+#pragma unroll
+                for (int c = 0; c < R; ++c) {
                     float col[R];
 #pragma unroll
-                    for (int a2 = 0; a2 < R; ++a2) col[a2] = Mr[a2][kb];
-                    store_vec<R>(cbuf + ty * PAD, col);
+                    for (int a = 0; a < R; ++a) col[a] = Mr[a][c];
+                    store_vec<R>(CsT + c * LDC + ty * PAD, col);
                 }
-                if (ty == kt) store_vec<R>(rbuf + tx * PAD, Mr[kb]);
-                __syncthreads();
-                const float piv = cbuf[kt * PAD + kb];
-                {
-                    // optimistic partial-pivoting check: warp w, rows k+1+20w ..
-                    const int r = k + 1 + 20 * warp + lane;
-                    const float dg = fabsf(piv);
-                    bool viol = (lane < 20 && r < m && fabsf(cbuf[slot(r)]) > dg);
-                    if (tid == 0 && !(dg > 0.f && dg < INFINITY)) viol = true;
-                    if (viol) sh_viol = 1;
+            }
+            __syncthreads();
+            if (sh_viol) break;
+            // rank-R update M += C' [M[K,:] with 0 at K]
+#pragma unroll
+            for (int c = 0; c < R; ++c) {
+                float rv[R];
+                load_vec<R>(Rw + c * LDC + tx * PAD, rv);
+                const float* cp = CsT + c * LDC + ty * PAD;
+                // the column operand four rows at a time (fewer live registers)
+#pragma unroll
+                for (int a0 = 0; a0 < R; a0 += 4) {
+                    float cv[4];
+                    if (a0 + 4 <= R) {
+                        const float4 t4 = *reinterpret_cast<const float4*>(cp + a0);
+                        cv[0] = t4.x; cv[1] = t4.y; cv[2] = t4.z; cv[3] = t4.w;
+                    } else {
+                        const float2 t2 = *reinterpret_cast<const float2*>(cp + a0);
+                        cv[0] = t2.x; cv[1] = t2.y; cv[2] = 0.f; cv[3] = 0.f;
+                    }
+#pragma unroll
+                    for (int a = a0; a < a0 + 4 && a < R; ++a)
+#pragma unroll
+                        for (int b = 0; b < R; ++b) Mr[a][b] = fmaf(cv[a - a0], rv[b], Mr[a][b]);
                 }
-                const float inv = __frcp_rn(piv);
-                float ck[R], rb[R];
-                load_vec<R>(cbuf + ty * PAD, ck);
-                load_vec<R>(rbuf + tx * PAD, rb);
-#pragma unroll
-                for (int b = 0; b < R; ++b) rb[b] *= inv;
-                if (tx == kt) {
-                    rb[kb] = inv;
-#pragma unroll
-                    for (int a2 = 0; a2 < R; ++a2) Mr[a2][kb] = 0.f;
-                }
-#pragma unroll
-                for (int a2 = 0; a2 < R; ++a2)
-#pragma unroll
-                    for (int b = 0; b < R; ++b) Mr[a2][b] = fmaf(-ck[a2], rb[b], Mr[a2][b]);
-                if (ty == kt) {
-#pragma unroll
-                    for (int b = 0; b < R; ++b) Mr[kb][b] = rb[b];
-                }
-                par ^= 1;
             }
         }
-        __syncthreads();
+        __syncthreads();   // the panel buffers are dead before the staging area is reused
         if (sh_viol) {
             // Redo this block row with partial pivoting in shared memory:
-            // S_j in place of G_{j-1}, implicit pivoting (rows never move),
-            // then G_j[r][c] = M[perm[r]][rinv[c]].
+            // S_j from G_{j-1} (in the factor pool) and D_j, implicit
+            // pivoting (rows never move), then G_j[r][c] = M[perm[r]][rinv[c]].
+            const float* Gp = G + (long long)(j > 0 ? j - 1 : 0) * blk;
             for (int idx = tid; idx < m * m; idx += FACT_THREADS) {
                 const int r = idx / m, c = idx - r * m;
-                float v = (j > 0) ? -tbeta2 * Ms[r * LDS + c] : 0.f;
+                const float v = (j > 0) ? -tbeta2 * Gp[packed_index<float>(r, c, mp)] : 0.f;
                 Ms[r * LDS + c] = v + dval(j, r, c);
             }
             for (int t = tid; t < m; t += FACT_THREADS) used[t] = 0;
@@ -610,13 +706,13 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_reg(int nsub, 
                 if (sh_fail) break;
                 const int r = sh_r;
                 const float inv = 1.f / sh_piv;
-                for (int t = tid; t < m; t += FACT_THREADS) colk[0][t] = Ms[t * LDS + k];
+                for (int t = tid; t < m; t += FACT_THREADS) fcol[t] = Ms[t * LDS + k];
                 __syncthreads();
                 for (int t = tid; t < m; t += FACT_THREADS) Ms[r * LDS + t] = (t == k ? 1.f : Ms[r * LDS + t]) * inv;
                 __syncthreads();
                 for (int idx = tid; idx < m * m; idx += FACT_THREADS) {
                     const int rr = idx / m, t = idx - rr * m;
-                    if (rr != r) Ms[rr * LDS + t] = (t == k ? 0.f : Ms[rr * LDS + t]) - colk[0][rr] * Ms[r * LDS + t];
+                    if (rr != r) Ms[rr * LDS + t] = (t == k ? 0.f : Ms[rr * LDS + t]) - fcol[rr] * Ms[r * LDS + t];
                 }
                 __syncthreads();
             }
@@ -685,14 +781,14 @@ cudaError_t launch_local_init(cudaStream_t st, int nsub, const SubDev* subs, con
 }
 
 template <int R>
-cudaError_t launch_factor_reg(cudaStream_t st, int count, const SubDev* subs, const ProbDev* probs,
+cudaError_t launch_factor_panel(cudaStream_t st, int count, const SubDev* subs, const ProbDev* probs,
                               const double* X, LocalState* ls, const double* cpool, double* coef,
                               float* gpool, int only_active, const int* list) {
     const size_t sm = (size_t)(16 * R) * (16 * R + 4) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_local_factor_reg<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_local_factor_panel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_local_factor_reg<R><<<count, FACT_THREADS, sm, st>>>(count, subs, probs, X, ls, cpool, coef, gpool,
+    k_local_factor_panel<R><<<count, FACT_THREADS, sm, st>>>(count, subs, probs, X, ls, cpool, coef, gpool,
                                                            only_active, list);
     return cudaGetLastError();
 }
@@ -701,11 +797,11 @@ cudaError_t launch_local_factor_f32(cudaStream_t st, int tile, int count, const 
                                     const ProbDev* probs, const double* X, LocalState* ls, const double* cpool,
                                     double* coef, float* gpool, int only_active) {
     switch (tile) {
-        case 2: return launch_factor_reg<2>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
-        case 4: return launch_factor_reg<4>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
-        case 6: return launch_factor_reg<6>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
-        case 8: return launch_factor_reg<8>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
-        case 10: return launch_factor_reg<10>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+        case 2: return launch_factor_panel<2>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+        case 4: return launch_factor_panel<4>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+        case 6: return launch_factor_panel<6>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+        case 8: return launch_factor_panel<8>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+        case 10: return launch_factor_panel<10>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
         default: return cudaErrorInvalidValue;
     }
 }
