@@ -36,6 +36,15 @@ SM_MAX_MHZ = 2070.0
 FP32_LANES = 128     # FP32 FMA lanes per SM
 FP64_LANES = 2       # FP64 FMA per clock per SM on GB300 (1.2 TFLOP/s class)
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of the n1023 workload (profiles/dram_jvp_n1023.md), valid
+# while the kernel's sources are unchanged since that capture.
+TRAFFIC = {"jvp": {"bytes_per_launch": 8562495616.0, "workload": "n1023",
+                   "sources": ["paper_2411_00546_gb300/csrc/solve.cu",
+                               "paper_2411_00546_gb300/csrc/ras_internal.cuh"],
+                   "sha256": ["588457ff564180912d912e96443a5d2758f6e12796525f8f11a4079dcff6e691",
+                              "89a36b8d2a40fc2d51bf5f808a87799d0ea8420f60056fb72de9c77aec0c43be"]}}
+
 # Counts of one RASPEN_eps solve (see run_reference).
 SOLVE_COUNTS = {"n1023": {"inner_its_sum": 1794, "evaluations": 3, "gmres_its": 147}}
 
@@ -49,6 +58,128 @@ def field_err(a, b, other):
     return float(np.abs(a - b).max() / scale)
 
 
+def traffic_for(kind, workload):
+    """Captured DRAM bytes per launch of `kind`, or None when there is no
+    capture for this workload or the kernel's sources changed since."""
+    import hashlib
+    t = TRAFFIC.get(kind)
+    if t is None or t["workload"] != workload:
+        return None
+    for path, sha in zip(t["sources"], t["sha256"]):
+        try:
+            with open(os.path.join(ROOT, path), "rb") as fh:
+                if hashlib.sha256(fh.read()).hexdigest() != sha:
+                    return None
+        except OSError:
+            return None
+    return t["bytes_per_launch"]
+
+
+def measure_batch(ras, torch, dev, stream):
+    """Uneven batch (64 independent problems, seed 4): one batched RASPEN solve
+    in mixed precision, timed with CUDA events after one warm-up solve, and
+    the same problems solved one after another in their own handles; the
+    results of the two agree to the mixed tolerance (reported)."""
+    import numpy as np
+    from paper_2411_00546_gb300 import inputs
+    cfgs = inputs.uneven_batch()
+    o = ras.make_opts(precision=ras.RAS_MIXED, eps0=0.1, gamma=0.1, eps_min=1e-6, tol=1e-10, inner_tol=1e-8,
+                      sigma=1.1)
+    yds = [torch.tensor(inputs.make_yd(c), dtype=torch.float64, device=dev) for c in cfgs]
+    probs = [dict(n=c["n"], sx=c["sx"], sy=c["sy"], overlap=c["overlap"], phi=c["phi"], nu=c["nu"], mu=c["mu"],
+                  y_d=yd) for c, yd in zip(cfgs, yds)]
+    h = ras.ras_batch_create(probs, o, stream=stream.cuda_stream)
+    ys = [torch.zeros((c["n"], c["n"]), dtype=torch.float64, device=dev) for c in cfgs]
+    ps = [torch.zeros_like(y) for y in ys]
+
+    def solve():
+        with torch.cuda.stream(stream):
+            for y, p in zip(ys, ps):
+                y.zero_()
+                p.zero_()
+        return ras.ras_batch_raspen_solve(h, ys, ps, check=False)
+
+    solve()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc, st = solve()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    bytes_ = ras.ras_device_bytes(h)
+    ras.ras_destroy(h)
+    seq_ms, err = 0.0, 0.0
+    for k, c in enumerate(cfgs):
+        h1 = ras.ras_create(c["n"], c["sx"], c["sy"], c["overlap"], c["phi"], c["nu"], c["mu"], yds[k], None, o,
+                            stream=stream.cuda_stream)
+        y1 = torch.zeros_like(ys[k])
+        p1 = torch.zeros_like(ys[k])
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ras.ras_raspen_solve(h1, y1, p1, check=False)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        seq_ms += a.elapsed_time(b)
+        ras.ras_destroy(h1)
+        yb, pb, ya, pa = (t.cpu().numpy() for t in (ys[k], ps[k], y1, p1))
+        err = max(err, field_err(yb, ya, pa), field_err(pb, pa, ya))
+    return {"workload": "64 problems, n ~ U{63,127,255,511}, mu ~ logU[1e-4,1e-2], nu ~ logU[1e-6,1e-3], "
+                        "phi ~ U{y^3, exp}, block 32..64, overlap 2..8, Fourier y_d seeds 1000+k (seed 4)",
+            "problems_per_s": len(cfgs) / (ms / 1e3), "ms": ms, "status": rc,
+            "outer_its_max": max(x.outer_its for x in st), "device_bytes": bytes_,
+            "sequential_problems_per_s": len(cfgs) / (seq_ms / 1e3), "sequential_ms": seq_ms,
+            "max_err_batched_vs_alone": err}
+
+
+def measure_serving(ras, torch, dev, stream, count):
+    """Serving: the first `count` requests of the Poisson stream (lambda = 200/s,
+    seed 5, n ~ U{127,255,511,1023}) through the continuous-batching server
+    (HBM budget 150 GB, up to 64 admitted), mixed precision; p50/p99 latency
+    and solves/s. Baseline: the same requests solved one at a time in FP64 in
+    arrival order (a single FIFO queue), from their measured solve times."""
+    from paper_2411_00546_gb300 import inputs, serve
+    stream_reqs = inputs.arrival_stream()[:count]
+    reqs = [(t, dict(n=c["n"], sx=c["sx"], sy=c["sy"], overlap=c["overlap"], phi=c["phi"], nu=c["nu"],
+                     mu=c["mu"], y_d=inputs.make_yd(c))) for t, c in stream_reqs]
+    base = dict(eps0=0.1, gamma=0.1, eps_min=1e-6, tol=1e-10, inner_tol=1e-8, sigma=1.1)
+    o = ras.make_opts(precision=ras.RAS_MIXED, **base)
+    serve.run_stream(reqs[:2], 150e9, 64, o, stream.cuda_stream)   # warm-up
+    out = serve.run_stream(reqs, 150e9, 64, o, stream.cuda_stream)
+    lat = list(out["latency_s"].values())
+    span = out["wall_s"] - out["first_arrival_s"]
+    res = {"workload": "first %d requests of the Poisson stream (lambda 200/s, seed 5), n ~ U{127,255,511,1023}, "
+                       "mu, nu, phi, y_d as the uneven batch" % count,
+           "budget_bytes": 150e9, "max_active": 64, "p50_ms": 1e3 * serve.percentile(lat, 50),
+           "p99_ms": 1e3 * serve.percentile(lat, 99), "solves_per_s": len(lat) / span, "steps": out["steps"],
+           "peak_active": out["peak_active"], "peak_device_bytes": out["peak_device_bytes"],
+           "all_ok": all(v == ras.RAS_OK for v in out["status"].values())}
+    # sequential FP64 baseline: one solve at a time, first come first served
+    o64 = ras.make_opts(precision=ras.RAS_FP64, **base)
+    t_free, seq_lat = 0.0, []
+    for (t, d), (_, c) in zip(reqs, stream_reqs):
+        yd = torch.tensor(d["y_d"], dtype=torch.float64, device=dev)
+        h = ras.ras_create(c["n"], c["sx"], c["sy"], c["overlap"], c["phi"], c["nu"], c["mu"], yd, None, o64,
+                           stream=stream.cuda_stream)
+        y = torch.zeros_like(yd)
+        p = torch.zeros_like(yd)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ras.ras_raspen_solve(h, y, p, check=False)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ras.ras_destroy(h)
+        start = max(t, t_free)
+        t_free = start + a.elapsed_time(b) / 1e3
+        seq_lat.append(t_free - t)
+    res["sequential_fp64"] = {"p50_ms": 1e3 * serve.percentile(seq_lat, 50),
+                              "p99_ms": 1e3 * serve.percentile(seq_lat, 99),
+                              "solves_per_s": len(seq_lat) / (t_free - reqs[0][0])}
+    return res
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -59,6 +190,9 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=32)
     return ap.parse_args()
 
 
@@ -332,6 +466,66 @@ def main():
                 e["gbs"] = round(kw / (kms / 1e3) / 1e9, 1)
         kernels[k] = e
 
+    # global residual kernel (Sec. 3.3 F at the solution): 20 launches, each
+    # after an L2 flush (its 42 MB working set would otherwise sit in L2)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    Fy = torch.empty_like(y)
+    Fp = torch.empty_like(y)
+    ras.ras_profile(h, 1)
+    for _ in range(20):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ras.ras_residual(h, y, p, cfg["eps_min"], Fy, Fp)
+    torch.cuda.synchronize(dev)
+    prof_res = ras.ras_profile_all(h)["residual"]
+    ras.ras_profile(h, 0)
+    del flush
+
+    clk = float(pk.get("sm_max_mhz", SM_MAX_MHZ)) * 1e6
+    fp32_peak = SM_COUNT * FP32_LANES * 2 * clk / 1e12
+    fp64_peak = SM_COUNT * FP64_LANES * 2 * clk / 1e12
+    hbm_peak = float(pk.get("hbm_gbs", FALLBACK_HBM_GBS))
+
+    def roof_entry(kind, ms, n, work):
+        if n == 0 or ms <= 0:
+            return None
+        if kind == "factor":
+            a = work / (ms / 1e3) / 1e12
+            return {"bound": "alu", "achieved": round(a, 3), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                    "frac": round(a / fp32_peak, 4), "avg_launch_ms": round(ms / n, 4), "launches": n,
+                    "work": "16 wx^3 wy flops per subdomain", "peak_source": "derived FP32 FMA rate"}
+        e = {"bound": "hbm", "achieved": round(work / (ms / 1e3) / 1e9, 1), "peak": hbm_peak, "unit": "GB/s",
+             "avg_launch_ms": round(ms / n, 4), "launches": n, "peak_source": src}
+        e["frac"] = round(e["achieved"] / hbm_peak, 4)
+        if kind == "krylov":
+            # one FP64 FMA per 8-byte basis element read: the FP64 pipe binds
+            a64 = 2.0 * (work / 8.0) / (ms / 1e3) / 1e12
+            e.update({"bound": "fp64", "fp64_achieved_tflops": round(a64, 3),
+                      "fp64_peak_tflops": round(fp64_peak, 3), "fp64_frac": round(a64 / fp64_peak, 4),
+                      "hbm_frac": e["frac"]})
+            e["frac"] = e["fp64_frac"]
+        return e
+
+    kernel_rooflines = {}
+    for k, (kms, kn, kw) in list(prof.items()) + [("residual", prof_res)]:
+        if k in ("other", "init", "linesearch"):
+            continue
+        r = roof_entry(k, kms, kn, kw)
+        if r is not None:
+            kernel_rooflines[k] = r
+    if "residual" in kernel_rooflines:
+        kernel_rooflines["residual"]["note"] = ("20 launches at the solution, L2 flushed before each; "
+                                                "40 B per node (y, p, y_d read, F_y, F_p written)")
+    if roof is not None:
+        roof["traffic"] = traffic_for(dom, args.workload)
+
+    batch = None
+    if not args.no_batch:
+        batch = measure_batch(ras, torch, dev, stream)
+    serving = None
+    if not args.no_serve:
+        serving = measure_serving(ras, torch, dev, stream, args.serve_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
@@ -364,7 +558,9 @@ def main():
                           "l2": "no flush: device working set %.2f GB (local factors, Krylov basis) far "
                                 "above the 129 MB L2" % (dev_bytes / 1e9),
                           "solve_stats": stats[-1], "fp64": fp64, "kernel_share": kernel_share,
-                          "kernels": kernels, "y_max": float(np.abs(y_mixed).max()),
+                          "kernels": kernels, "kernel_rooflines": kernel_rooflines,
+                          "uneven_batch": batch, "serving": serving,
+                          "y_max": float(np.abs(y_mixed).max()),
                           "p_max": float(np.abs(p_mixed).max())},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clocks.summary()}

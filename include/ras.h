@@ -158,6 +158,60 @@ int ras_problem_count(const ras_problem* h);
  * ras_raspen_solve take only handles with one problem (else RAS_EINVAL). */
 int ras_batch_raspen_solve(ras_problem* h, double* const* y, double* const* p, ras_stats* stats);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of RASPEN_eps solves (Alg. 2): requests of any size and
+ * any (nu, mu, phi, y_d, f) are submitted at any time; every ras_server_step
+ * admits waiting requests while the budget allows, then advances every
+ * admitted request by one outer iteration of Alg. 2 (evaluate the RASPEN
+ * function at x_k, with eps-continuation in the local solves when k = 0;
+ * test; GMRES and update when the test fails), with the local solves,
+ * Jacobian actions and Krylov vectors of all admitted requests in shared
+ * launches. A request's iterate x_k = (y, p) and data stay on the device
+ * between steps; a request whose test passes (or that fails) is finished
+ * and holds its result until fetched. Each request's sequence of operations
+ * is that of ras_raspen_solve on the problem alone (same x0 = 0, same
+ * options), so its result agrees with the solve alone to rounding.
+ *
+ * ras_server_create: hbm_budget = device bytes the server may hold (slot
+ *   storage of admitted and unfetched requests plus the batch workspace, by
+ *   the estimate of ras_server_request_bytes); max_active = most requests
+ *   advanced together (1..4096); o = options shared by all requests (NULL:
+ *   defaults); stream = cudaStream_t for all work. RAS_EINVAL on bad values.
+ * ras_server_request_bytes: host-only estimate for one request: slot bytes
+ *   (y, p, y_d, f) and workspace bytes. RAS_EINVAL for an invalid desc.
+ * ras_server_submit: desc as for ras_batch_create, but y_d and f are HOST
+ *   pointers (n*n doubles, copied before the call returns). Queues the
+ *   request (first come, first served); *id receives its id (> 0).
+ *   RAS_ENOMEM if the request alone exceeds the budget.
+ * ras_server_step: admission, then one outer iteration of every admitted
+ *   request; *active = requests still admitted after it, *finished = requests
+ *   that finished in it (either pointer may be NULL). With nothing admitted it
+ *   only admits. Returns RAS_OK, or RAS_ECUDA / RAS_ETIMEOUT (the server must
+ *   then be destroyed).
+ * ras_server_counts: requests waiting, admitted, finished and not fetched.
+ * ras_server_finished_ids: up to cap ids of finished requests, oldest first;
+ *   returns how many were written.
+ * ras_server_fetch: copies the result of finished request id to y_host,
+ *   p_host (n*n doubles each, either may be NULL) and its stats, frees its slot
+ *   and returns its status (RAS_OK or RAS_ENOCONV); RAS_EINVAL for an unknown
+ *   id. An idle server (nothing waiting or admitted) then releases its
+ *   workspace.
+ * ras_server_device_bytes: device bytes held now (workspace + slots).
+ * The paper has no serving loop: this is the benchmark spec's continuous-batching
+ * use of Alg. 2 and Alg. 3 over independent problems. */
+typedef struct ras_server ras_server;
+int ras_server_create(size_t hbm_budget, int max_active, const ras_opts* o, void* stream, ras_server** out);
+int ras_server_request_bytes(const ras_problem_desc* d, const ras_opts* o, size_t* slot_bytes,
+                             size_t* scratch_bytes);
+int ras_server_submit(ras_server* s, const ras_problem_desc* d, long long* id);
+int ras_server_step(ras_server* s, int* active, int* finished);
+int ras_server_counts(const ras_server* s, int* pending, int* active, int* finished);
+int ras_server_finished_ids(const ras_server* s, long long* ids, int cap);
+int ras_server_fetch(ras_server* s, long long id, double* y_host, double* p_host, ras_stats* st);
+size_t ras_server_device_bytes(const ras_server* s);
+const char* ras_server_last_error(const ras_server* s);
+void ras_server_destroy(ras_server* s);
+
 /* Set the target smoothing parameter eps_min (> 0; P_eps is not smooth at 0). */
 int ras_set_eps(ras_problem* h, double eps_min);
 

@@ -15,6 +15,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <deque>
 #include <string>
 #include <vector>
 
@@ -69,6 +70,12 @@ struct ras_problem {
     double* coefG = nullptr;
     double* partials = nullptr;
     int nbp = 0;                 // blocks per problem of the segmented kernels
+    // block tables of the segmented kernels, one per mask row (0: GMRES/JVP,
+    // 1: outer loop, 2: every problem), VEC_BLOCKS + nprob entries each
+    int2* d_tab = nullptr;
+    int* d_nbps = nullptr;       // 3 rows of nprob block counts
+    int ntab[3] = {0, 0, 0};
+    std::vector<int> last_mask[3];
     double* scal = nullptr;      // device scalars, 4 * 32 per problem
     double* h_scal = nullptr;    // pinned host scalars, same layout
     double* V = nullptr;
@@ -87,8 +94,10 @@ struct ras_problem {
     double prof_ms[RAS_K_COUNT] = {};
     long long prof_n[RAS_K_COUNT] = {};
     double prof_work[RAS_K_COUNT] = {};
-    std::vector<void*> allocs;
+    std::vector<std::pair<void*, size_t>> allocs;   // device allocations and their bytes
     size_t bytes = 0;
+    std::vector<int> h_lists;                       // host copy of d_lists
+    size_t cap_hscal = 0;                           // doubles in h_scal
     std::string err;
 };
 
@@ -163,16 +172,37 @@ int dalloc(ras_problem* h, T** p, size_t count) {
         cudaGetLastError();
         return fail(h, RAS_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
     }
-    h->allocs.push_back((void*)*p);
+    h->allocs.emplace_back((void*)*p, count * sizeof(T));
     h->bytes += count * sizeof(T);
     return RAS_OK;
 }
 
 void dfree(ras_problem* h, void* p) {
     if (!p) return;
-    auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
-    if (it != h->allocs.end()) h->allocs.erase(it);
+    for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it) {
+        if (it->first == p) {
+            h->bytes -= it->second;
+            h->allocs.erase(it);
+            break;
+        }
+    }
     cudaFree(p);
+}
+
+size_t dcap(const ras_problem* h, const void* p) {
+    for (const auto& a : h->allocs)
+        if (a.first == p) return a.second;
+    return 0;
+}
+
+// *p holds at least count elements afterwards (contents not kept on growth).
+template <class T>
+int ensure(ras_problem* h, T** p, size_t count) {
+    if (count == 0) count = 1;
+    if (*p && dcap(h, *p) >= count * sizeof(T)) return RAS_OK;
+    dfree(h, *p);
+    *p = nullptr;
+    return dalloc(h, p, count);
 }
 
 // Balanced split of range(n) into s blocks, the first (n mod s) one node larger.
@@ -216,16 +246,12 @@ NewtonParams inner_params(const ras_opts& o) {
 
 int alloc_factor_pools(ras_problem* h) {
     const int prec = h->o.precision;
-    if (h->gprec == prec) return RAS_OK;
-    dfree(h, h->gpool);
-    dfree(h, h->wpool);
-    h->gpool = h->wpool = nullptr;
     const size_t es = (prec == RAS_MIXED) ? sizeof(float) : sizeof(double);
-    char* g = nullptr;
-    char* w = nullptr;
-    TRY(dalloc(h, &g, (size_t)h->Gsum * es));
-    TRY(dalloc(h, &w, (size_t)h->Lsum * es));
+    char* g = static_cast<char*>(h->gpool);
+    char* w = static_cast<char*>(h->wpool);
+    TRY(ensure(h, &g, (size_t)h->Gsum * es));
     h->gpool = g;
+    TRY(ensure(h, &w, (size_t)h->Lsum * es));
     h->wpool = w;
     h->gprec = prec;
     return RAS_OK;
@@ -281,23 +307,63 @@ long long plane(const ras_problem* h, int p) { return (long long)h->probs[p].n *
 
 double resid_bytes(const ras_problem* h) { return (h->f ? 48.0 : 40.0) * (double)plane(h, 0); }
 
-int set_mask(ras_problem* h, int row, const std::vector<int>& m) {
-    CK(cudaMemcpyAsync(h->d_mask + row * h->nprob, m.data(), h->nprob * sizeof(int), cudaMemcpyHostToDevice,
-                       h->st));
+// Block table of row `row`: VEC_BLOCKS blocks spread over the problems with
+// m[p] != 0 in proportion to their segment lengths (at least one each, and
+// no more than one per 512 elements).
+int build_grid(ras_problem* h, int row, const std::vector<int>& m) {
+    if (h->last_mask[row] == m) return RAS_OK;
+    const int P = h->nprob, cap = ras::VEC_BLOCKS + P;
+    double tot = 0.0;
+    for (int p = 0; p < P; ++p)
+        if (m[p]) tot += (double)h->segs[p].len;
+    std::vector<int> nbps(P, 0);
+    std::vector<int2> tab;
+    for (int p = 0; p < P; ++p) {
+        if (!m[p]) continue;
+        const double len = (double)h->segs[p].len;
+        const int most = (int)std::max(1.0, std::ceil(len / 512.0));
+        int nb = (int)std::floor(ras::VEC_BLOCKS * len / tot + 0.5);
+        nb = std::max(1, std::min(nb, std::min(most, (int)ras::VEC_BLOCKS)));
+        nbps[p] = nb;
+        for (int b = 0; b < nb; ++b) tab.push_back(make_int2(p, b));
+    }
+    if ((int)tab.size() > cap) return fail(h, RAS_EINVAL, "block table overflow");
+    CK(cudaMemcpyAsync(h->d_nbps + row * P, nbps.data(), P * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    if (!tab.empty())
+        CK(cudaMemcpyAsync(h->d_tab + (size_t)row * cap, tab.data(), tab.size() * sizeof(int2),
+                           cudaMemcpyHostToDevice, h->st));
+    h->ntab[row] = (int)tab.size();
+    h->last_mask[row] = m;
     return RAS_OK;
 }
 
-// Per-problem squared norms of the segments of v (problems flagged in dmask),
-// into h->scal[p * SS] (device) and h->h_scal[p * SS] (host).
-int seg_norms2(ras_problem* h, const double* v, const int* dmask) {
-    const int P = h->nprob, nb = h->nbp;
+ras::SegGrid seg_grid(const ras_problem* h, int row) {
+    ras::SegGrid g;
+    g.tab = h->d_tab + (size_t)row * (ras::VEC_BLOCKS + h->nprob);
+    g.nbps = h->d_nbps + row * h->nprob;
+    g.nblocks = h->ntab[row];
+    return g;
+}
+
+int set_mask(ras_problem* h, int row, const std::vector<int>& m) {
+    CK(cudaMemcpyAsync(h->d_mask + row * h->nprob, m.data(), h->nprob * sizeof(int), cudaMemcpyHostToDevice,
+                       h->st));
+    return build_grid(h, row, m);
+}
+
+// Per-problem squared norms of the segments of v (problems of mask row
+// `row`), into h->scal[p * SS] (device) and h->h_scal[p * SS] (host).
+int seg_norms2(ras_problem* h, const double* v, int row) {
+    const int P = h->nprob;
+    const ras::SegGrid g = seg_grid(h, row);
     double len = 0.0;
-    for (auto& s : h->segs) len += 8.0 * s.len;
+    for (int p = 0; p < P; ++p)
+        if (h->last_mask[row][p]) len += 8.0 * h->segs[p].len;
     CK(timed(h, RAS_K_KRYLOV, len, [&] {
-        return ras::launch_seg_dot(h->st, P, nb, h->d_segs, dmask, v, h->L, 1, v, h->partials);
+        return ras::launch_seg_dot(h->st, g, h->d_segs, v, h->L, 1, v, h->partials);
     }));
     CK(timed(h, RAS_K_OTHER, 0.0,
-             [&] { return ras::launch_seg_reduce(h->st, P, nb, dmask, 1, h->partials, h->scal); }));
+             [&] { return ras::launch_seg_reduce(h->st, P, g.nbps, 1, h->partials, h->scal); }));
     CK(cudaMemcpyAsync(h->h_scal, h->scal, (size_t)P * SS * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     return sync(h);
 }
@@ -532,26 +598,21 @@ int precond_internal(ras_problem* h, const double* R, double* Zo) {
 template <class Aop, class Mop>
 int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, const std::vector<int>& part,
           std::vector<int>& its, std::vector<int>& conv) {
-    const int P = h->nprob, nb = h->nbp, m = h->o.gmres_restart, maxit = h->o.gmres_maxit;
+    const int P = h->nprob, m = h->o.gmres_restart, maxit = h->o.gmres_maxit;
     const long long L = h->L;
     const double rtol = h->o.gmres_rtol;
-    if (h->Vm < m) {
-        dfree(h, h->V);
-        h->V = nullptr;
-        TRY(dalloc(h, &h->V, (size_t)(m + 1) * L));
-        h->Vm = m;
-    }
+    TRY(ensure(h, &h->V, (size_t)(m + 1) * L));
+    h->Vm = m;
     double* V = h->V;
     double* r = h->T2;
     double* upd = h->T3;
-    const int* dmask = h->d_mask;   // row 0
     its.assign(P, 0);
     conv.assign(P, 0);
     CK(cudaMemsetAsync(x, 0, L * sizeof(double), h->st));
     std::vector<int> act(P, 0), cyc(P, 0), steps(P, 0);
     std::vector<double> target(P, 0.0), beta(P, 0.0);
     TRY(set_mask(h, 0, part));
-    TRY(seg_norms2(h, b, dmask));
+    TRY(seg_norms2(h, b, 0));
     for (int p = 0; p < P; ++p) {
         if (!part[p]) continue;
         const double bn = std::sqrt(h->h_scal[p * SS]);
@@ -567,7 +628,7 @@ int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, c
     for (;;) {
         // true residual norms of the problems still iterating
         TRY(set_mask(h, 0, act));
-        TRY(seg_norms2(h, r, dmask));
+        TRY(seg_norms2(h, r, 0));
         bool any = false;
         for (int p = 0; p < P; ++p) {
             if (!act[p]) continue;
@@ -584,7 +645,7 @@ int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, c
         TRY(set_mask(h, 0, cyc));
         // V_0 = r / beta (device-side, from the squared norms in h->scal)
         CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
-            return ras::launch_seg_scale(h->st, P, nb, h->d_segs, dmask, r, h->scal, 1.0, V);
+            return ras::launch_seg_scale(h->st, seg_grid(h, 0), h->d_segs, r, h->scal, 1.0, V);
         }));
         std::fill(H.begin(), H.end(), 0.0);
         std::fill(g.begin(), g.end(), 0.0);
@@ -608,26 +669,26 @@ int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, c
             double* h2 = h->scal + (size_t)P * SS;
             double* n2 = h->scal + (size_t)2 * P * SS;
             CK(timed(h, RAS_K_KRYLOV, dbytes, [&] {
-                return ras::launch_seg_dot(h->st, P, nb, h->d_segs, dmask, V, L, j + 1, w, h->partials);
+                return ras::launch_seg_dot(h->st, seg_grid(h, 0), h->d_segs, V, L, j + 1, w, h->partials);
             }));
             CK(timed(h, RAS_K_OTHER, 0.0,
-                     [&] { return ras::launch_seg_reduce(h->st, P, nb, dmask, j + 1, h->partials, h1); }));
+                     [&] { return ras::launch_seg_reduce(h->st, P, seg_grid(h, 0).nbps, j + 1, h->partials, h1); }));
             CK(timed(h, RAS_K_KRYLOV, abytes, [&] {
-                return ras::launch_seg_axpy(h->st, P, nb, h->d_segs, dmask, V, L, j + 1, h1, -1.0, w);
+                return ras::launch_seg_axpy(h->st, seg_grid(h, 0), h->d_segs, V, L, j + 1, h1, -1.0, w);
             }));
             CK(timed(h, RAS_K_KRYLOV, dbytes, [&] {
-                return ras::launch_seg_dot(h->st, P, nb, h->d_segs, dmask, V, L, j + 1, w, h->partials);
+                return ras::launch_seg_dot(h->st, seg_grid(h, 0), h->d_segs, V, L, j + 1, w, h->partials);
             }));
             CK(timed(h, RAS_K_OTHER, 0.0,
-                     [&] { return ras::launch_seg_reduce(h->st, P, nb, dmask, j + 1, h->partials, h2); }));
+                     [&] { return ras::launch_seg_reduce(h->st, P, seg_grid(h, 0).nbps, j + 1, h->partials, h2); }));
             CK(timed(h, RAS_K_KRYLOV, abytes, [&] {
-                return ras::launch_seg_axpy(h->st, P, nb, h->d_segs, dmask, V, L, j + 1, h2, -1.0, w);
+                return ras::launch_seg_axpy(h->st, seg_grid(h, 0), h->d_segs, V, L, j + 1, h2, -1.0, w);
             }));
             CK(timed(h, RAS_K_KRYLOV, 8.0 * seglen, [&] {
-                return ras::launch_seg_dot(h->st, P, nb, h->d_segs, dmask, w, L, 1, w, h->partials);
+                return ras::launch_seg_dot(h->st, seg_grid(h, 0), h->d_segs, w, L, 1, w, h->partials);
             }));
             CK(timed(h, RAS_K_OTHER, 0.0,
-                     [&] { return ras::launch_seg_reduce(h->st, P, nb, dmask, 1, h->partials, n2); }));
+                     [&] { return ras::launch_seg_reduce(h->st, P, seg_grid(h, 0).nbps, 1, h->partials, n2); }));
             CK(cudaMemcpyAsync(h->h_scal, h->scal, (size_t)3 * P * SS * sizeof(double), cudaMemcpyDeviceToHost,
                                h->st));
             TRY(sync(h));
@@ -664,7 +725,7 @@ int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, c
             if (changed) TRY(set_mask(h, 0, cyc));
             if (std::any_of(cyc.begin(), cyc.end(), [](int v) { return v != 0; })) {
                 CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
-                    return ras::launch_seg_scale(h->st, P, nb, h->d_segs, dmask, w, n2, 1.0, w);
+                    return ras::launch_seg_scale(h->st, seg_grid(h, 0), h->d_segs, w, n2, 1.0, w);
                 }));
             }
         }
@@ -691,7 +752,7 @@ int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, c
         TRY(set_mask(h, 0, took));
         CK(cudaMemsetAsync(upd, 0, L * sizeof(double), h->st));
         CK(timed(h, RAS_K_KRYLOV, 8.0 * seglen * (maxsteps + 2), [&] {
-            return ras::launch_seg_axpy(h->st, P, nb, h->d_segs, dmask, V, L, maxsteps, ycoef, 1.0, upd);
+            return ras::launch_seg_axpy(h->st, seg_grid(h, 0), h->d_segs, V, L, maxsteps, ycoef, 1.0, upd);
         }));
         const double* add = upd;
         if (prec) {
@@ -699,14 +760,14 @@ int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, c
             add = h->Z;
         }
         CK(timed(h, RAS_K_KRYLOV, 24.0 * seglen, [&] {
-            return ras::launch_seg_add_scaled(h->st, P, nb, h->d_segs, dmask, x, add, 1.0, x);
+            return ras::launch_seg_add_scaled(h->st, seg_grid(h, 0), h->d_segs, x, add, 1.0, x);
         }));
         // r = b - A x for the problems still iterating
         if (std::none_of(act.begin(), act.end(), [](int v) { return v != 0; })) return RAS_OK;
         TRY(set_mask(h, 0, act));
         TRY(A(x, r, act));
         CK(timed(h, RAS_K_KRYLOV, 24.0 * seglen, [&] {
-            return ras::launch_seg_add_scaled(h->st, P, nb, h->d_segs, dmask, b, r, -1.0, r);
+            return ras::launch_seg_add_scaled(h->st, seg_grid(h, 0), h->d_segs, b, r, -1.0, r);
         }));
     }
 }
@@ -715,16 +776,15 @@ int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, c
 // RASPEN for every problem of the handle, in lockstep: a problem leaves the
 // loop when its own stop test holds (or at kmax).
 int raspen_internal(ras_problem* h, ras_stats* s) {
-    const int P = h->nprob, nb = h->nbp;
+    const int P = h->nprob;
     const ras_opts& o = h->o;
     std::vector<double> pstart(P, o.eps0);
     int rc = ras_apply_internal(h, pstart, h->F, s);
     if (rc < 0) return rc;
     std::vector<int> all(P, 1), need(P, 0), k(P, 0), its, conv;
     std::vector<double> nrm(P), stop(P);
-    const int* dneed = h->d_mask + P;   // row 1
     TRY(set_mask(h, 1, all));
-    TRY(seg_norms2(h, h->F, dneed));
+    TRY(seg_norms2(h, h->F, 1));
     for (int p = 0; p < P; ++p) {
         nrm[p] = std::sqrt(h->h_scal[p * SS]);
         stop[p] = std::max(o.tol, o.tol * nrm[p]);
@@ -746,11 +806,11 @@ int raspen_internal(ras_problem* h, ras_stats* s) {
         if (!any) break;
         TRY(set_mask(h, 1, need));
         CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
-            return ras::launch_seg_scale(h->st, P, nb, h->d_segs, dneed, h->F, nullptr, -1.0, h->T1);
+            return ras::launch_seg_scale(h->st, seg_grid(h, 1), h->d_segs, h->F, nullptr, -1.0, h->T1);
         }));
         TRY(gmres(h, A, M, false, h->T1, h->Dv, need, its, conv));
         CK(timed(h, RAS_K_KRYLOV, 24.0 * seglen, [&] {
-            return ras::launch_seg_add_scaled(h->st, P, nb, h->d_segs, dneed, h->X, h->Dv, 1.0, h->X);
+            return ras::launch_seg_add_scaled(h->st, seg_grid(h, 1), h->d_segs, h->X, h->Dv, 1.0, h->X);
         }));
         for (int p = 0; p < P; ++p) {
             if (need[p]) {
@@ -767,7 +827,7 @@ int raspen_internal(ras_problem* h, ras_stats* s) {
                 if (s) s[p].outer_its = k[p];
             return rc;
         }
-        TRY(seg_norms2(h, h->F, dneed));
+        TRY(seg_norms2(h, h->F, 1));
         for (int p = 0; p < P; ++p)
             if (need[p]) nrm[p] = std::sqrt(h->h_scal[p * SS]);
     }
@@ -787,7 +847,6 @@ int raspen_internal(ras_problem* h, ras_stats* s) {
 
 // --------------------------------------------------------------- Newton_RAS
 int newton_ras_internal(ras_problem* h, ras_stats* s) {
-    const int nb = h->nbp;
     const long long N = plane(h, 0);
     const ras_opts& o = h->o;
     const double seglen = (double)h->segs[0].len;
@@ -816,7 +875,7 @@ int newton_ras_internal(ras_problem* h, ras_stats* s) {
             return ras::launch_coef_global(h->st, h->probs[0], h->X, h->X + N, eps, h->coefG);
         }));
         CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
-            return ras::launch_seg_scale(h->st, 1, nb, h->d_segs, nullptr, h->F, nullptr, -1.0, h->T1);
+            return ras::launch_seg_scale(h->st, seg_grid(h, 2), h->d_segs, h->F, nullptr, -1.0, h->T1);
         }));
         TRY(gmres(h, A, M, true, h->T1, h->Dv, one, its, conv));
         if (s) s->gmres_its += its[0];
@@ -833,7 +892,7 @@ int newton_ras_internal(ras_problem* h, ras_stats* s) {
             if (!(nt <= o.sigma * nrm)) s->exhausted += 1;
         }
         CK(timed(h, RAS_K_KRYLOV, 24.0 * seglen, [&] {
-            return ras::launch_seg_add_scaled(h->st, 1, nb, h->d_segs, nullptr, h->X, h->Dv, alpha, h->X);
+            return ras::launch_seg_add_scaled(h->st, seg_grid(h, 2), h->d_segs, h->X, h->Dv, alpha, h->X);
         }));
         const double en = ras::next_eps(eps, o.gamma, o.eps_min);
         if (en == eps) {
@@ -892,26 +951,26 @@ int ras_default_opts(ras_opts* o) {
     return RAS_OK;
 }
 
-int ras_batch_create(int count, const ras_problem_desc* pd, const ras_opts* o, void* stream, ras_problem** out) {
-    if (!out) return RAS_EINVAL;
-    *out = nullptr;
-    if (count < 1 || count > 4096 || !pd) return RAS_EINVAL;
-    for (int p = 0; p < count; ++p) {
-        const ras_problem_desc& d = pd[p];
-        if (d.n < 2 || d.sx < 1 || d.sy < 1 || d.sx > d.n || d.sy > d.n || d.overlap < 0 || d.phi < 0 ||
-            d.phi > 2 || !(d.nu > 0) || !(d.mu > 0) || !std::isfinite(d.nu) || !std::isfinite(d.mu) || !d.y_d)
-            return RAS_EINVAL;
-    }
-    ras_problem* h = new ras_problem();
+namespace {
+
+bool desc_valid(const ras_problem_desc& d) {
+    return d.n >= 2 && d.sx >= 1 && d.sy >= 1 && d.sx <= d.n && d.sy <= d.n && d.overlap >= 0 && d.phi >= 0 &&
+           d.phi <= 2 && d.nu > 0 && d.mu > 0 && std::isfinite(d.nu) && std::isfinite(d.mu);
+}
+
+// Host-side layout of a set of problems: problem and subdomain descriptors,
+// segment offsets of the global vectors, offsets into the local pools and
+// the register-tile classes. The y_d / f pointers are set by the caller.
+int build_layout(ras_problem* h, int count, const ras_problem_desc* pd) {
     h->nprob = count;
     h->desc.assign(pd, pd + count);
-    if (o) h->o = *o;
-    else ras_default_opts(&h->o);
-    h->st = (cudaStream_t)stream;
-    int rc = validate_opts(h, h->o);
-    if (rc < 0) { delete h; return rc; }
-    long long voff = 0, noff = 0, goff = 0, vec = 0, nn_tot = 0;
-    bool any_f = false;
+    h->probs.clear();
+    h->segs.clear();
+    h->subs.clear();
+    h->sub_first.clear();
+    h->sub_count.clear();
+    h->maxm = 0;
+    long long voff = 0, noff = 0, goff = 0, vec = 0;
     for (int p = 0; p < count; ++p) {
         const ras_problem_desc& d = pd[p];
         const int n = d.n;
@@ -949,64 +1008,117 @@ int ras_batch_create(int count, const ras_problem_desc* pd, const ras_opts* o, v
         }
         h->sub_count.push_back((int)h->subs.size() - h->sub_first.back());
         vec += 2LL * n * n;
-        nn_tot += (long long)n * n;
-        any_f = any_f || d.f != nullptr;
     }
-    if (h->maxm > ras::MAX_M) {
-        delete h;
-        return RAS_EINVAL;
-    }
+    if (h->maxm > ras::MAX_M) return fail(h, RAS_EINVAL, "a subdomain is wider than 80 nodes (2 wx > 160)");
     h->nsub = (int)h->subs.size();
     h->Lsum = voff; h->Nsum = noff; h->Gsum = goff; h->L = vec;
     // register-tile classes of the FP32 factorisation: tile = mp / 16
-    std::vector<int> lists;
+    h->h_lists.clear();
     h->tile_off.assign(NTILE, 0);
     h->tile_cnt.assign(NTILE, 0);
     for (int c = 0; c < NTILE; ++c) {
-        h->tile_off[c] = (int)lists.size();
+        h->tile_off[c] = (int)h->h_lists.size();
         for (int i = 0; i < h->nsub; ++i)
-            if (h->subs[i].mp / 32 - 1 == c) lists.push_back(i);
-        h->tile_cnt[c] = (int)lists.size() - h->tile_off[c];
+            if (h->subs[i].mp / 32 - 1 == c) h->h_lists.push_back(i);
+        h->tile_cnt[c] = (int)h->h_lists.size() - h->tile_off[c];
     }
     h->nbp = std::max(8, ras::VEC_BLOCKS / count);
-    rc = RAS_OK;
-    auto A = [&](int r) { if (rc == RAS_OK && r < 0) rc = r; };
-    A(dalloc(h, &h->yd, nn_tot));
-    if (any_f) A(dalloc(h, &h->f, nn_tot));
-    A(dalloc(h, &h->d_subs, h->nsub));
-    A(dalloc(h, &h->d_probs, count));
-    A(dalloc(h, &h->d_segs, count));
-    A(dalloc(h, &h->d_lists, std::max<size_t>(1, lists.size())));
-    A(dalloc(h, &h->cpool, h->Lsum));
-    A(dalloc(h, &h->dpool, h->Lsum));
-    A(dalloc(h, &h->Kpool, h->Lsum));
-    A(dalloc(h, &h->Ktpool, h->Lsum));
-    A(dalloc(h, &h->rpool, h->Lsum));
-    A(dalloc(h, &h->coef, 3 * h->Nsum));
-    A(dalloc(h, &h->ls, h->nsub));
-    A(dalloc(h, &h->d_active, 1));
-    A(dalloc(h, &h->d_err, 1));
-    A(dalloc(h, &h->d_mask, 2 * count));
-    A(dalloc(h, &h->d_pstart, count));
-    for (double** p : {&h->X, &h->F, &h->Dv, &h->Ov, &h->T1, &h->T2, &h->T3, &h->Z}) A(dalloc(h, p, h->L));
-    if (count == 1) A(dalloc(h, &h->coefG, 3 * nn_tot));
-    A(dalloc(h, &h->partials, (size_t)count * SS * std::max(h->nbp, (int)ras::VEC_BLOCKS)));
-    A(dalloc(h, &h->scal, (size_t)4 * count * SS));
-    if (rc == RAS_OK) A(alloc_factor_pools(h));
-    if (rc == RAS_OK) {
-        if (cudaMallocHost((void**)&h->h_active, sizeof(int)) != cudaSuccess ||
-            cudaMallocHost((void**)&h->h_scal, (size_t)4 * count * SS * sizeof(double)) != cudaSuccess) {
+    h->jvp_ready = false;
+    for (int r = 0; r < 3; ++r) {
+        h->last_mask[r].clear();
+        h->ntab[r] = 0;
+    }
+    return RAS_OK;
+}
+
+// Device buffers for the current layout (grown, never shrunk; contents of a
+// grown buffer are not kept). own_data: the handle stores y_d and f itself.
+int ensure_pools(ras_problem* h, bool own_data) {
+    const int count = h->nprob;
+    long long nn_tot = 0;
+    bool any_f = false;
+    for (int p = 0; p < count; ++p) {
+        nn_tot += plane(h, p);
+        any_f = any_f || h->desc[p].f != nullptr;
+    }
+    if (own_data) {
+        TRY(ensure(h, &h->yd, nn_tot));
+        if (any_f) TRY(ensure(h, &h->f, nn_tot));
+    }
+    TRY(ensure(h, &h->d_subs, h->nsub));
+    TRY(ensure(h, &h->d_probs, count));
+    TRY(ensure(h, &h->d_segs, count));
+    TRY(ensure(h, &h->d_lists, std::max<size_t>(1, h->h_lists.size())));
+    for (double** q : {&h->cpool, &h->dpool, &h->Kpool, &h->Ktpool, &h->rpool}) TRY(ensure(h, q, h->Lsum));
+    TRY(ensure(h, &h->coef, 3 * h->Nsum));
+    TRY(ensure(h, &h->ls, h->nsub));
+    TRY(ensure(h, &h->d_active, 1));
+    if (!h->d_err) {
+        TRY(dalloc(h, &h->d_err, 1));
+        CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st));
+    }
+    TRY(ensure(h, &h->d_mask, 2 * count));
+    TRY(ensure(h, &h->d_tab, (size_t)3 * (ras::VEC_BLOCKS + count)));
+    TRY(ensure(h, &h->d_nbps, (size_t)3 * count));
+    TRY(ensure(h, &h->d_pstart, count));
+    for (double** q : {&h->X, &h->F, &h->Dv, &h->Ov, &h->T1, &h->T2, &h->T3, &h->Z}) TRY(ensure(h, q, h->L));
+    if (count == 1) TRY(ensure(h, &h->coefG, 3 * nn_tot));
+    TRY(ensure(h, &h->partials, (size_t)count * SS * std::max(h->nbp, (int)ras::VEC_BLOCKS)));
+    TRY(ensure(h, &h->scal, (size_t)4 * count * SS));
+    TRY(alloc_factor_pools(h));
+    if (!h->h_active) {
+        if (cudaMallocHost((void**)&h->h_active, sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
-            rc = RAS_ENOMEM;
+            return fail(h, RAS_ENOMEM, "pinned host allocation failed");
         }
     }
+    const size_t ns = (size_t)4 * count * SS;
+    if (h->cap_hscal < ns) {
+        if (h->h_scal) cudaFreeHost(h->h_scal);
+        h->h_scal = nullptr;
+        h->cap_hscal = 0;
+        if (cudaMallocHost((void**)&h->h_scal, ns * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, RAS_ENOMEM, "pinned host allocation failed");
+        }
+        h->cap_hscal = ns;
+    }
+    return RAS_OK;
+}
+
+int upload_layout(ras_problem* h) {
+    TRY(build_grid(h, 2, std::vector<int>(h->nprob, 1)));
+    CK(cudaMemcpyAsync(h->d_subs, h->subs.data(), h->nsub * sizeof(SubDev), cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->d_probs, h->probs.data(), h->nprob * sizeof(ProbDev), cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->d_segs, h->segs.data(), h->nprob * sizeof(Seg), cudaMemcpyHostToDevice, h->st));
+    if (!h->h_lists.empty())
+        CK(cudaMemcpyAsync(h->d_lists, h->h_lists.data(), h->h_lists.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           h->st));
+    return RAS_OK;
+}
+
+}  // namespace
+
+int ras_batch_create(int count, const ras_problem_desc* pd, const ras_opts* o, void* stream, ras_problem** out) {
+    if (!out) return RAS_EINVAL;
+    *out = nullptr;
+    if (count < 1 || count > 4096 || !pd) return RAS_EINVAL;
+    for (int p = 0; p < count; ++p)
+        if (!desc_valid(pd[p]) || !pd[p].y_d) return RAS_EINVAL;
+    ras_problem* h = new ras_problem();
+    if (o) h->o = *o;
+    else ras_default_opts(&h->o);
+    h->st = (cudaStream_t)stream;
+    int rc = validate_opts(h, h->o);
+    if (rc == RAS_OK) rc = build_layout(h, count, pd);
+    if (rc == RAS_OK) rc = ensure_pools(h, true);
     if (rc != RAS_OK) {
         ras_destroy(h);
         return rc;
     }
     // y_d and f of problem p at the plane offset sum_{q<p} n_q^2
     long long poff = 0;
-    cudaError_t e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st);
+    cudaError_t e = cudaSuccess;
     for (int p = 0; p < count && e == cudaSuccess; ++p) {
         const long long N = plane(h, p);
         h->probs[p].yd = h->yd + poff;
@@ -1016,16 +1128,10 @@ int ras_batch_create(int count, const ras_problem_desc* pd, const ras_opts* o, v
             e = cudaMemcpyAsync(h->f + poff, pd[p].f, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
         poff += N;
     }
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->d_subs, h->subs.data(), h->nsub * sizeof(SubDev), cudaMemcpyHostToDevice, h->st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->d_probs, h->probs.data(), count * sizeof(ProbDev), cudaMemcpyHostToDevice, h->st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->d_segs, h->segs.data(), count * sizeof(Seg), cudaMemcpyHostToDevice, h->st);
-    if (e == cudaSuccess && !lists.empty())
-        e = cudaMemcpyAsync(h->d_lists, lists.data(), lists.size() * sizeof(int), cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess && upload_layout(h) != RAS_OK) e = cudaErrorUnknown;
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) {
+        cudaGetLastError();
         ras_destroy(h);
         return RAS_ECUDA;
     }
@@ -1088,8 +1194,12 @@ int ras_residual(ras_problem* h, const double* y, const double* p, double eps, d
                  double* norm_host) {
     if (!h || !y || !p || !(eps > 0)) return RAS_EINVAL;
     TRY(need_single(h));
-    CK(ras::launch_residual_global(h->st, h->probs[0], y, p, nullptr, nullptr, 0.0, eps, Fy, Fp, h->partials));
-    CK(ras::launch_reduce_partials(h->st, h->partials, ras::VEC_BLOCKS, 2, h->scal));
+    CK(timed(h, RAS_K_RESIDUAL, resid_bytes(h), [&] {
+        return ras::launch_residual_global(h->st, h->probs[0], y, p, nullptr, nullptr, 0.0, eps, Fy, Fp,
+                                           h->partials);
+    }));
+    CK(timed(h, RAS_K_OTHER, 0.0,
+             [&] { return ras::launch_reduce_partials(h->st, h->partials, ras::VEC_BLOCKS, 2, h->scal); }));
     CK(cudaMemcpyAsync(h->h_scal, h->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     TRY(sync(h));
     if (norm_host) *norm_host = std::sqrt(h->h_scal[0]);
@@ -1211,11 +1321,360 @@ void ras_destroy(ras_problem* h) {
     cudaStreamSynchronize(h->st);
     prof_flush(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-    for (void* p : h->allocs) cudaFree(p);
+    for (auto& a : h->allocs) cudaFree(a.first);
     h->allocs.clear();
     if (h->h_active) cudaFreeHost(h->h_active);
     if (h->h_scal) cudaFreeHost(h->h_scal);
     delete h;
+}
+
+// ------------------------------------------------------------------ serving
+// Continuous batching of RASPEN_eps solves (Alg. 2). A step runs one outer
+// iteration for every admitted request at once: the evaluation of the RASPEN
+// function at x_k (local Newton solves with eps-continuation for k = 0, at
+// eps_min after), the stop test, and for the requests that go on the GMRES
+// solve and the update x_{k+1} = x_k + d, all in the batched kernels. This is
+// the sequence of Alg. 2 for every request (evaluate, test, solve, update),
+// grouped so that only x_k and host counters persist between steps; requests
+// join and leave between steps. Each admitted request owns slot storage
+// (y, p, y_d and f, stream-ordered allocation); the batch workspace is laid
+// out anew for the admitted set when it changes (buffers only grow).
+// Admission is first come, first served while the estimate of slot storage
+// plus workspace stays within the HBM budget.
+struct ras_server {
+    ras_problem* ws = nullptr;
+    size_t budget = 0;
+    int max_active = 0;
+    ras_opts o{};
+    cudaStream_t st = nullptr;
+    struct Req {
+        long long id = 0;
+        ras_problem_desc d{};
+        std::vector<double> yd_h, f_h;   // staged host data until admission
+        double* mem = nullptr;           // slot storage: y | p | y_d [| f]
+        size_t slot = 0, scratch = 0;    // admission estimate
+        int k = 0;
+        bool failed = false;
+        double stop = 0.0;
+        ras_stats stats{};
+    };
+    std::deque<Req*> pending;
+    std::vector<Req*> active;
+    std::vector<Req*> finished;          // result kept until fetched
+    bool dirty = true;
+    long long next_id = 1;
+    size_t slot_held = 0, scratch_active = 0, ws_cap = 0;
+    std::string err;
+};
+
+namespace {
+
+int sfail(ras_server* s, int code, const std::string& msg) {
+    if (s) s->err = msg;
+    return code;
+}
+
+// Device bytes a request needs: its slot storage and its share of the batch
+// workspace (local pools, factors, global and Krylov vectors, descriptors).
+int request_bytes(const ras_problem_desc& d, const ras_opts& o, size_t& slot, size_t& scratch) {
+    ras_problem tmp;
+    tmp.o = o;
+    if (build_layout(&tmp, 1, &d) != RAS_OK) return RAS_EINVAL;
+    const double n2 = (double)d.n * d.n;
+    const size_t es = (o.precision == RAS_MIXED) ? sizeof(float) : sizeof(double);
+    slot = (size_t)((3.0 + (d.f ? 1.0 : 0.0)) * n2 * sizeof(double));
+    double b = 5.0 * tmp.Lsum * sizeof(double) + 3.0 * tmp.Nsum * sizeof(double) +
+               (double)tmp.nsub * (sizeof(LocalState) + sizeof(SubDev) + 2 * sizeof(int)) +
+               (double)tmp.Gsum * es + (double)tmp.Lsum * es +
+               (8.0 + o.gmres_restart + 1.0) * tmp.L * sizeof(double) + 3.0 * n2 * sizeof(double) +
+               (double)SS * ras::VEC_BLOCKS * sizeof(double) + 4.0 * SS * sizeof(double) + 256.0;
+    scratch = (size_t)b;
+    return RAS_OK;
+}
+
+int server_relayout(ras_server* s) {
+    if (!s->ws) {
+        s->ws = new ras_problem();
+        s->ws->o = s->o;
+        s->ws->st = s->st;
+    }
+    ras_problem* h = s->ws;
+    std::vector<ras_problem_desc> descs;
+    for (auto* r : s->active) {
+        ras_problem_desc d = r->d;
+        const long long N = (long long)d.n * d.n;
+        d.y_d = r->mem + 2 * N;
+        d.f = r->f_h.empty() ? nullptr : r->mem + 3 * N;
+        descs.push_back(d);
+    }
+    TRY(build_layout(h, (int)descs.size(), descs.data()));
+    TRY(ensure_pools(h, false));
+    for (int p = 0; p < h->nprob; ++p) {
+        h->probs[p].yd = descs[p].y_d;
+        h->probs[p].f = descs[p].f;
+    }
+    TRY(upload_layout(h));
+    s->dirty = false;
+    return RAS_OK;
+}
+
+int server_admit(ras_server* s) {
+    while (!s->pending.empty() && (int)s->active.size() < s->max_active) {
+        auto* r = s->pending.front();
+        const size_t cap = std::max(s->ws_cap, s->scratch_active + r->scratch);
+        if (cap + s->slot_held + r->slot > s->budget) break;   // first come, first served
+        void* m = nullptr;
+        if (cudaMallocAsync(&m, r->slot, s->st) != cudaSuccess) {
+            cudaGetLastError();
+            break;   // retry at a later step
+        }
+        r->mem = static_cast<double*>(m);
+        const long long N = (long long)r->d.n * r->d.n;
+        cudaError_t e = cudaMemsetAsync(r->mem, 0, 2 * N * sizeof(double), s->st);   // x0 = 0
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(r->mem + 2 * N, r->yd_h.data(), N * sizeof(double), cudaMemcpyHostToDevice, s->st);
+        if (e == cudaSuccess && !r->f_h.empty())
+            e = cudaMemcpyAsync(r->mem + 3 * N, r->f_h.data(), N * sizeof(double), cudaMemcpyHostToDevice, s->st);
+        if (e != cudaSuccess) return sfail(s, RAS_ECUDA, std::string("admission copy: ") + cudaGetErrorString(e));
+        s->pending.pop_front();
+        s->active.push_back(r);
+        s->slot_held += r->slot;
+        s->scratch_active += r->scratch;
+        s->ws_cap = cap;
+        s->dirty = true;
+    }
+    return RAS_OK;
+}
+
+int server_outer_iteration(ras_server* s) {
+    ras_problem* h = s->ws;
+    const int P = h->nprob;
+    const ras_opts& o = s->o;
+    for (int p = 0; p < P; ++p) {
+        const long long N = plane(h, p);
+        CK(cudaMemcpyAsync(h->X + h->probs[p].ofs, s->active[p]->mem, 2 * N * sizeof(double),
+                           cudaMemcpyDeviceToDevice, h->st));
+    }
+    std::vector<double> pstart(P);
+    std::vector<ras_stats> st(P);
+    for (int p = 0; p < P; ++p) {
+        pstart[p] = (s->active[p]->k == 0) ? o.eps0 : o.eps_min;
+        st[p] = s->active[p]->stats;
+    }
+    const int rc = ras_apply_internal(h, pstart, h->F, st.data());
+    if (rc == RAS_ECUDA || rc == RAS_ETIMEOUT) return rc;
+    for (int p = 0; p < P; ++p) {
+        if (st[p].local_failures > s->active[p]->stats.local_failures) s->active[p]->failed = true;
+        s->active[p]->stats = st[p];
+    }
+    std::vector<int> all(P, 1), need(P, 0), its, conv;
+    TRY(set_mask(h, 1, all));
+    TRY(seg_norms2(h, h->F, 1));
+    bool any = false;
+    for (int p = 0; p < P; ++p) {
+        auto* r = s->active[p];
+        const double nrm = std::sqrt(h->h_scal[p * SS]);
+        if (r->k == 0) {
+            r->stop = std::max(o.tol, o.tol * nrm);
+            r->stats.res0 = nrm;
+        }
+        r->stats.res = nrm;
+        need[p] = (!r->failed && nrm > r->stop && r->k < o.kmax_outer_raspen) ? 1 : 0;
+        any = any || need[p];
+        if (!need[p]) {
+            r->stats.outer_its = r->k;
+            r->stats.status = r->failed ? RAS_ENOCONV : (nrm <= r->stop ? RAS_OK : RAS_ENOCONV);
+        }
+    }
+    if (any) {
+        double seglen = 0.0;
+        for (int p = 0; p < P; ++p)
+            if (need[p]) seglen += (double)h->segs[p].len;
+        auto A = [&](const double* in, double* out, const std::vector<int>& mask) {
+            return jvp_internal(h, in, out, &mask);
+        };
+        auto M = [&](const double*, double*, const std::vector<int>&) { return RAS_OK; };
+        TRY(set_mask(h, 1, need));
+        CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
+            return ras::launch_seg_scale(h->st, seg_grid(h, 1), h->d_segs, h->F, nullptr, -1.0, h->T1);
+        }));
+        TRY(gmres(h, A, M, false, h->T1, h->Dv, need, its, conv));
+        CK(timed(h, RAS_K_KRYLOV, 24.0 * seglen, [&] {
+            return ras::launch_seg_add_scaled(h->st, seg_grid(h, 1), h->d_segs, h->X, h->Dv, 1.0, h->X);
+        }));
+        for (int p = 0; p < P; ++p) {
+            if (!need[p]) continue;
+            s->active[p]->k += 1;
+            s->active[p]->stats.gmres_its += its[p];
+        }
+    }
+    for (int p = 0; p < P; ++p) {
+        const long long N = plane(h, p);
+        CK(cudaMemcpyAsync(s->active[p]->mem, h->X + h->probs[p].ofs, 2 * N * sizeof(double),
+                           cudaMemcpyDeviceToDevice, h->st));
+    }
+    TRY(sync(h));
+    // retire the requests that stopped
+    std::vector<ras_server::Req*> keep;
+    for (int p = 0; p < P; ++p) {
+        auto* r = s->active[p];
+        if (need[p]) {
+            keep.push_back(r);
+        } else {
+            s->finished.push_back(r);
+            s->scratch_active -= r->scratch;
+            s->dirty = true;
+        }
+    }
+    s->active.swap(keep);
+    return RAS_OK;
+}
+
+}  // namespace
+
+int ras_server_create(size_t hbm_budget, int max_active, const ras_opts* o, void* stream, ras_server** out) {
+    if (!out) return RAS_EINVAL;
+    *out = nullptr;
+    if (hbm_budget == 0 || max_active < 1 || max_active > 4096) return RAS_EINVAL;
+    auto* s = new ras_server();
+    if (o) s->o = *o;
+    else ras_default_opts(&s->o);
+    ras_problem probe;
+    if (validate_opts(&probe, s->o) != RAS_OK) {
+        delete s;
+        return RAS_EINVAL;
+    }
+    s->budget = hbm_budget;
+    s->max_active = max_active;
+    s->st = (cudaStream_t)stream;
+    *out = s;
+    return RAS_OK;
+}
+
+int ras_server_request_bytes(const ras_problem_desc* d, const ras_opts* o, size_t* slot_bytes,
+                             size_t* scratch_bytes) {
+    if (!d || !desc_valid(*d)) return RAS_EINVAL;
+    ras_opts oo;
+    if (o) oo = *o;
+    else ras_default_opts(&oo);
+    size_t a = 0, b = 0;
+    TRY(request_bytes(*d, oo, a, b));
+    if (slot_bytes) *slot_bytes = a;
+    if (scratch_bytes) *scratch_bytes = b;
+    return RAS_OK;
+}
+
+int ras_server_submit(ras_server* s, const ras_problem_desc* d, long long* id) {
+    if (!s || !d || !id || !desc_valid(*d) || !d->y_d) return RAS_EINVAL;
+    auto* r = new ras_server::Req();
+    r->d = *d;
+    if (request_bytes(r->d, s->o, r->slot, r->scratch) != RAS_OK) {
+        delete r;
+        return sfail(s, RAS_EINVAL, "a subdomain is wider than 80 nodes (2 wx > 160)");
+    }
+    if (r->slot + r->scratch > s->budget) {
+        delete r;
+        return sfail(s, RAS_ENOMEM, "the request alone exceeds the HBM budget");
+    }
+    const size_t N = (size_t)d->n * d->n;
+    r->yd_h.assign(d->y_d, d->y_d + N);
+    if (d->f) r->f_h.assign(d->f, d->f + N);
+    r->d.y_d = nullptr;
+    r->d.f = nullptr;
+    r->id = s->next_id++;
+    s->pending.push_back(r);
+    *id = r->id;
+    return RAS_OK;
+}
+
+int ras_server_step(ras_server* s, int* active, int* finished) {
+    if (!s) return RAS_EINVAL;
+    const size_t fin0 = s->finished.size();
+    int rc = server_admit(s);
+    if (rc == RAS_OK && !s->active.empty()) {
+        if (s->dirty) rc = server_relayout(s);
+        if (rc == RAS_OK) rc = server_outer_iteration(s);
+        if (rc < 0 && s->ws) s->err = s->ws->err;
+    }
+    if (active) *active = (int)s->active.size();
+    if (finished) *finished = (int)(s->finished.size() - fin0);
+    return rc;
+}
+
+int ras_server_counts(const ras_server* s, int* pending, int* active, int* finished) {
+    if (!s) return RAS_EINVAL;
+    if (pending) *pending = (int)s->pending.size();
+    if (active) *active = (int)s->active.size();
+    if (finished) *finished = (int)s->finished.size();
+    return RAS_OK;
+}
+
+int ras_server_finished_ids(const ras_server* s, long long* ids, int cap) {
+    if (!s || (cap > 0 && !ids)) return RAS_EINVAL;
+    int k = 0;
+    for (auto* r : s->finished) {
+        if (k >= cap) break;
+        ids[k++] = r->id;
+    }
+    return k;
+}
+
+int ras_server_fetch(ras_server* s, long long id, double* y_host, double* p_host, ras_stats* st) {
+    if (!s) return RAS_EINVAL;
+    for (auto it = s->finished.begin(); it != s->finished.end(); ++it) {
+        ras_server::Req* r = *it;
+        if (r->id != id) continue;
+        const long long N = (long long)r->d.n * r->d.n;
+        cudaError_t e = cudaSuccess;
+        if (y_host) e = cudaMemcpyAsync(y_host, r->mem, N * sizeof(double), cudaMemcpyDeviceToHost, s->st);
+        if (e == cudaSuccess && p_host)
+            e = cudaMemcpyAsync(p_host, r->mem + N, N * sizeof(double), cudaMemcpyDeviceToHost, s->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+        if (e != cudaSuccess) return sfail(s, RAS_ECUDA, std::string("fetch: ") + cudaGetErrorString(e));
+        if (st) *st = r->stats;
+        cudaFreeAsync(r->mem, s->st);
+        s->slot_held -= r->slot;
+        s->finished.erase(it);
+        const int status = r->stats.status;
+        delete r;
+        // an idle server gives its workspace back
+        if (s->active.empty() && s->pending.empty() && s->ws) {
+            cudaStreamSynchronize(s->st);
+            ras_destroy(s->ws);
+            s->ws = nullptr;
+            s->ws_cap = 0;
+            s->dirty = true;
+        }
+        return status;
+    }
+    return sfail(s, RAS_EINVAL, "no finished request with this id");
+}
+
+size_t ras_server_device_bytes(const ras_server* s) {
+    if (!s) return 0;
+    return (s->ws ? s->ws->bytes : 0) + s->slot_held;
+}
+
+const char* ras_server_last_error(const ras_server* s) {
+    if (!s) return "null server";
+    return s->err.c_str();
+}
+
+void ras_server_destroy(ras_server* s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->st);
+    for (auto* r : s->active) {
+        if (r->mem) cudaFreeAsync(r->mem, s->st);
+        delete r;
+    }
+    for (auto* r : s->finished) {
+        if (r->mem) cudaFreeAsync(r->mem, s->st);
+        delete r;
+    }
+    for (auto* r : s->pending) delete r;
+    if (s->ws) ras_destroy(s->ws);
+    cudaStreamSynchronize(s->st);
+    delete s;
 }
 
 long long ras_launch_count(void) { return ras::g_launches.load(); }

@@ -672,10 +672,11 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub
             // S_j from G_{j-1} (in the factor pool) and D_j, implicit
             // pivoting (rows never move), then G_j[r][c] = M[perm[r]][rinv[c]].
             const float* Gp = G + (long long)(j > 0 ? j - 1 : 0) * blk;
-            for (int idx = tid; idx < m * m; idx += FACT_THREADS) {
-                const int r = idx / m, c = idx - r * m;
-                const float v = (j > 0) ? -tbeta2 * Gp[packed_index<float>(r, c, mp)] : 0.f;
-                Ms[r * LDS + c] = v + dval(j, r, c);
+            for (int r = warp; r < m; r += FACT_THREADS / 32) {
+                for (int c = lane; c < m; c += 32) {
+                    const float v = (j > 0) ? -tbeta2 * Gp[packed_index<float>(r, c, mp)] : 0.f;
+                    Ms[r * LDS + c] = v + dval(j, r, c);
+                }
             }
             for (int t = tid; t < m; t += FACT_THREADS) used[t] = 0;
             __syncthreads();
@@ -710,9 +711,22 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub
                 __syncthreads();
                 for (int t = tid; t < m; t += FACT_THREADS) Ms[r * LDS + t] = (t == k ? 1.f : Ms[r * LDS + t]) * inv;
                 __syncthreads();
-                for (int idx = tid; idx < m * m; idx += FACT_THREADS) {
-                    const int rr = idx / m, t = idx - rr * m;
-                    if (rr != r) Ms[rr * LDS + t] = (t == k ? 0.f : Ms[rr * LDS + t]) - fcol[rr] * Ms[r * LDS + t];
+                // rows by warp, columns by lane; the pivot row in registers
+                constexpr int NC = (MM + 31) / 32;
+                float prow[NC];
+#pragma unroll
+                for (int q = 0; q < NC; ++q) {
+                    const int t = lane + 32 * q;
+                    prow[q] = (t < m) ? Ms[r * LDS + t] : 0.f;
+                }
+                for (int rr = warp; rr < m; rr += FACT_THREADS / 32) {
+                    if (rr == r) continue;
+                    const float fct = fcol[rr];
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) {
+                        const int t = lane + 32 * q;
+                        if (t < m) Ms[rr * LDS + t] = (t == k ? 0.f : Ms[rr * LDS + t]) - fct * prow[q];
+                    }
                 }
                 __syncthreads();
             }

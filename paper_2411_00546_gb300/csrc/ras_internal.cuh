@@ -193,16 +193,25 @@ cudaError_t launch_add_scaled(cudaStream_t st, const double* x, const double* d,
 // segmented (one segment per problem) Krylov kernels: residual.cu.
 // Partials / results are laid out [problem][32] (32 = max vectors).
 constexpr int SEG_STRIDE = 32;
-cudaError_t launch_seg_dot(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask, const double* V,
-                           long long ld, int nv, const double* w, double* partials);
-cudaError_t launch_seg_reduce(cudaStream_t st, int nprob, int nbp, const int* mask, int nv, const double* partials,
+// Blocks of the segmented kernels: block b works on problem tab[b].x as its
+// tab[b].y-th of nbps[problem] blocks (problems left out have nbps = 0). The
+// host spreads VEC_BLOCKS blocks over the taking-part problems in proportion
+// to their segment lengths; partial sums use the stride VEC_BLOCKS.
+struct SegGrid {
+    const int2* tab;
+    const int* nbps;
+    int nblocks;
+};
+cudaError_t launch_seg_dot(cudaStream_t st, SegGrid g, const Seg* segs, const double* V, long long ld, int nv,
+                           const double* w, double* partials);
+cudaError_t launch_seg_reduce(cudaStream_t st, int nprob, const int* nbps, int nv, const double* partials,
                               double* out);
-cudaError_t launch_seg_axpy(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask, const double* V,
-                            long long ld, int nv, const double* h, double sign, double* w);
-cudaError_t launch_seg_scale(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask,
-                             const double* src, const double* n2, double sign, double* dst);
-cudaError_t launch_seg_add_scaled(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask,
-                                  const double* x, const double* d, double alpha, double* out);
+cudaError_t launch_seg_axpy(cudaStream_t st, SegGrid g, const Seg* segs, const double* V, long long ld, int nv,
+                            const double* h, double sign, double* w);
+cudaError_t launch_seg_scale(cudaStream_t st, SegGrid g, const Seg* segs, const double* src, const double* n2,
+                             double sign, double* dst);
+cudaError_t launch_seg_add_scaled(cudaStream_t st, SegGrid g, const Seg* segs, const double* x, const double* d,
+                                  double alpha, double* out);
 
 // per-subdomain kernels: local.cu. X, F, D, O, R, Z are global vector bases
 // (problem k at ProbDev.ofs); pools are indexed by SubDev offsets.

@@ -187,67 +187,87 @@ __global__ void __launch_bounds__(NT) k_add_scaled(const double* x, const double
 
 
 // ------------------------------------------------------------------ segmented
-// Grid (nbp, nprob): blocks blockIdx.x of problem blockIdx.y grid-stride over
-// that problem's segment; problems with mask == 0 are skipped. Reductions use
-// fixed trees and fixed block order (deterministic).
+// 1-D grid over a SegGrid table: block b works on problem tab[b].x, as its
+// tab[b].y-th of nbps blocks, grid-striding over that problem's segment.
+// Reductions use fixed trees and a fixed block order (deterministic for a
+// given table).
+__host__ __device__ constexpr int pow2_ceil(int v) { return v <= 1 ? 1 : 2 * pow2_ceil((v + 1) / 2); }
+
 template <int NVC>
-__global__ void __launch_bounds__(NT) k_seg_dot(const Seg* __restrict__ segs, const int* __restrict__ mask,
-                                                const double* __restrict__ V, long long ld, int nv,
+__global__ void __launch_bounds__(NT) k_seg_dot(SegGrid sg_, const Seg* __restrict__ segs,
+                                                const double* __restrict__ V, long long ld,
                                                 const double* __restrict__ w, double* partials) {
+    constexpr int P = pow2_ceil(NVC);   // values per lane, padded with zeros
     __shared__ double red[NT / 32][NVC];
-    const int pb = blockIdx.y, nbp = gridDim.x;
-    if (mask && !mask[pb]) return;
+    const int2 e = sg_.tab[blockIdx.x];
+    const int pb = e.x, bi = e.y, nb = sg_.nbps[pb];
     const Seg sg = segs[pb];
-    double acc[NVC];
+    double acc[P];
 #pragma unroll
-    for (int v = 0; v < NVC; ++v) acc[v] = 0.0;
-    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < sg.len; g += (long long)nbp * NT) {
+    for (int v = 0; v < P; ++v) acc[v] = 0.0;
+    for (long long g = (long long)bi * NT + threadIdx.x; g < sg.len; g += (long long)nb * NT) {
         const long long x = sg.ofs + g;
         const double wv = w[x];
 #pragma unroll
         for (int v = 0; v < NVC; ++v) acc[v] += V[(long long)v * ld + x] * wv;
     }
+    // Warp sums of the P values by a transposing butterfly: at offset s each
+    // lane keeps one half of its remaining values (the upper half when
+    // lane & s) and adds the partner's copy of that half, so the FP64 adds
+    // per lane are P - 1 (plus one per remaining level) instead of 5 P.
+    // Lane l then holds value vi(l) summed over the lanes that share its
+    // bits below the last transposing offset.
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int vi = 0;
+    int s = 16;
 #pragma unroll
-    for (int v = 0; v < NVC; ++v) {
-        double a = acc[v];
+    for (int cnt = P; cnt > 1; cnt >>= 1) {
+        const int half = cnt >> 1;
+        const bool up = (lane & s) != 0;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
-        if (lane == 0) red[warp][v] = a;
+        for (int k = 0; k < half; ++k) {
+            const double send = up ? acc[k] : acc[k + half];
+            const double keep = up ? acc[k + half] : acc[k];
+            acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+        if (up) vi += half;
+        s >>= 1;
     }
+    double a = acc[0];
+    for (int off = s; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+    if ((lane & ((32 / P) - 1)) == 0 && vi < NVC) red[warp][vi] = a;
     __syncthreads();
     if (threadIdx.x < NVC) {
-        double a = 0.0;
+        double t = 0.0;
 #pragma unroll
-        for (int k = 0; k < NT / 32; ++k) a += red[k][threadIdx.x];
-        partials[((long long)pb * SEG_STRIDE + threadIdx.x) * nbp + blockIdx.x] = a;
+        for (int k = 0; k < NT / 32; ++k) t += red[k][threadIdx.x];
+        partials[((long long)pb * SEG_STRIDE + threadIdx.x) * VEC_BLOCKS + bi] = t;
     }
-    (void)nv;
 }
 
-// out[p*32 + v] = sum over the nbp partials of (p, v), in block order.
-__global__ void k_seg_reduce(int nbp, const int* __restrict__ mask, const double* __restrict__ partials,
-                             double* out) {
+// out[p*32 + v] = sum over the nbps[p] partials of (p, v), in block order.
+__global__ void k_seg_reduce(const int* __restrict__ nbps, const double* __restrict__ partials, double* out) {
     const int v = blockIdx.x, pb = blockIdx.y;
-    if (mask && !mask[pb]) return;
+    const int nb = nbps[pb];
+    if (nb == 0) return;
     __shared__ double red[NT];
     double a = 0.0;
-    for (int k = threadIdx.x; k < nbp; k += NT) a += partials[((long long)pb * SEG_STRIDE + v) * nbp + k];
+    for (int k = threadIdx.x; k < nb; k += NT) a += partials[((long long)pb * SEG_STRIDE + v) * VEC_BLOCKS + k];
     a = block_sum1<NT>(a, red);
     if (threadIdx.x == 0) out[pb * SEG_STRIDE + v] = a;
 }
 
 // w += sign * sum_v h[p*32 + v] V_v on each segment.
-__global__ void __launch_bounds__(NT) k_seg_axpy(const Seg* __restrict__ segs, const int* __restrict__ mask,
+__global__ void __launch_bounds__(NT) k_seg_axpy(SegGrid sg_, const Seg* __restrict__ segs,
                                                  const double* __restrict__ V, long long ld, int nv,
                                                  const double* __restrict__ h, double sign, double* w) {
     __shared__ double hs[SEG_STRIDE];
-    const int pb = blockIdx.y, nbp = gridDim.x;
-    if (mask && !mask[pb]) return;
+    const int2 e = sg_.tab[blockIdx.x];
+    const int pb = e.x, bi = e.y, nb = sg_.nbps[pb];
     if (threadIdx.x < nv) hs[threadIdx.x] = sign * h[pb * SEG_STRIDE + threadIdx.x];
     __syncthreads();
     const Seg sg = segs[pb];
-    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < sg.len; g += (long long)nbp * NT) {
+    for (long long g = (long long)bi * NT + threadIdx.x; g < sg.len; g += (long long)nb * NT) {
         const long long x = sg.ofs + g;
         double acc = w[x];
         for (int v = 0; v < nv; ++v) acc += hs[v] * V[(long long)v * ld + x];
@@ -256,37 +276,35 @@ __global__ void __launch_bounds__(NT) k_seg_axpy(const Seg* __restrict__ segs, c
 }
 
 // dst = sign * src / sqrt(n2[p*32]) (n2 null: dst = sign * src) on each segment.
-__global__ void __launch_bounds__(NT) k_seg_scale(const Seg* __restrict__ segs, const int* __restrict__ mask,
-                                                  const double* src, const double* __restrict__ n2, double sign,
-                                                  double* dst) {
-    const int pb = blockIdx.y, nbp = gridDim.x;
-    if (mask && !mask[pb]) return;
+__global__ void __launch_bounds__(NT) k_seg_scale(SegGrid sg_, const Seg* __restrict__ segs, const double* src,
+                                                  const double* __restrict__ n2, double sign, double* dst) {
+    const int2 e = sg_.tab[blockIdx.x];
+    const int pb = e.x, bi = e.y, nb = sg_.nbps[pb];
     const double s = n2 ? sign / sqrt(n2[pb * SEG_STRIDE]) : sign;
     const Seg sg = segs[pb];
-    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < sg.len; g += (long long)nbp * NT)
+    for (long long g = (long long)bi * NT + threadIdx.x; g < sg.len; g += (long long)nb * NT)
         dst[sg.ofs + g] = s * src[sg.ofs + g];
 }
 
 // out = fma(alpha, d, x) on each segment.
-__global__ void __launch_bounds__(NT) k_seg_add_scaled(const Seg* __restrict__ segs, const int* __restrict__ mask,
-                                                       const double* x, const double* d, double alpha,
-                                                       double* out) {
-    const int pb = blockIdx.y, nbp = gridDim.x;
-    if (mask && !mask[pb]) return;
+__global__ void __launch_bounds__(NT) k_seg_add_scaled(SegGrid sg_, const Seg* __restrict__ segs, const double* x,
+                                                       const double* d, double alpha, double* out) {
+    const int2 e = sg_.tab[blockIdx.x];
+    const int pb = e.x, bi = e.y, nb = sg_.nbps[pb];
     const Seg sg = segs[pb];
-    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < sg.len; g += (long long)nbp * NT)
+    for (long long g = (long long)bi * NT + threadIdx.x; g < sg.len; g += (long long)nb * NT)
         out[sg.ofs + g] = fma(alpha, d[sg.ofs + g], x[sg.ofs + g]);
 }
 
 }  // namespace
 
-cudaError_t launch_seg_dot(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask, const double* V,
-                           long long ld, int nv, const double* w, double* partials) {
+cudaError_t launch_seg_dot(cudaStream_t st, SegGrid g, const Seg* segs, const double* V, long long ld, int nv,
+                           const double* w, double* partials) {
+    if (g.nblocks == 0) return cudaSuccess;
     count_launch();
-    const dim3 grid(nbp, nprob);
     switch (nv) {
 #define RAS_SEG_CASE(K) \
-    case K: k_seg_dot<K><<<grid, NT, 0, st>>>(segs, mask, V, ld, nv, w, partials); break;
+    case K: k_seg_dot<K><<<g.nblocks, NT, 0, st>>>(g, segs, V, ld, w, partials); break;
         RAS_SEG_CASE(1) RAS_SEG_CASE(2) RAS_SEG_CASE(3) RAS_SEG_CASE(4) RAS_SEG_CASE(5) RAS_SEG_CASE(6)
         RAS_SEG_CASE(7) RAS_SEG_CASE(8) RAS_SEG_CASE(9) RAS_SEG_CASE(10) RAS_SEG_CASE(11) RAS_SEG_CASE(12)
         RAS_SEG_CASE(13) RAS_SEG_CASE(14) RAS_SEG_CASE(15) RAS_SEG_CASE(16) RAS_SEG_CASE(17) RAS_SEG_CASE(18)
@@ -299,38 +317,38 @@ cudaError_t launch_seg_dot(cudaStream_t st, int nprob, int nbp, const Seg* segs,
     return cudaGetLastError();
 }
 
-cudaError_t launch_seg_reduce(cudaStream_t st, int nprob, int nbp, const int* mask, int nv, const double* partials,
+cudaError_t launch_seg_reduce(cudaStream_t st, int nprob, const int* nbps, int nv, const double* partials,
                               double* out) {
     if (nv < 1 || nv > SEG_STRIDE) return cudaErrorInvalidValue;
     count_launch();
-    k_seg_reduce<<<dim3(nv, nprob), NT, 0, st>>>(nbp, mask, partials, out);
+    k_seg_reduce<<<dim3(nv, nprob), NT, 0, st>>>(nbps, partials, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_seg_axpy(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask, const double* V,
-                            long long ld, int nv, const double* h, double sign, double* w) {
+cudaError_t launch_seg_axpy(cudaStream_t st, SegGrid g, const Seg* segs, const double* V, long long ld, int nv,
+                            const double* h, double sign, double* w) {
     if (nv < 1 || nv > SEG_STRIDE) return cudaErrorInvalidValue;
+    if (g.nblocks == 0) return cudaSuccess;
     count_launch();
-    k_seg_axpy<<<dim3(nbp, nprob), NT, 0, st>>>(segs, mask, V, ld, nv, h, sign, w);
+    k_seg_axpy<<<g.nblocks, NT, 0, st>>>(g, segs, V, ld, nv, h, sign, w);
     return cudaGetLastError();
 }
 
-cudaError_t launch_seg_scale(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask,
-                             const double* src, const double* n2, double sign, double* dst) {
+cudaError_t launch_seg_scale(cudaStream_t st, SegGrid g, const Seg* segs, const double* src, const double* n2,
+                             double sign, double* dst) {
+    if (g.nblocks == 0) return cudaSuccess;
     count_launch();
-    k_seg_scale<<<dim3(nbp, nprob), NT, 0, st>>>(segs, mask, src, n2, sign, dst);
+    k_seg_scale<<<g.nblocks, NT, 0, st>>>(g, segs, src, n2, sign, dst);
     return cudaGetLastError();
 }
 
-cudaError_t launch_seg_add_scaled(cudaStream_t st, int nprob, int nbp, const Seg* segs, const int* mask,
-                                  const double* x, const double* d, double alpha, double* out) {
+cudaError_t launch_seg_add_scaled(cudaStream_t st, SegGrid g, const Seg* segs, const double* x, const double* d,
+                                  double alpha, double* out) {
+    if (g.nblocks == 0) return cudaSuccess;
     count_launch();
-    k_seg_add_scaled<<<dim3(nbp, nprob), NT, 0, st>>>(segs, mask, x, d, alpha, out);
+    k_seg_add_scaled<<<g.nblocks, NT, 0, st>>>(g, segs, x, d, alpha, out);
     return cudaGetLastError();
 }
-
-namespace {
-}  // namespace
 
 cudaError_t launch_residual_global(cudaStream_t st, const ProbDev& P, const double* y, const double* p,
                                    const double* dy, const double* dp, double alpha, double eps,

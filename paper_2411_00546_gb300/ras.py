@@ -98,6 +98,17 @@ _SIGS = {
     "ras_profile": (_I, [_P, _I]),
     "ras_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)]),
     "ras_residual_static": (_I, [_I, _I, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "ras_server_create": (_I, [ctypes.c_size_t, _I, ctypes.POINTER(ras_opts), _P, ctypes.POINTER(_P)]),
+    "ras_server_request_bytes": (_I, [ctypes.POINTER(ras_problem_desc), ctypes.POINTER(ras_opts),
+                                      ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    "ras_server_submit": (_I, [_P, ctypes.POINTER(ras_problem_desc), ctypes.POINTER(ctypes.c_longlong)]),
+    "ras_server_step": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "ras_server_counts": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "ras_server_finished_ids": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), _I]),
+    "ras_server_fetch": (_I, [_P, ctypes.c_longlong, _P, _P, ctypes.POINTER(ras_stats)]),
+    "ras_server_device_bytes": (ctypes.c_size_t, [_P]),
+    "ras_server_last_error": (ctypes.c_char_p, [_P]),
+    "ras_server_destroy": (None, [_P]),
 }
 
 RAS_STATIC_MAX_N = 8192
@@ -365,3 +376,131 @@ def make_opts(**kw):
             raise KeyError(k)
         setattr(o, k, v)
     return o
+
+
+# ------------------------------------------------------------------ serving
+
+def _host_ptr(a, n):
+    """Pointer to a host float64 array of n elements (numpy array or CPU tensor)."""
+    import numpy as np
+    if hasattr(a, "is_cuda"):
+        if a.is_cuda:
+            raise ValueError("expected host data")
+        a = a.numpy()
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n:
+        raise ValueError("expected %d elements, got %d" % (n, a.size))
+    return a, ctypes.c_void_p(a.ctypes.data)
+
+
+def _desc(d, host):
+    """ras_problem_desc from a dict (n, sx, sy, overlap, phi, nu, mu, y_d[, f]);
+    returns the struct and the arrays it points to (keep them alive)."""
+    n = d["n"]
+    c = ras_problem_desc()
+    c.n, c.sx, c.sy, c.overlap, c.phi = n, d["sx"], d["sy"], d["overlap"], d["phi"]
+    c.nu, c.mu = d["nu"], d["mu"]
+    keep = []
+    if host:
+        for key in ("y_d", "f"):
+            if d.get(key) is not None:
+                arr, ptr = _host_ptr(d[key], n * n)
+                keep.append(arr)
+                setattr(c, key, ptr)
+    else:
+        c.y_d = _ptr(d["y_d"], n * n)
+        c.f = _ptr(d.get("f"), n * n)
+    return c, keep
+
+
+class Server:
+    """Opaque ras_server* (continuous batching of RASPEN solves)."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+        self.sizes = {}
+
+    def _check(self, rc, ok=(RAS_OK,)):
+        if rc not in ok:
+            raise RasError(rc, lib().ras_server_last_error(self.ptr).decode())
+        return rc
+
+
+def ras_server_create(hbm_budget, max_active, opts=None, stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    out = ctypes.c_void_p()
+    rc = lib().ras_server_create(int(hbm_budget), int(max_active), ctypes.byref(opts) if opts is not None else None,
+                                 ctypes.c_void_p(stream), ctypes.byref(out))
+    if rc != RAS_OK:
+        raise RasError(rc, "ras_server_create rejected its arguments")
+    return Server(out)
+
+
+def ras_server_request_bytes(d, opts=None):
+    """(slot_bytes, workspace_bytes) estimate of one request (host only)."""
+    c, _ = _desc(dict(d, y_d=None, f=None), host=True)
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    rc = lib().ras_server_request_bytes(ctypes.byref(c), ctypes.byref(opts) if opts is not None else None,
+                                        ctypes.byref(a), ctypes.byref(b))
+    if rc != RAS_OK:
+        raise RasError(rc, "invalid problem description")
+    return a.value, b.value
+
+
+def ras_server_submit(s, d):
+    """Queue one request; d: dict with n, sx, sy, overlap, phi, nu, mu and host
+    y_d (and optional f) arrays. Returns its id."""
+    c, keep = _desc(d, host=True)
+    rid = ctypes.c_longlong()
+    s._check(lib().ras_server_submit(s.ptr, ctypes.byref(c), ctypes.byref(rid)))
+    s.sizes[rid.value] = d["n"]
+    del keep
+    return rid.value
+
+
+def ras_server_step(s):
+    """Admission and one outer iteration; returns (admitted, finished_now)."""
+    a, f = _I(), _I()
+    s._check(lib().ras_server_step(s.ptr, ctypes.byref(a), ctypes.byref(f)))
+    return a.value, f.value
+
+
+def ras_server_counts(s):
+    p, a, f = _I(), _I(), _I()
+    s._check(lib().ras_server_counts(s.ptr, ctypes.byref(p), ctypes.byref(a), ctypes.byref(f)))
+    return p.value, a.value, f.value
+
+
+def ras_server_finished_ids(s, cap=4096):
+    ids = (ctypes.c_longlong * cap)()
+    k = lib().ras_server_finished_ids(s.ptr, ids, cap)
+    if k < 0:
+        s._check(k)
+    return list(ids[:k])
+
+
+def ras_server_fetch(s, rid):
+    """Result of a finished request: (status, y, p, stats) with host float64
+    numpy arrays of shape (n, n)."""
+    import numpy as np
+    n = s.sizes.pop(rid)
+    y = np.empty((n, n), dtype=np.float64)
+    p = np.empty((n, n), dtype=np.float64)
+    st = ras_stats()
+    rc = lib().ras_server_fetch(s.ptr, rid, ctypes.c_void_p(y.ctypes.data), ctypes.c_void_p(p.ctypes.data),
+                                ctypes.byref(st))
+    if rc == RAS_EINVAL:
+        raise RasError(rc, lib().ras_server_last_error(s.ptr).decode())
+    return rc, y, p, st
+
+
+def ras_server_device_bytes(s):
+    return lib().ras_server_device_bytes(s.ptr)
+
+
+def ras_server_destroy(s):
+    if s.ptr:
+        lib().ras_server_destroy(s.ptr)
+        s.ptr = None
