@@ -39,11 +39,11 @@ FP64_LANES = 2       # FP64 FMA per clock per SM on GB300 (1.2 TFLOP/s class)
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the n1023 workload (profiles/dram_jvp_n1023.md), valid
 # while the kernel's sources are unchanged since that capture.
-TRAFFIC = {"jvp": {"bytes_per_launch": 8562495616.0, "workload": "n1023",
+TRAFFIC = {"jvp": {"bytes_per_launch": 8562460160.0, "workload": "n1023",
                    "sources": ["paper_2411_00546_gb300/csrc/solve.cu",
                                "paper_2411_00546_gb300/csrc/ras_internal.cuh"],
                    "sha256": ["588457ff564180912d912e96443a5d2758f6e12796525f8f11a4079dcff6e691",
-                              "89a36b8d2a40fc2d51bf5f808a87799d0ea8420f60056fb72de9c77aec0c43be"]}}
+                              "44b7d7a75537c022eace1b7d8df8e0513d554912c9e388aa42c90e618cae0dfa"]}}
 
 # Counts of one RASPEN_eps solve (see run_reference).
 SOLVE_COUNTS = {"n1023": {"inner_its_sum": 1794, "evaluations": 3, "gmres_its": 147}}
