@@ -70,6 +70,7 @@ struct ras_problem {
     double* coefG = nullptr;
     double* partials = nullptr;
     int nbp = 0;                 // blocks per problem of the segmented kernels
+    int sms = 0;                 // SMs of the device (0 until queried)
     // block tables of the segmented kernels, one per mask row (0: GMRES/JVP,
     // 1: outer loop, 2: every problem), VEC_BLOCKS + nprob entries each
     int2* d_tab = nullptr;
@@ -406,15 +407,23 @@ void stats_clear(ras_stats* s, int count) {
 
 // Factorisation launches: FP32 one per register-tile class, FP64 one.
 template <typename T>
-int launch_factor(ras_problem* h, int only_active, double flops) {
+// nwork: most subdomains that factorise in this sweep (the active count, or
+// every subdomain); with at most one per SM the 1024-thread kernel is used.
+int launch_factor(ras_problem* h, int only_active, double flops, int nwork) {
     if (sizeof(T) == sizeof(float)) {
+        if (h->sms == 0) {
+            int dev = 0;
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
+        }
         bool first = true;   // the profile books the flops on the first launch of the sweep
         for (int c = 0; c < NTILE; ++c) {
             if (h->tile_cnt[c] == 0) continue;
+            const int wide = std::min(nwork, h->tile_cnt[c]) <= h->sms ? 1 : 0;
             CK(timed(h, RAS_K_FACTOR, first ? flops : 0.0, [&] {
                 return ras::launch_local_factor_f32(h->st, 2 * (c + 1), h->tile_cnt[c], h->d_lists + h->tile_off[c],
                                                     h->d_subs, h->d_probs, h->X, h->ls, h->cpool, h->coef,
-                                                    (float*)h->gpool, only_active);
+                                                    (float*)h->gpool, only_active, wide);
             }));
             first = false;
         }
@@ -456,7 +465,7 @@ int ras_apply_T(ras_problem* h, const std::vector<double>& pstart, double* Fout,
             TRY(read_ls(before));
             fl = factor_flops(h, &before, false);
         }
-        TRY(launch_factor<T>(h, 1, fl));
+        TRY(launch_factor<T>(h, 1, fl, *h->h_active));
         CK(timed(h, RAS_K_DIRECTION, 0.0, [&] {
             return ras::launch_local_direction<T>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs, h->ls, np,
                                                   h->coef, gp, h->Kpool, h->dpool, h->rpool, wp, h->d_err);
@@ -485,7 +494,7 @@ int ras_apply_T(ras_problem* h, const std::vector<double>& pstart, double* Fout,
         TRY(read_ls(before));
         fl_all = factor_flops(h, &before, true);
     }
-    TRY(launch_factor<T>(h, 0, fl_all));
+    TRY(launch_factor<T>(h, 0, fl_all, h->nsub));
     CK(timed(h, RAS_K_OTHER, 0.0, [&] {
         return ras::launch_local_prolong(h->st, h->nsub, h->d_subs, h->d_probs, h->ls, h->cpool, Fout);
     }));
@@ -565,9 +574,9 @@ int factor_at(ras_problem* h, double eps) {
     CK(cudaMemsetAsync(h->cpool, 0, h->Lsum * sizeof(double), h->st));
     CK(cudaMemcpyAsync(h->ls, ls.data(), h->nsub * sizeof(LocalState), cudaMemcpyHostToDevice, h->st));
     if (h->o.precision == RAS_MIXED) {
-        TRY(launch_factor<float>(h, 0, factor_flops(h, nullptr, false)));
+        TRY(launch_factor<float>(h, 0, factor_flops(h, nullptr, false), h->nsub));
     } else {
-        TRY(launch_factor<double>(h, 0, factor_flops(h, nullptr, false)));
+        TRY(launch_factor<double>(h, 0, factor_flops(h, nullptr, false), h->nsub));
     }
     CK(cudaMemcpyAsync(ls.data(), h->ls, h->nsub * sizeof(LocalState), cudaMemcpyDeviceToHost, h->st));
     TRY(sync(h));

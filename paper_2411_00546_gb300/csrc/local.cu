@@ -778,6 +778,282 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub
     }
 }
 
+// Entries of D_j (grid row j of the local Jacobian) inside the tile of
+// thread (ty, ty + DT) of a wide CTA (R x R tiles, any R): the 2 x 2 node
+// blocks on the diagonal (4 beta + phi', the control coupling
+// (1/nu)(1 - P_eps'(-p/mu)) in the y-row and phi'' p - 1 in the p-row) and
+// -beta two places off it (the x-neighbours of the same field).
+template <int R, int DT>
+__device__ __forceinline__ void add_band_any(float (&Mr)[R][R], int ty, int m, int wx, int j, float tdiag,
+                                             float tbeta, const double* ca, const double* cb, const double* cc) {
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+#pragma unroll
+        for (int b = 0; b < R; ++b) {
+            const int off = DT * R + b - a;
+            if (off < -2 || off > 2) continue;
+            const int r = ty * R + a, c = r + off;
+            if (r >= m || c < 0 || c >= m) continue;
+            const int q = j * wx + (r >> 1);
+            const bool yrow = (r & 1) == 0;
+            if (off == 0) Mr[a][b] += tdiag + (float)ca[q];
+            else if (off == 1) { if (yrow) Mr[a][b] += (float)cb[q]; }
+            else if (off == -1) { if (!yrow) Mr[a][b] += (float)cc[q]; }
+            else Mr[a][b] -= tbeta;
+        }
+    }
+}
+
+// FP32 factorisation with one 1024-thread CTA per subdomain (one CTA per SM):
+// thread (ty, tx) of the 32 x 32 CTA (tid = 32 tx + ty: a thread column is a
+// warp) holds the R x R tile (R = mp / 32) of the block row matrix in
+// registers. The algorithm is that of k_local_factor_panel (panels of R
+// pivots swept by the panel's column owners, here a whole warp, then one
+// rank-R update), with 32 warps sharing each block row: the dependent pivot
+// chain of a panel is R pivots of R x R work per lane, and the update is
+// spread over four times as many warps.
+template <int R>
+__global__ void __launch_bounds__(1024, 1) k_local_factor_wide(int nsub, const SubDev* __restrict__ subs,
+                                                               const ProbDev* __restrict__ probs,
+                                                               const double* X, LocalState* ls,
+                                                               const double* cpool, double* coef,
+                                                               float* gpool, int only_active,
+                                                               const int* __restrict__ list) {
+    constexpr int NTH = 1024, NWARP = 32;
+    constexpr int MM = 32 * R;
+    constexpr int PAD = ((R + 3) / 4) * 4;   // owner stride of the row panel
+    constexpr int LDR = 32 * PAD;            // one row of the row panel
+    constexpr int LDCT = 32 * R;             // one column of the swept panel: [a][ty]
+    constexpr int LDS = MM + 4;              // staging stride of the full block
+    constexpr int OFF_CT = 0;
+    constexpr int OFF_RW = OFF_CT + 2 * R * LDCT;
+    static_assert(OFF_RW + 2 * R * LDR <= MM * LDS, "panel buffers fit in the staging area");
+    __shared__ float fcol[MM];
+    __shared__ int pivr[MM];
+    __shared__ int sinv[MM];
+    __shared__ int used[MM];
+    __shared__ int sh_viol, sh_r, sh_fail;
+    __shared__ float sh_piv;
+    extern __shared__ __align__(16) float Ms[];
+    if ((int)blockIdx.x >= nsub) return;
+    const int i = list ? list[blockIdx.x] : (int)blockIdx.x;
+    if (only_active && !ls[i].active) return;
+    if (ls[i].status == ST_SKIP) return;
+    const SubDev s = subs[i];
+    const ProbDev P = probs[s.prob];
+    const int m = 2 * s.wx, W = s.wy, nn = s.wx * s.wy, mp = s.mp;
+    const int tid = threadIdx.x, ty = tid & 31, tx = tid >> 5, warp = tid >> 5, lane = tid & 31;
+
+    const double eps = ls[i].eps;
+    const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu;
+    double* ca = coef + 3 * s.noff;
+    double* cb = ca + nn;
+    double* cc = cb + nn;
+    {
+        const double* c = cpool + s.voff;
+        const LocalView V = make_view(s, P, X, c, nullptr, 0.0);
+        for (int q = tid; q < nn; q += NTH) {
+            const int lx = q % s.wx, ly = q / s.wx;
+            const double y = V.val(lx, ly, 0), p = V.val(lx, ly, 1);
+            double ph, d1, d2;
+            phi_eval(P.phi, P.kappa, y, ph, d1, d2);
+            ca[q] = d1;
+            cb[q] = inu * (1.0 - dP_eps(-p / mu, eps));
+            cc[q] = d2 * p - 1.0;
+        }
+    }
+    if (tid == 0) sh_fail = 0;
+    __syncthreads();   // coefficients visible to the whole CTA
+
+    const float tbeta = (float)beta, tbeta2 = (float)(beta * beta), tdiag = (float)(4.0 * beta);
+    const long long blk = (long long)mp * mp;
+    float* G = gpool + s.goff;
+    float Mr[R][R];
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int b = 0; b < R; ++b) Mr[a][b] = 0.f;
+    bool failed = false;
+    auto dval = [=](int j, int r, int c) -> float {
+        const int ix = r >> 1, f = r & 1, cx = c >> 1, cf = c & 1;
+        const int q = j * s.wx + ix;
+        if (cx == ix) {
+            if (cf == f) return tdiag + (float)ca[q];
+            return (f == 0) ? (float)cb[q] : (float)cc[q];
+        }
+        return (cf == f && (cx == ix - 1 || cx == ix + 1)) ? -tbeta : 0.f;
+    };
+    for (int j = 0; j < W && !failed; ++j) {
+        // S_j = D_j - beta^2 G_{j-1}: the tile holds G_{j-1} (zero for j = 0)
+#pragma unroll
+        for (int a = 0; a < R; ++a)
+#pragma unroll
+            for (int b = 0; b < R; ++b) Mr[a][b] = -tbeta2 * Mr[a][b];
+        const int dt = tx - ty;
+        if (dt == 0) add_band_any<R, 0>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
+        else if (dt == 1) add_band_any<R, 1>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
+        else if (dt == -1) add_band_any<R, -1>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
+        else if (R == 1 && dt == 2) add_band_any<R, 2>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
+        else if (R == 1 && dt == -2) add_band_any<R, -2>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
+        if (tid == 0) sh_viol = 0;
+
+        for (int kt = 0; kt < 32 && kt * R < m; ++kt) {
+            float* CsT = Ms + OFF_CT + (kt & 1) * (R * LDCT);
+            float* Rw = Ms + OFF_RW + (kt & 1) * (R * LDR);
+            if (ty == kt) {
+                if (tx == kt) {
+#pragma unroll
+                    for (int c = 0; c < R; ++c) {
+                        float z[R];
+#pragma unroll
+                        for (int b = 0; b < R; ++b) z[b] = 0.f;
+                        store_vec<R>(Rw + c * LDR + tx * PAD, z);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < R; ++c) store_vec<R>(Rw + c * LDR + tx * PAD, Mr[c]);
+                    // rows K restart from 0: the update below leaves C'[K,K] M[K,J]
+                    // there (M[K,J] + (C'[K,K] - I) M[K,J] would cancel, C'[K,K] ~ 1/(4 beta))
+#pragma unroll
+                    for (int a = 0; a < R; ++a)
+#pragma unroll
+                        for (int b = 0; b < R; ++b) Mr[a][b] = 0.f;
+                }
+            }
+            if (tx == kt) {
+                const bool ok = panel_sweep<R>(Mr, ty, kt, m, 0xffffffffu, kt);
+                if (!ok && ty == 0) sh_viol = 1;
+#pragma unroll
+                for (int c = 0; c < R; ++c)
+#pragma unroll
+                    for (int a = 0; a < R; ++a) CsT[c * LDCT + a * 32 + ty] = Mr[a][c];
+            }
+            __syncthreads();
+            if (sh_viol) break;
+            // rank-R update M += C' [M[K,:] with 0 at K]
+#pragma unroll
+            for (int c = 0; c < R; ++c) {
+                float rv[R];
+                load_vec<R>(Rw + c * LDR + tx * PAD, rv);
+#pragma unroll
+                for (int a = 0; a < R; ++a) {
+                    const float cv = CsT[c * LDCT + a * 32 + ty];
+#pragma unroll
+                    for (int b = 0; b < R; ++b) Mr[a][b] = fmaf(cv, rv[b], Mr[a][b]);
+                }
+            }
+        }
+        __syncthreads();   // the panel buffers are dead before the staging area is reused
+        if (sh_viol) {
+            // Redo this block row with partial pivoting in shared memory:
+            // S_j from G_{j-1} (in the factor pool) and D_j, implicit
+            // pivoting (rows never move), then G_j[r][c] = M[perm[r]][rinv[c]].
+            const float* Gp = G + (long long)(j > 0 ? j - 1 : 0) * blk;
+            for (int r = warp; r < m; r += NWARP) {
+                for (int c = lane; c < m; c += 32) {
+                    const float v = (j > 0) ? -tbeta2 * Gp[packed_index<float>(r, c, mp)] : 0.f;
+                    Ms[r * LDS + c] = v + dval(j, r, c);
+                }
+            }
+            for (int t = tid; t < m; t += NTH) used[t] = 0;
+            __syncthreads();
+            for (int k = 0; k < m; ++k) {
+                if (warp == 0) {
+                    unsigned bb = 0u;
+                    int bi = 0x7fffffff;
+                    for (int r = lane; r < m; r += 32) {
+                        if (!used[r]) {
+                            const unsigned u = __float_as_uint(fabsf(Ms[r * LDS + k]));
+                            if (u > bb) { bb = u; bi = r; }
+                        }
+                    }
+                    const unsigned mx = __reduce_max_sync(0xffffffffu, bb);
+                    const int r = (int)__reduce_min_sync(0xffffffffu, (unsigned)(bb == mx ? bi : 0x7fffffff));
+                    if (lane == 0) {
+                        if (mx == 0u || mx >= 0x7f800000u || r >= m) {
+                            sh_fail = 1;
+                        } else {
+                            sh_r = r;
+                            used[r] = 1;
+                            pivr[k] = r;
+                            sh_piv = Ms[r * LDS + k];
+                        }
+                    }
+                }
+                __syncthreads();
+                if (sh_fail) break;
+                const int r = sh_r;
+                const float inv = 1.f / sh_piv;
+                for (int t = tid; t < m; t += NTH) fcol[t] = Ms[t * LDS + k];
+                __syncthreads();
+                for (int t = tid; t < m; t += NTH) Ms[r * LDS + t] = (t == k ? 1.f : Ms[r * LDS + t]) * inv;
+                __syncthreads();
+                constexpr int NC = (MM + 31) / 32;
+                float prow[NC];
+#pragma unroll
+                for (int q = 0; q < NC; ++q) {
+                    const int t = lane + 32 * q;
+                    prow[q] = (t < m) ? Ms[r * LDS + t] : 0.f;
+                }
+                for (int rr = warp; rr < m; rr += NWARP) {
+                    if (rr == r) continue;
+                    const float fct = fcol[rr];
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) {
+                        const int t = lane + 32 * q;
+                        if (t < m) Ms[rr * LDS + t] = (t == k ? 0.f : Ms[rr * LDS + t]) - fct * prow[q];
+                    }
+                }
+                __syncthreads();
+            }
+            if (sh_fail) {
+                failed = true;
+                break;
+            }
+            for (int t = tid; t < m; t += NTH) sinv[pivr[t]] = t;   // rinv
+            __syncthreads();
+#pragma unroll
+            for (int a = 0; a < R; ++a) {
+                const int r = ty * R + a;
+#pragma unroll
+                for (int b = 0; b < R; ++b) {
+                    const int c = tx * R + b;
+                    Mr[a][b] = (r < m && c < m) ? Ms[pivr[r] * LDS + sinv[c]] : 0.f;
+                }
+            }
+            __syncthreads();
+        }
+        // G_j into shared memory, then packed to HBM
+#pragma unroll
+        for (int a2 = 0; a2 < R; ++a2) {
+            const int r = ty * R + a2;
+#pragma unroll
+            for (int b = 0; b < R; ++b) {
+                const int c = tx * R + b;
+                if (r < mp && c < mp) Ms[r * LDS + c] = (r < m && c < m) ? Mr[a2][b] : 0.f;
+            }
+        }
+        __syncthreads();
+        {
+            // entry e * 256 + t of the packed block (e = slab sl, vector v;
+            // t = 8 rho + kappa): row rho + 32 sl, columns kappa*cw + 4v .. +3
+            const int cw = mp >> 3, nv = cw >> 2, nslab = mp >> 5;
+            float4* Gj4 = reinterpret_cast<float4*>(G + (long long)j * blk);
+            for (int idx = tid; idx < nslab * nv * 256; idx += NTH) {
+                const int e = idx >> 8, t = idx & 255;
+                const int sl = e / nv, v = e - sl * nv;
+                const float* row = Ms + ((t >> 3) + 32 * sl) * LDS + (t & 7) * cw;
+                Gj4[idx] = *reinterpret_cast<const float4*>(row + 4 * v);
+            }
+        }
+        __syncthreads();
+    }
+    if (failed && tid == 0) {
+        ls[i].status = ST_ESINGULAR;
+        ls[i].active = 0;
+    }
+}
+
 template <typename T>
 size_t factor_smem(int maxm) {
     return (size_t)maxm * (maxm + 1) * sizeof(T) + (size_t)maxm * sizeof(T) + 3 * (size_t)maxm * sizeof(int);
@@ -807,9 +1083,32 @@ cudaError_t launch_factor_panel(cudaStream_t st, int count, const SubDev* subs, 
     return cudaGetLastError();
 }
 
+template <int R>
+cudaError_t launch_factor_wide(cudaStream_t st, int count, const SubDev* subs, const ProbDev* probs,
+                               const double* X, LocalState* ls, const double* cpool, double* coef,
+                               float* gpool, int only_active, const int* list) {
+    const size_t sm = (size_t)(32 * R) * (32 * R + 4) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_local_factor_wide<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_local_factor_wide<R><<<count, 1024, sm, st>>>(count, subs, probs, X, ls, cpool, coef, gpool, only_active,
+                                                    list);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_local_factor_f32(cudaStream_t st, int tile, int count, const int* list, const SubDev* subs,
                                     const ProbDev* probs, const double* X, LocalState* ls, const double* cpool,
-                                    double* coef, float* gpool, int only_active) {
+                                    double* coef, float* gpool, int only_active, int wide) {
+    if (wide) {
+        switch (tile) {
+            case 2: return launch_factor_wide<1>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+            case 4: return launch_factor_wide<2>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+            case 6: return launch_factor_wide<3>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+            case 8: return launch_factor_wide<4>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+            case 10: return launch_factor_wide<5>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (tile) {
         case 2: return launch_factor_panel<2>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
         case 4: return launch_factor_panel<4>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
@@ -827,7 +1126,7 @@ cudaError_t launch_local_factor(cudaStream_t st, int nsub, int maxm, const SubDe
     if (sizeof(T) == sizeof(float)) {
         const int mpmax = ((maxm + 31) / 32) * 32;
         return launch_local_factor_f32(st, mpmax / 16, nsub, nullptr, subs, probs, X, ls, cpool, coef,
-                                       reinterpret_cast<float*>(gpool), only_active);
+                                       reinterpret_cast<float*>(gpool), only_active, 0);
     }
     const size_t sm = factor_smem<T>(maxm);
     cudaError_t e = cudaFuncSetAttribute(k_local_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

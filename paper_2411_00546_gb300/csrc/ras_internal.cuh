@@ -220,9 +220,13 @@ cudaError_t launch_local_init(cudaStream_t st, int nsub, const SubDev* subs, con
                               double* cpool, double* Kpool, int* active_count);
 // FP32 register-tile factorisation of the `count` subdomains in `list`
 // (device indices; null = 0..count-1), all with packed size mp <= 16*tile.
+// FP32 factorisation of one register-tile class (tile = mp / 16) over the
+// `count` subdomains of `list`: 256-thread CTAs (two per SM) by default;
+// wide != 0 selects 1024-thread CTAs (one per SM), faster when at most one
+// CTA per SM has work.
 cudaError_t launch_local_factor_f32(cudaStream_t st, int tile, int count, const int* list, const SubDev* subs,
                                     const ProbDev* probs, const double* X, LocalState* ls, const double* cpool,
-                                    double* coef, float* gpool, int only_active);
+                                    double* coef, float* gpool, int only_active, int wide);
 template <typename T>
 cudaError_t launch_local_factor(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                                 const ProbDev* probs, const double* X, LocalState* ls,
