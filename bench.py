@@ -497,6 +497,14 @@ def main():
         e = {"bound": "hbm", "achieved": round(work / (ms / 1e3) / 1e9, 1), "peak": hbm_peak, "unit": "GB/s",
              "avg_launch_ms": round(ms / n, 4), "launches": n, "peak_source": src}
         e["frac"] = round(e["achieved"] / hbm_peak, 4)
+        if kind == "residual":
+            # FP64-pipe bound on GB300: about 42 FP64 operations per node (two
+            # square roots and a division among them) against 40 bytes
+            a64 = 42.0 * (work / 40.0) / (ms / 1e3) / 1e12
+            e.update({"bound": "fp64", "fp64_achieved_tflops": round(a64, 3),
+                      "fp64_peak_tflops": round(fp64_peak, 3), "fp64_frac": round(a64 / fp64_peak, 4),
+                      "hbm_frac": e["frac"]})
+            e["frac"] = e["fp64_frac"]
         if kind == "krylov":
             # one FP64 FMA per 8-byte basis element read: the FP64 pipe binds
             a64 = 2.0 * (work / 8.0) / (ms / 1e3) / 1e12

@@ -71,6 +71,8 @@ struct ras_problem {
     double* partials = nullptr;
     int nbp = 0;                 // blocks per problem of the segmented kernels
     int sms = 0;                 // SMs of the device (0 until queried)
+    int* d_order = nullptr;      // subdomain indices, largest factors first (solve kernels)
+    int* d_ticket = nullptr;     // work counter of the persistent solve kernels
     // block tables of the segmented kernels, one per mask row (0: GMRES/JVP,
     // 1: outer loop, 2: every problem), VEC_BLOCKS + nprob entries each
     int2* d_tab = nullptr;
@@ -375,7 +377,7 @@ int residual_norm(ras_problem* h, const double* x, const double* d, double alpha
     const long long N = plane(h, 0);
     CK(timed(h, RAS_K_RESIDUAL, resid_bytes(h), [&] {
         return ras::launch_residual_global(h->st, h->probs[0], x, x + N, d, d ? d + N : nullptr, alpha, eps, Fout,
-                                           Fout ? Fout + N : nullptr, h->partials);
+                                           Fout ? Fout + N : nullptr, h->partials, 1);
     }));
     CK(timed(h, RAS_K_OTHER, 0.0,
              [&] { return ras::launch_reduce_partials(h->st, h->partials, ras::VEC_BLOCKS, 2, h->scal); }));
@@ -468,7 +470,8 @@ int ras_apply_T(ras_problem* h, const std::vector<double>& pstart, double* Fout,
         TRY(launch_factor<T>(h, 1, fl, *h->h_active));
         CK(timed(h, RAS_K_DIRECTION, 0.0, [&] {
             return ras::launch_local_direction<T>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs, h->ls, np,
-                                                  h->coef, gp, h->Kpool, h->dpool, h->rpool, wp, h->d_err);
+                                                  h->coef, gp, h->Kpool, h->dpool, h->rpool, wp, h->d_err,
+                                                  h->d_order, h->d_ticket);
         }));
         const size_t dir_rec = h->prof_recs.size();
         CK(cudaMemsetAsync(h->d_active, 0, sizeof(int), h->st));
@@ -554,10 +557,10 @@ int jvp_internal(ras_problem* h, const double* D, double* O, const std::vector<i
         if (h->o.precision == RAS_MIXED)
             return ras::launch_local_jvp<float>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs,
                                                 (const float*)h->gpool, (float*)h->wpool, h->coef, h->dpool,
-                                                h->rpool, h->Ktpool, nir, D, O, dm, h->d_err);
+                                                h->rpool, h->Ktpool, nir, D, O, dm, h->d_err, h->d_order, h->d_ticket);
         return ras::launch_local_jvp<double>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs,
                                              (const double*)h->gpool, (double*)h->wpool, h->coef, h->dpool,
-                                             h->rpool, h->Ktpool, 0, D, O, dm, h->d_err);
+                                             h->rpool, h->Ktpool, 0, D, O, dm, h->d_err, h->d_order, h->d_ticket);
     }));
     return RAS_OK;
 }
@@ -590,9 +593,11 @@ int precond_internal(ras_problem* h, const double* R, double* Zo) {
     CK(timed(h, RAS_K_PRECOND, solve_bytes(h, nullptr), [&] {
         if (h->o.precision == RAS_MIXED)
             return ras::launch_local_precond<float>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs,
-                                                    (const float*)h->gpool, (float*)h->wpool, R, Zo, h->d_err);
+                                                    (const float*)h->gpool, (float*)h->wpool, R, Zo, h->d_err,
+                                                    h->d_order, h->d_ticket);
         return ras::launch_local_precond<double>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs,
-                                                 (const double*)h->gpool, (double*)h->wpool, R, Zo, h->d_err);
+                                                 (const double*)h->gpool, (double*)h->wpool, R, Zo, h->d_err,
+                                                 h->d_order, h->d_ticket);
     }));
     return RAS_OK;
 }
@@ -1058,6 +1063,8 @@ int ensure_pools(ras_problem* h, bool own_data) {
     TRY(ensure(h, &h->d_probs, count));
     TRY(ensure(h, &h->d_segs, count));
     TRY(ensure(h, &h->d_lists, std::max<size_t>(1, h->h_lists.size())));
+    TRY(ensure(h, &h->d_order, h->nsub));
+    TRY(ensure(h, &h->d_ticket, 1));
     for (double** q : {&h->cpool, &h->dpool, &h->Kpool, &h->Ktpool, &h->rpool}) TRY(ensure(h, q, h->Lsum));
     TRY(ensure(h, &h->coef, 3 * h->Nsum));
     TRY(ensure(h, &h->ls, h->nsub));
@@ -1097,6 +1104,15 @@ int ensure_pools(ras_problem* h, bool own_data) {
 
 int upload_layout(ras_problem* h) {
     TRY(build_grid(h, 2, std::vector<int>(h->nprob, 1)));
+    // solve order: largest factor (wy * mp^2) first, ties by index
+    std::vector<int> order(h->nsub);
+    for (int k = 0; k < h->nsub; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long long)h->subs[a].wy * h->subs[a].mp * h->subs[a].mp >
+               (long long)h->subs[b].wy * h->subs[b].mp * h->subs[b].mp;
+    });
+    CK(cudaMemcpyAsync(h->d_order, order.data(), h->nsub * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    TRY(sync(h));
     CK(cudaMemcpyAsync(h->d_subs, h->subs.data(), h->nsub * sizeof(SubDev), cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->d_probs, h->probs.data(), h->nprob * sizeof(ProbDev), cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->d_segs, h->segs.data(), h->nprob * sizeof(Seg), cudaMemcpyHostToDevice, h->st));
@@ -1205,7 +1221,7 @@ int ras_residual(ras_problem* h, const double* y, const double* p, double eps, d
     TRY(need_single(h));
     CK(timed(h, RAS_K_RESIDUAL, resid_bytes(h), [&] {
         return ras::launch_residual_global(h->st, h->probs[0], y, p, nullptr, nullptr, 0.0, eps, Fy, Fp,
-                                           h->partials);
+                                           h->partials, 0);
     }));
     CK(timed(h, RAS_K_OTHER, 0.0,
              [&] { return ras::launch_reduce_partials(h->st, h->partials, ras::VEC_BLOCKS, 2, h->scal); }));

@@ -64,7 +64,7 @@ __device__ __forceinline__ LocalView make_view(const SubDev& s, const ProbDev& P
 __device__ void local_residual(const LocalView& V, const ProbDev& P, double eps, double* out,
                                double& nrm2, double& flr2, double* red) {
     const int wx = V.wx, nn = wx * V.wy;
-    const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu;
+    const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu, imu = 1.0 / P.mu;
     double a = 0.0, b = 0.0;
     for (int q = threadIdx.x; q < nn; q += NT) {
         const int lx = q % wx, ly = q / wx;
@@ -76,7 +76,7 @@ __device__ void local_residual(const LocalView& V, const ProbDev& P, double eps,
         double ph, d1, d2;
         phi_eval(P.phi, P.kappa, yc, ph, d1, d2);
         const double fv = P.f ? P.f[g] : 0.0;
-        const double pe_ = P_eps(-pc / mu, eps);
+        const double pe_ = P_eps(-pc * imu, eps);
         const double Fy = beta * (4.0 * yc - yw - ye - ys - yn) + ph - fv + inu * (pc + mu * pe_);
         const double Fp = beta * (4.0 * pc - pw - pe - ps - pn) + d1 * pc - yc + P.yd[g];
         const double My = beta * (4.0 * fabs(yc) + fabs(yw) + fabs(ye) + fabs(ys) + fabs(yn)) + fabs(ph) +

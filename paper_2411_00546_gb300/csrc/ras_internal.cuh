@@ -173,7 +173,7 @@ void count_launch();
 // global (grid) kernels: residual.cu
 cudaError_t launch_residual_global(cudaStream_t st, const ProbDev& P, const double* y, const double* p,
                                    const double* dy, const double* dp, double alpha, double eps,
-                                   double* Fy, double* Fp, double* partials);
+                                   double* Fy, double* Fp, double* partials, int floor);
 cudaError_t launch_reduce_partials(cudaStream_t st, const double* partials, int nparts, int nvals,
                                    double* out);
 cudaError_t launch_coef_global(cudaStream_t st, const ProbDev& P, const double* y, const double* p,
@@ -231,11 +231,16 @@ template <typename T>
 cudaError_t launch_local_factor(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                                 const ProbDev* probs, const double* X, LocalState* ls,
                                 const double* cpool, double* coef, T* gpool, int only_active);
+// The local-solve kernels (direction, Jacobian action, linear RAS) are
+// persistent: the grid holds as many CTAs as fit at once, and each takes the
+// next of the nsub positions of `order` (subdomain indices, largest factors
+// first) from *ticket, which the launcher zeroes on the stream.
 template <typename T>
 cudaError_t launch_local_direction(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                                    const ProbDev* probs, LocalState* ls, NewtonParams np,
                                    const double* coef, const T* gpool, const double* Kpool,
-                                   double* dpool, double* rpool, T* wpool, int* err);
+                                   double* dpool, double* rpool, T* wpool, int* err, const int* order,
+                                   int* ticket);
 cudaError_t launch_local_linesearch(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,
                                     const double* X, LocalState* ls, NewtonParams np, double* cpool,
                                     const double* dpool, double* Kpool, double* Ktpool,
@@ -246,9 +251,9 @@ template <typename T>
 cudaError_t launch_local_jvp(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                              const ProbDev* probs, const T* gpool, T* wpool, const double* coef,
                              double* zpool, double* rpool, double* bpool, int nir, const double* D,
-                             double* O, const int* pmask, int* err);
+                             double* O, const int* pmask, int* err, const int* order, int* ticket);
 template <typename T>
 cudaError_t launch_local_precond(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                                  const ProbDev* probs, const T* gpool, T* wpool, const double* R,
-                                 double* Z, int* err);
+                                 double* Z, int* err, const int* order, int* ticket);
 }  // namespace ras

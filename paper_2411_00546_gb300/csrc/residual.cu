@@ -17,8 +17,11 @@ __device__ __forceinline__ double gval(const double* Z, int n, int i, int j) {
 }
 
 // F at x + alpha d (d may be null). Writes Fy/Fp when non-null; per-block
-// partial sums of ||F||^2 and of the rounding-floor estimate into
-// partials[blockIdx] and partials[NB + blockIdx].
+// partial sums of ||F||^2 into partials[blockIdx] and, with FLOOR, of the
+// rounding-floor estimate (nodewise sums of |terms|) into
+// partials[NB + blockIdx]. Block b takes the grid rows b, b + NB, ...; its
+// threads take the nodes of a row, so no node index is divided.
+template <bool FLOOR>
 __global__ void __launch_bounds__(NT) k_residual_global(ProbDev P, const double* __restrict__ y,
                                                         const double* __restrict__ p,
                                                         const double* __restrict__ dy,
@@ -27,8 +30,7 @@ __global__ void __launch_bounds__(NT) k_residual_global(ProbDev P, const double*
                                                         double* partials) {
     __shared__ double red[2 * NT];
     const int n = P.n;
-    const long long nn = (long long)n * n;
-    const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu;
+    const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu, imu = 1.0 / P.mu;
     auto vy = [=](int i, int j) -> double {
         if (i < 0 || i >= n || j < 0 || j >= n) return 0.0;
         const long long g = (long long)j * n + i;
@@ -40,24 +42,28 @@ __global__ void __launch_bounds__(NT) k_residual_global(ProbDev P, const double*
         return dp ? fma(alpha, dp[g], p[g]) : p[g];
     };
     double a = 0.0, b = 0.0;
-    for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < nn; g += (long long)NB * NT) {
-        const int i = (int)(g % n), j = (int)(g / n);
-        const double yc = vy(i, j), yw = vy(i - 1, j), ye = vy(i + 1, j), ys = vy(i, j - 1), yn = vy(i, j + 1);
-        const double pc = vp(i, j), pw = vp(i - 1, j), pe = vp(i + 1, j), ps = vp(i, j - 1), pn = vp(i, j + 1);
-        double ph, d1, d2;
-        phi_eval(P.phi, P.kappa, yc, ph, d1, d2);
-        const double fv = P.f ? P.f[g] : 0.0;
-        const double pe_ = P_eps(-pc / mu, eps);
-        const double Fyv = beta * (4.0 * yc - yw - ye - ys - yn) + ph - fv + inu * (pc + mu * pe_);
-        const double Fpv = beta * (4.0 * pc - pw - pe - ps - pn) + d1 * pc - yc + P.yd[g];
-        const double My = beta * (4.0 * fabs(yc) + fabs(yw) + fabs(ye) + fabs(ys) + fabs(yn)) + fabs(ph) +
-                          fabs(fv) + inu * (fabs(pc) + mu * fabs(pe_));
-        const double Mp = beta * (4.0 * fabs(pc) + fabs(pw) + fabs(pe) + fabs(ps) + fabs(pn)) +
-                          fabs(d1 * pc) + fabs(yc) + fabs(P.yd[g]);
-        if (Fy) Fy[g] = Fyv;
-        if (Fp) Fp[g] = Fpv;
-        a += Fyv * Fyv + Fpv * Fpv;
-        b += My * My + Mp * Mp;
+    for (int j = blockIdx.x; j < n; j += NB) {
+        for (int i = threadIdx.x; i < n; i += NT) {
+            const long long g = (long long)j * n + i;
+            const double yc = vy(i, j), yw = vy(i - 1, j), ye = vy(i + 1, j), ys = vy(i, j - 1), yn = vy(i, j + 1);
+            const double pc = vp(i, j), pw = vp(i - 1, j), pe = vp(i + 1, j), ps = vp(i, j - 1), pn = vp(i, j + 1);
+            double ph, d1, d2;
+            phi_eval(P.phi, P.kappa, yc, ph, d1, d2);
+            const double fv = P.f ? P.f[g] : 0.0;
+            const double pe_ = P_eps(-pc * imu, eps);
+            const double Fyv = beta * (4.0 * yc - yw - ye - ys - yn) + ph - fv + inu * (pc + mu * pe_);
+            const double Fpv = beta * (4.0 * pc - pw - pe - ps - pn) + d1 * pc - yc + P.yd[g];
+            if (Fy) Fy[g] = Fyv;
+            if (Fp) Fp[g] = Fpv;
+            a += Fyv * Fyv + Fpv * Fpv;
+            if (FLOOR) {
+                const double My = beta * (4.0 * fabs(yc) + fabs(yw) + fabs(ye) + fabs(ys) + fabs(yn)) + fabs(ph) +
+                                  fabs(fv) + inu * (fabs(pc) + mu * fabs(pe_));
+                const double Mp = beta * (4.0 * fabs(pc) + fabs(pw) + fabs(pe) + fabs(ps) + fabs(pn)) +
+                                  fabs(d1 * pc) + fabs(yc) + fabs(P.yd[g]);
+                b += My * My + Mp * Mp;
+            }
+        }
     }
     block_sum2<NT>(a, b, red);
     if (threadIdx.x == 0) {
@@ -352,9 +358,12 @@ cudaError_t launch_seg_add_scaled(cudaStream_t st, SegGrid g, const Seg* segs, c
 
 cudaError_t launch_residual_global(cudaStream_t st, const ProbDev& P, const double* y, const double* p,
                                    const double* dy, const double* dp, double alpha, double eps,
-                                   double* Fy, double* Fp, double* partials) {
+                                   double* Fy, double* Fp, double* partials, int floor) {
     count_launch();
-    k_residual_global<<<NB, NT, 0, st>>>(P, y, p, dy, dp, alpha, eps, Fy, Fp, partials);
+    if (floor)
+        k_residual_global<true><<<NB, NT, 0, st>>>(P, y, p, dy, dp, alpha, eps, Fy, Fp, partials);
+    else
+        k_residual_global<false><<<NB, NT, 0, st>>>(P, y, p, dy, dp, alpha, eps, Fy, Fp, partials);
     return cudaGetLastError();
 }
 

@@ -8,15 +8,18 @@
 // The solve is a chain of 2W-1 dependent matrix-vector products; each reads
 // one mp x mp block (100 KB in FP32 at mp = 160) that does not depend on the
 // chain. The blocks are therefore streamed ahead of the chain: every block is
-// stored as mp/32 contiguous slabs (packed_index), and a ring of DEPTH slab
-// buffers in shared memory is filled by TMA bulk copies (cp.async.bulk,
-// completion on an mbarrier) issued DEPTH slabs ahead of the slab being used.
+// stored as mp/32 contiguous slabs (packed_index), and a ring of D slab
+// buffers in shared memory (as many as fit in RING_BYTES) is filled by TMA
+// bulk copies (cp.async.bulk, completion on an mbarrier) issued D slabs ahead
+// of the slab being used.
 // Thread t = 8 rho + kappa multiplies its own contiguous part of a slab (row
 // rho + 32 s, column chunk kappa) with the vector and the 8 partial sums of a
 // row are added with warp shuffles. Every mbarrier wait is bounded; on timeout
 // the CTA waits (bounded) for its copies in flight, records ST_ETIMEOUT in
 // *err and returns.
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "ras_internal.cuh"
 
@@ -26,12 +29,18 @@ namespace {
 
 constexpr int NT = LOC_THREADS;
 static_assert(NT == 256, "packed layout assumes 256 threads");
+static_assert(MAX_M <= NT, "one entry of a block row per thread");
 constexpr long long WAIT_LIMIT = 1LL << 22;   // try_wait rounds before giving up
 
+// The slab ring: RING_BYTES of shared memory split into as many slab slots as
+// fit for the block size at hand (at most MAXD), so narrow blocks keep more
+// slabs in flight. Two CTAs fit on an SM.
 template <typename T>
 struct Ring {
-    static constexpr int DEPTH = (sizeof(T) == 4) ? 4 : 2;
+    static constexpr int RING_BYTES = 80 * 1024;
+    static constexpr int MAXD = 16;
     static constexpr int SLAB_MAX = 256 * ((MAX_M / 8) / (16 / (int)sizeof(T))) * 16;  // bytes
+    static_assert(RING_BYTES >= 2 * SLAB_MAX, "at least two slabs in flight");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -83,57 +92,64 @@ __device__ __forceinline__ T shfl_x(T v, int m) {
     return __shfl_xor_sync(0xffffffffu, v, m);
 }
 
-// Shared state of one CTA's slab stream. `seq` counts slabs over the CTA's
-// whole life, so ring slot and mbarrier parity stay consistent across solves.
+// Shared state of one CTA's slab stream. Every solve uses slots 0..D-1 round
+// robin and consumes every slab it issues, so between solves all slots are
+// idle and D may change; `phase` (uniform over the CTA) holds the parity that
+// each slot's mbarrier completes next.
 template <typename T>
 struct Stream {
-    unsigned char* ring;   // DEPTH slabs
-    uint64_t* full;        // DEPTH mbarriers
+    unsigned char* ring;   // RING_BYTES of slab slots
+    uint64_t* full;        // MAXD mbarriers
     int* fail;             // shared flag
-    uint32_t seq;          // slabs consumed so far (uniform)
+    uint32_t phase;        // bit k: parity of slot k's next completion
 };
 
 template <typename T>
 __device__ void stream_init(Stream<T>& S, unsigned char* smem) {
-    constexpr int D = Ring<T>::DEPTH;
+    constexpr int MD = Ring<T>::MAXD;
     S.ring = smem;
-    S.full = reinterpret_cast<uint64_t*>(smem + D * Ring<T>::SLAB_MAX);
-    S.fail = reinterpret_cast<int*>(S.full + D);
-    S.seq = 0;
+    S.full = reinterpret_cast<uint64_t*>(smem + Ring<T>::RING_BYTES);
+    S.fail = reinterpret_cast<int*>(S.full + MD);
+    S.phase = 0u;
     if (threadIdx.x == 0) {
-        for (int k = 0; k < D; ++k) mbar_init(&S.full[k], 1);
+        for (int k = 0; k < MD; ++k) mbar_init(&S.full[k], 1);
         *S.fail = 0;
         fence_barrier_init();
     }
     __syncthreads();
 }
 
-// On a timeout: wait (bounded) for the copies still in flight, then report.
+// On a timeout: wait (bounded) for the copies still in flight (relative
+// slabs first .. last-1, slab `first` in slot k0 of a ring of D), then report.
 template <typename T>
-__device__ void stream_abort(Stream<T>& S, uint32_t first, uint32_t last, int* err) {
-    constexpr int D = Ring<T>::DEPTH;
+__device__ void stream_abort(Stream<T>& S, uint32_t first, uint32_t last, uint32_t k0, uint32_t D, int* err) {
     if (threadIdx.x == 0) {
-        for (uint32_t g = first; g < last; ++g) mbar_wait(&S.full[g % D], (g / D) & 1u);
+        uint32_t k = k0;
+        for (uint32_t q = first; q < last; ++q, k = (k + 1 == D) ? 0u : k + 1)
+            mbar_wait(&S.full[k], (S.phase >> k) & 1u);
         if (err) atomicExch(err, ST_ETIMEOUT);
     }
     __syncthreads();
 }
 
-// z = J_i^-1 b (see the file comment). rhs(j, t) -> T gives b; out(j, t, z)
-// consumes z. vec, tmp: shared arrays of mp T. w: global scratch, m*W T.
-// Returns false if a wait timed out (the CTA must then return).
-template <typename T, class Rhs, class Out>
+// z = J_i^-1 b (see the file comment). rhs(j, t) -> T gives b; pre(j, t) ->
+// double loads what out needs besides z; out(j, t, z, pre) consumes z. rhs,
+// pre and the read-back of w are called one block row ahead, so their global
+// loads overlap the streamed products instead of stalling every row.
+// vec, tmp: shared arrays of mp T. w: global scratch, m*W T. m <= NT: thread
+// t handles entry t of every block row. Returns false if a wait timed out
+// (the CTA must then return).
+template <typename T, class Rhs, class Pre, class Out>
 __device__ bool stream_solve(Stream<T>& S, const T* __restrict__ G, int m, int mp, int W, T beta, T* w, T* vec,
-                             T* tmp, Rhs rhs, Out out, int* err) {
-    constexpr int D = Ring<T>::DEPTH;
+                             T* tmp, Rhs rhs, Pre pre, Out out, int* err) {
     constexpr int VE = 16 / (int)sizeof(T);
     const int tid = threadIdx.x, kappa = tid & 7, rho = tid >> 3;
     const int cw = mp >> 3, nv = cw / VE, nslab = mp >> 5;
     const uint32_t slab_elems = 256u * nv * VE;
     const uint32_t slab_bytes = slab_elems * sizeof(T);
+    const uint32_t D = min((uint32_t)Ring<T>::MAXD, (uint32_t)Ring<T>::RING_BYTES / slab_bytes);
     const long long blk = (long long)mp * mp;
     const uint32_t total = (uint32_t)((2 * W - 1) * nslab);
-    const uint32_t base = S.seq;
     // slab q of this solve: forward blocks 0..W-2, then backward W-1..0
     auto src = [&](uint32_t q) -> const T* {
         const int f = (W - 1) * nslab;
@@ -150,18 +166,15 @@ __device__ bool stream_solve(Stream<T>& S, const T* __restrict__ G, int m, int m
     };
     if (tid == 0) {
         fence_proxy_async();
-        for (uint32_t q = 0; q < total && q < (uint32_t)D; ++q) {
-            const uint32_t g = base + q;
-            tma_load_1d(S.ring + (g % D) * Ring<T>::SLAB_MAX, src(q), slab_bytes, &S.full[g % D]);
-        }
+        for (uint32_t q = 0; q < total && q < D; ++q)
+            tma_load_1d(S.ring + q * slab_bytes, src(q), slab_bytes, &S.full[q]);
     }
-    uint32_t q = 0;
+    uint32_t q = 0, k = 0;   // slab q of this solve sits in slot k = q mod D
     // one mp x mp product from the stream: tmp = G_(next block) vec
     auto matvec = [&]() -> bool {
-        for (int sl = 0; sl < nslab; ++sl, ++q) {
-            const uint32_t g = base + q;
-            const bool ok = mbar_wait(&S.full[g % D], (g / D) & 1u);
-            const T* slot = reinterpret_cast<const T*>(S.ring + (g % D) * Ring<T>::SLAB_MAX);
+        for (int sl = 0; sl < nslab; ++sl, ++q, k = (k + 1 == D) ? 0u : k + 1) {
+            const bool ok = mbar_wait(&S.full[k], (S.phase >> k) & 1u);
+            const T* slot = reinterpret_cast<const T*>(S.ring + k * slab_bytes);
             T acc = (T)0;
             if (ok) {
                 const T* vk = vec + kappa * cw;
@@ -173,14 +186,13 @@ __device__ bool stream_solve(Stream<T>& S, const T* __restrict__ G, int m, int m
             }
             if (__syncthreads_or(!ok)) {
                 // copies issued so far: relative slabs < min(total, q + D)
-                stream_abort(S, g, base + min(total, q + (uint32_t)D), err);
-                S.seq = base + total;
+                stream_abort(S, q, min(total, q + D), k, D, err);
                 return false;
             }
+            S.phase ^= 1u << k;
             if (tid == 0 && q + D < total) {
                 fence_proxy_async();
-                const uint32_t gn = g + D;
-                tma_load_1d(S.ring + (gn % D) * Ring<T>::SLAB_MAX, src(q + D), slab_bytes, &S.full[gn % D]);
+                tma_load_1d(S.ring + k * slab_bytes, src(q + D), slab_bytes, &S.full[k]);
             }
             acc += shfl_x(acc, 1);
             acc += shfl_x(acc, 2);
@@ -191,34 +203,54 @@ __device__ bool stream_solve(Stream<T>& S, const T* __restrict__ G, int m, int m
         return true;
     };
     for (int t = m + tid; t < mp; t += NT) vec[t] = (T)0;
+    const bool mine = tid < m;
+    T nb = mine ? rhs(0, tid) : (T)0;   // b of the next block row
     for (int j = 0; j < W; ++j) {
-        for (int t = tid; t < m; t += NT) {
-            T v = rhs(j, t);
-            if (j > 0) v += beta * tmp[t];
-            vec[t] = v;
-            w[j * m + t] = v;
+        if (mine) {
+            T v = nb;
+            if (j > 0) v += beta * tmp[tid];
+            vec[tid] = v;
+            w[j * m + tid] = v;
+            if (j + 1 < W) nb = rhs(j + 1, tid);
         }
         __syncthreads();
         if (j < W - 1 && !matvec()) return false;
     }
+    T nw = mine ? w[(W - 1) * m + tid] : (T)0;   // w and pre of the next block row (backward)
+    double np_ = mine ? pre(W - 1, tid) : 0.0;
     for (int j = W - 1; j >= 0; --j) {
-        for (int t = tid; t < m; t += NT) {
-            T v = w[j * m + t];
-            if (j < W - 1) v += beta * tmp[t];
-            vec[t] = v;
+        double cur = 0.0;
+        if (mine) {
+            T v = nw;
+            if (j < W - 1) v += beta * tmp[tid];
+            vec[tid] = v;
+            cur = np_;
+            if (j > 0) {
+                nw = w[(j - 1) * m + tid];
+                np_ = pre(j - 1, tid);
+            }
         }
         __syncthreads();
         if (!matvec()) return false;
-        for (int t = tid; t < m; t += NT) out(j, t, tmp[t]);
+        if (mine) out(j, tid, tmp[tid], cur);
     }
     __syncthreads();
-    S.seq = base + total;
     return true;
 }
 
 template <typename T>
 size_t solve_smem() {
-    return (size_t)Ring<T>::DEPTH * Ring<T>::SLAB_MAX + Ring<T>::DEPTH * sizeof(uint64_t) + 16;
+    return (size_t)Ring<T>::RING_BYTES + Ring<T>::MAXD * sizeof(uint64_t) + 16;
+}
+
+// Persistent work distribution of the solve kernels: every CTA takes the next
+// position of `order` (subdomain indices, largest factors first) from a
+// ticket counter that the launcher zeroes, until the list is exhausted.
+__device__ __forceinline__ int next_position(int* ticket, int* slot) {
+    __syncthreads();   // every thread is done with the previous subdomain
+    if (threadIdx.x == 0) *slot = atomicAdd(ticket, 1);
+    __syncthreads();
+    return *slot;
 }
 
 // r = bsign * B - J_i z in FP64 with the Jacobian coefficients stored by the
@@ -258,13 +290,18 @@ __global__ void __launch_bounds__(NT) k_local_direction(int nsub, const SubDev* 
                                                         const ProbDev* __restrict__ probs, LocalState* ls,
                                                         NewtonParams np, const double* coef, const T* gpool,
                                                         const double* Kpool, double* dpool, double* rpool,
-                                                        T* wpool, int* err) {
+                                                        T* wpool, int* err, const int* order, int* ticket) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ T vec[MAX_M], tmp[MAX_M];
     __shared__ double red[2 * NT];
-    const int i = blockIdx.x;
-    if (i >= nsub) return;
-    if (!ls[i].active) return;
+    __shared__ int sh_next;
+    Stream<T> S;
+    stream_init(S, smem);
+    for (;;) {
+    const int pos = next_position(ticket, &sh_next);
+    if (pos >= nsub) break;
+    const int i = order[pos];
+    if (!ls[i].active) continue;
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
     const int m = 2 * s.wx, W = s.wy, L = m * W;
@@ -274,8 +311,6 @@ __global__ void __launch_bounds__(NT) k_local_direction(int nsub, const SubDev* 
     double* r = rpool + s.voff;
     T* w = wpool + s.voff;
     const T* G = gpool + s.goff;
-    Stream<T> S;
-    stream_init(S, smem);
     double b2 = 0.0, dummy = 0.0;
     for (int q = threadIdx.x; q < L; q += NT) {
         const double v = -K[q];
@@ -290,7 +325,8 @@ __global__ void __launch_bounds__(NT) k_local_direction(int nsub, const SubDev* 
         ++nsolves;
         if (!stream_solve<T>(
                 S, G, m, s.mp, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)r[j * m + t]; },
-                [=](int j, int t, T z) { d[j * m + t] += (double)z; }, err)) {
+                [=](int j, int t) { return d[j * m + t]; },
+                [=](int j, int t, T z, double old) { d[j * m + t] = old + (double)z; }, err)) {
             if (threadIdx.x == 0) {
                 ls[i].status = ST_ETIMEOUT;
                 ls[i].active = 0;
@@ -302,6 +338,7 @@ __global__ void __launch_bounds__(NT) k_local_direction(int nsub, const SubDev* 
         if (sqrt(r2) <= np.ir_rtol * bnorm) break;
     }
     if (threadIdx.x == 0) ls[i].solves += nsolves;
+    }
 }
 
 // Jacobian action of the RASPEN function (Alg. 4):
@@ -314,14 +351,19 @@ __global__ void __launch_bounds__(NT) k_local_jvp(int nsub, const SubDev* __rest
                                                   const ProbDev* __restrict__ probs, const T* gpool, T* wpool,
                                                   const double* coef, double* zpool, double* rpool,
                                                   double* bpool, int nir, const double* D, double* O,
-                                                  const int* pmask, int* err) {
+                                                  const int* pmask, int* err, const int* order, int* ticket) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ T vec[MAX_M], tmp[MAX_M];
     __shared__ double red[2 * NT];
-    const int i = blockIdx.x;
-    if (i >= nsub) return;
+    __shared__ int sh_next;
+    Stream<T> S;
+    stream_init(S, smem);
+    for (;;) {
+    const int pos = next_position(ticket, &sh_next);
+    if (pos >= nsub) break;
+    const int i = order[pos];
     const SubDev s = subs[i];
-    if (pmask && !pmask[s.prob]) return;
+    if (pmask && !pmask[s.prob]) continue;
     const ProbDev P = probs[s.prob];
     const int n = P.n, m = 2 * s.wx, W = s.wy;
     const long long nn = (long long)n * n;
@@ -330,8 +372,6 @@ __global__ void __launch_bounds__(NT) k_local_jvp(int nsub, const SubDev* __rest
     double* Oy = O + P.ofs;
     const T* G = gpool + s.goff;
     T* w = wpool + s.voff;
-    Stream<T> S;
-    stream_init(S, smem);
     auto bval = [=](int j, int t) -> double {
         const int lx = t >> 1, f = t & 1;
         const int gx = s.x0 + lx, gy = s.y0 + j;
@@ -343,19 +383,32 @@ __global__ void __launch_bounds__(NT) k_local_jvp(int nsub, const SubDev* __rest
         if (j == W - 1 && gy < n - 1) b += Df[(long long)(gy + 1) * n + gx];
         return -beta * b;
     };
-    auto owned_out = [=](int j, int t, double z) {
+    // owned node of local entry (j, t): its global index, else -1
+    auto owned = [=](int j, int t) -> long long {
         const int lx = t >> 1, f = t & 1;
         const int gx = s.x0 + lx, gy = s.y0 + j;
-        if (gx >= s.ox0 && gx < s.ox0 + s.owx && gy >= s.oy0 && gy < s.oy0 + s.owy) {
-            const long long g = f * nn + (long long)gy * n + gx;
-            Oy[g] = -Dy[g] - z;
-        }
+        if (gx >= s.ox0 && gx < s.ox0 + s.owx && gy >= s.oy0 && gy < s.oy0 + s.owy)
+            return f * nn + (long long)gy * n + gx;
+        return -1;
+    };
+    auto owned_out = [=](int j, int t, double z) {
+        const long long g = owned(j, t);
+        if (g >= 0) Oy[g] = -Dy[g] - z;
     };
     if (nir == 0) {
-        stream_solve<T>(
-            S, G, m, s.mp, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)bval(j, t); },
-            [=](int j, int t, T z) { owned_out(j, t, (double)z); }, err);
-        return;
+        if (!stream_solve<T>(
+                S, G, m, s.mp, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)bval(j, t); },
+                [=](int j, int t) {
+                    const long long g = owned(j, t);
+                    return g >= 0 ? -Dy[g] : 0.0;
+                },
+                [=](int j, int t, T z, double mdy) {
+                    const long long g = owned(j, t);
+                    if (g >= 0) Oy[g] = mdy - (double)z;
+                },
+                err))
+            return;
+        continue;
     }
     const int L = m * W;
     double* b = bpool + s.voff;
@@ -368,51 +421,74 @@ __global__ void __launch_bounds__(NT) k_local_jvp(int nsub, const SubDev* __rest
     __syncthreads();
     if (!stream_solve<T>(
             S, G, m, s.mp, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)b[j * m + t]; },
-            [=](int j, int t, T zz) { z[j * m + t] += (double)zz; }, err))
+            [=](int, int) { return 0.0; }, [=](int j, int t, T zz, double) { z[j * m + t] = (double)zz; }, err))
         return;
     for (int it = 0; it < nir; ++it) {
         local_linear_residual(s, beta, coef, 1.0, b, z, r, red);
         if (!stream_solve<T>(
                 S, G, m, s.mp, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)r[j * m + t]; },
-                [=](int j, int t, T zz) { z[j * m + t] += (double)zz; }, err))
+                [=](int j, int t) { return z[j * m + t]; },
+                [=](int j, int t, T zz, double old) { z[j * m + t] = old + (double)zz; }, err))
             return;
     }
     for (int q = threadIdx.x; q < L; q += NT) owned_out(q / m, q % m, z[q]);
+    }
 }
 
 // Linear RAS preconditioner: Z = sum_i tilde P_i J_i^-1 R_i R.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_local_precond(int nsub, const SubDev* __restrict__ subs,
                                                       const ProbDev* __restrict__ probs, const T* gpool,
-                                                      T* wpool, const double* R, double* Z, int* err) {
+                                                      T* wpool, const double* R, double* Z, int* err,
+                                                      const int* order, int* ticket) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ T vec[MAX_M], tmp[MAX_M];
-    const int i = blockIdx.x;
-    if (i >= nsub) return;
+    __shared__ int sh_next;
+    Stream<T> S;
+    stream_init(S, smem);
+    for (;;) {
+    const int pos = next_position(ticket, &sh_next);
+    if (pos >= nsub) break;
+    const int i = order[pos];
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
     const int n = P.n, m = 2 * s.wx, W = s.wy;
     const long long nn = (long long)n * n;
     const double* Ry = R + P.ofs;
     double* Zy = Z + P.ofs;
-    Stream<T> S;
-    stream_init(S, smem);
     auto rhs = [=](int j, int t) -> T {
         const int lx = t >> 1, f = t & 1;
         return (T)Ry[f * nn + (long long)(s.y0 + j) * n + s.x0 + lx];
     };
-    auto out = [=](int j, int t, T z) {
+    auto out = [=](int j, int t, T z, double) {
         const int lx = t >> 1, f = t & 1;
         const int gx = s.x0 + lx, gy = s.y0 + j;
         if (gx >= s.ox0 && gx < s.ox0 + s.owx && gy >= s.oy0 && gy < s.oy0 + s.owy)
             Zy[f * nn + (long long)gy * n + gx] = (double)z;
     };
-    stream_solve<T>(S, gpool + s.goff, m, s.mp, W, (T)P.beta, wpool + s.voff, vec, tmp, rhs, out, err);
+    if (!stream_solve<T>(S, gpool + s.goff, m, s.mp, W, (T)P.beta, wpool + s.voff, vec, tmp, rhs,
+                         [=](int, int) { return 0.0; }, out, err))
+        return;
+    }
 }
 
 template <class K>
 cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Grid of a persistent solve kernel: as many CTAs as fit on the device at
+// once, at most one per subdomain; the ticket is zeroed on the stream first.
+template <class K>
+cudaError_t persistent_grid(K kernel, size_t smem, int nsub, cudaStream_t st, int* ticket, int& grid) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    grid = std::max(1, std::min(nsub, std::max(1, per_sm) * sms));
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -421,14 +497,17 @@ template <typename T>
 cudaError_t launch_local_direction(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                                    const ProbDev* probs, LocalState* ls, NewtonParams np,
                                    const double* coef, const T* gpool, const double* Kpool,
-                                   double* dpool, double* rpool, T* wpool, int* err) {
+                                   double* dpool, double* rpool, T* wpool, int* err, const int* order,
+                                   int* ticket) {
     (void)maxm;
     const size_t sm = solve_smem<T>();
     cudaError_t e = set_smem(k_local_direction<T>, sm);
+    int grid = 0;
+    if (e == cudaSuccess) e = persistent_grid(k_local_direction<T>, sm, nsub, st, ticket, grid);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_local_direction<T><<<nsub, NT, sm, st>>>(nsub, subs, probs, ls, np, coef, gpool, Kpool, dpool, rpool,
-                                               wpool, err);
+    k_local_direction<T><<<grid, NT, sm, st>>>(nsub, subs, probs, ls, np, coef, gpool, Kpool, dpool, rpool,
+                                               wpool, err, order, ticket);
     return cudaGetLastError();
 }
 
@@ -436,39 +515,44 @@ template <typename T>
 cudaError_t launch_local_jvp(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                              const ProbDev* probs, const T* gpool, T* wpool, const double* coef,
                              double* zpool, double* rpool, double* bpool, int nir, const double* D,
-                             double* O, const int* pmask, int* err) {
+                             double* O, const int* pmask, int* err, const int* order, int* ticket) {
     (void)maxm;
     const size_t sm = solve_smem<T>();
     cudaError_t e = set_smem(k_local_jvp<T>, sm);
+    int grid = 0;
+    if (e == cudaSuccess) e = persistent_grid(k_local_jvp<T>, sm, nsub, st, ticket, grid);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_local_jvp<T><<<nsub, NT, sm, st>>>(nsub, subs, probs, gpool, wpool, coef, zpool, rpool, bpool, nir, D, O,
-                                         pmask, err);
+    k_local_jvp<T><<<grid, NT, sm, st>>>(nsub, subs, probs, gpool, wpool, coef, zpool, rpool, bpool, nir, D, O,
+                                         pmask, err, order, ticket);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_local_precond(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                                  const ProbDev* probs, const T* gpool, T* wpool, const double* R,
-                                 double* Z, int* err) {
+                                 double* Z, int* err, const int* order, int* ticket) {
     (void)maxm;
     const size_t sm = solve_smem<T>();
     cudaError_t e = set_smem(k_local_precond<T>, sm);
+    int grid = 0;
+    if (e == cudaSuccess) e = persistent_grid(k_local_precond<T>, sm, nsub, st, ticket, grid);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_local_precond<T><<<nsub, NT, sm, st>>>(nsub, subs, probs, gpool, wpool, R, Z, err);
+    k_local_precond<T><<<grid, NT, sm, st>>>(nsub, subs, probs, gpool, wpool, R, Z, err, order, ticket);
     return cudaGetLastError();
 }
 
-#define RAS_INSTANTIATE(T)                                                                                   \
-    template cudaError_t launch_local_direction<T>(cudaStream_t, int, int, const SubDev*, const ProbDev*,      \
-                                                   LocalState*, NewtonParams, const double*, const T*,          \
-                                                   const double*, double*, double*, T*, int*);                 \
+#define RAS_INSTANTIATE(T)                                                                              \
+    template cudaError_t launch_local_direction<T>(cudaStream_t, int, int, const SubDev*, const ProbDev*, \
+                                                   LocalState*, NewtonParams, const double*, const T*,    \
+                                                   const double*, double*, double*, T*, int*, const int*, \
+                                                   int*);                                                 \
     template cudaError_t launch_local_jvp<T>(cudaStream_t, int, int, const SubDev*, const ProbDev*, const T*,  \
                                              T*, const double*, double*, double*, double*, int,                \
-                                             const double*, double*, const int*, int*);                        \
+                                             const double*, double*, const int*, int*, const int*, int*);      \
     template cudaError_t launch_local_precond<T>(cudaStream_t, int, int, const SubDev*, const ProbDev*,        \
-                                                 const T*, T*, const double*, double*, int*);
+                                                 const T*, T*, const double*, double*, int*, const int*, int*);
 RAS_INSTANTIATE(float)
 RAS_INSTANTIATE(double)
 #undef RAS_INSTANTIATE
