@@ -39,11 +39,11 @@ FP64_LANES = 2       # FP64 FMA per clock per SM on GB300 (1.2 TFLOP/s class)
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the n1023 workload (profiles/dram_jvp_n1023.md), valid
 # while the kernel's sources are unchanged since that capture.
-TRAFFIC = {"jvp": {"bytes_per_launch": 8562460160.0, "workload": "n1023",
+TRAFFIC = {"jvp": {"bytes_per_launch": 8545434453.3, "workload": "n1023",
                    "sources": ["paper_2411_00546_gb300/csrc/solve.cu",
                                "paper_2411_00546_gb300/csrc/ras_internal.cuh"],
-                   "sha256": ["588457ff564180912d912e96443a5d2758f6e12796525f8f11a4079dcff6e691",
-                              "44b7d7a75537c022eace1b7d8df8e0513d554912c9e388aa42c90e618cae0dfa"]}}
+                   "sha256": ["e6a725b53c9fa6fd5be1d63c47be3a9f8fba74c98487c6719fcebc01fb0e2a7f",
+                              "1174ab519f130c8c51685596a1939d589bf997d74280e9e42af51f6822c54263"]}}
 
 # Counts of one RASPEN_eps solve (see run_reference).
 SOLVE_COUNTS = {"n1023": {"inner_its_sum": 1794, "evaluations": 3, "gmres_its": 147}}
