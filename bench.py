@@ -45,6 +45,8 @@ TRAFFIC = {"jvp": {"bytes_per_launch": 8545434453.3, "workload": "n1023",
                    "sha256": ["e6a725b53c9fa6fd5be1d63c47be3a9f8fba74c98487c6719fcebc01fb0e2a7f",
                               "1174ab519f130c8c51685596a1939d589bf997d74280e9e42af51f6822c54263"]}}
 
+NEWTON_CAP = 25      # outer iterations of the unpreconditioned Newton baselines in the bench
+
 # Counts of one RASPEN_eps solve (see run_reference).
 SOLVE_COUNTS = {"n1023": {"inner_its_sum": 1794, "evaluations": 3, "gmres_its": 147}}
 
@@ -180,6 +182,45 @@ def measure_serving(ras, torch, dev, stream, count):
     return res
 
 
+def measure_methods(ras, torch, dev, stream):
+    """The paper's method comparison (Sec. 5, its tables of outer / GMRES /
+    inner counts and times) on the n255 workload in mixed precision: RASPEN,
+    Newton_RAS and Newton (unpreconditioned GMRES), each without and with
+    eps-continuation (eps0 = eps_min or 0.1)."""
+    from paper_2411_00546_gb300 import inputs
+    cfg = inputs.problem("n255")
+    n = cfg["n"]
+    yd = torch.tensor(inputs.make_yd(cfg), dtype=torch.float64, device=dev)
+    out = {"workload": "n255: n=255, 8x8 subdomains, overlap 4, phi=y^3, nu=%g, mu=%g, Fourier y_d seed %d"
+                       % (cfg["nu"], cfg["mu"], cfg["yd"][1]),
+           "note": "Newton runs are capped at %d outer iterations (GMRES(30), at most 1000 steps each); "
+                   "status -3 means the cap was reached" % NEWTON_CAP}
+    methods = [("RASPEN", ras.ras_raspen_solve), ("Newton_RAS", ras.ras_newton_ras_solve),
+               ("Newton", ras.ras_newton_solve)]
+    for name, fn in methods:
+        for cont in (False, True):
+            o = ras.make_opts(precision=ras.RAS_MIXED, tol=cfg["tol"], inner_tol=cfg["inner_tol"],
+                              sigma=cfg["sigma"], gamma=cfg["gamma"], eps_min=cfg["eps_min"],
+                              eps0=cfg["eps0"] if cont else cfg["eps_min"])
+            if name == "Newton":
+                o.kmax_outer_newton = NEWTON_CAP   # unpreconditioned GMRES: bounded run
+            h = ras.ras_create(n, cfg["sx"], cfg["sy"], cfg["overlap"], cfg["phi"], cfg["nu"], cfg["mu"], yd, None,
+                               o, stream=stream.cuda_stream)
+            y = torch.zeros_like(yd)
+            p = torch.zeros_like(yd)
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rc, st = fn(h, y, p, check=False)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ras.ras_destroy(h)
+            out[name + ("_eps" if cont else "")] = {
+                "ms": round(a.elapsed_time(b), 2), "status": rc, "outer_its": st.outer_its,
+                "gmres_its": st.gmres_its, "inner_its_sum": st.inner_its_sum, "halvings": st.halvings}
+    return out
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,6 +233,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-methods", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)
     return ap.parse_args()
 
@@ -533,6 +575,9 @@ def main():
     serving = None
     if not args.no_serve:
         serving = measure_serving(ras, torch, dev, stream, args.serve_requests)
+    methods = None
+    if not args.no_methods:
+        methods = measure_methods(ras, torch, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -567,7 +612,7 @@ def main():
                                 "above the 129 MB L2" % (dev_bytes / 1e9),
                           "solve_stats": stats[-1], "fp64": fp64, "kernel_share": kernel_share,
                           "kernels": kernels, "kernel_rooflines": kernel_rooflines,
-                          "uneven_batch": batch, "serving": serving,
+                          "uneven_batch": batch, "serving": serving, "methods": methods,
                           "y_max": float(np.abs(y_mixed).max()),
                           "p_max": float(np.abs(p_mixed).max())},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

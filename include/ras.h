@@ -258,8 +258,16 @@ int ras_raspen_solve(ras_problem* h, double* y, double* p, ras_stats* stats);
  * GMRES right-preconditioned by linear RAS). In/out as ras_raspen_solve. */
 int ras_newton_ras_solve(ras_problem* h, double* y, double* p, ras_stats* stats);
 
+/* Newton (Alg. 1 on F_eps(x) = 0, eps-continuation when eps0 > eps_min: the
+ * paper's Newton / Newton_eps baselines of Sec. 5) with unpreconditioned
+ * GMRES on the global Jacobian F_eps'(x) applied matrix-free in FP64 (no local
+ * factorisations). In/out as ras_raspen_solve; single-problem handles only
+ * (else RAS_EINVAL); RAS_ENOCONV when kmax_outer_newton is reached. */
+int ras_newton_solve(ras_problem* h, double* y, double* p, ras_stats* stats);
+
 #define RAS_METHOD_RASPEN     0
 #define RAS_METHOD_NEWTON_RAS 1
+#define RAS_METHOD_NEWTON     2
 /* End-to-end call on HOST buffers: copies y_d_host (n*n, NULL keeps the
  * current y_d) and the initial guess y_host, p_host to the device, solves with
  * `method`, and copies the solution back into y_host, p_host. */

@@ -9,6 +9,9 @@
   are solved by GMRES right-preconditioned with the linear RAS preconditioner
   (the paper's Newton_RAS, Sec. 4.1 and 5.1). With eps_0 > eps_min it is
   Newton_RAS,eps.
+* newton_gmres: Alg. 1 on the global system whose Newton systems are solved by
+  unpreconditioned GMRES (the paper's Newton and, with eps_0 > eps_min,
+  Newton_eps baselines, Sec. 4.1 and 5.1).
 * newton_dense: Alg. 1 with a dense LU solve of the full Jacobian (brute force,
   small grids only).
 * newton_sparse: Alg. 1 with a sparse direct solve of the full Jacobian.
@@ -107,6 +110,34 @@ def newton_ras(prob, sx, sy, overlap, opts, Y0=None, P0=None):
             wY, wP = _split(w, n)
             return _join(*pre.apply(wY, wP))
         g = gmres(A, -F, opts.gmres_restart, opts.gmres_rtol, opts.gmres_maxit, M)
+        gm.append(g.iterations)
+        return g.x
+
+    x0 = np.zeros(2 * n * n) if Y0 is None else _join(Y0, P0)
+    res = damped_newton(residual, solve, x0, opts.eps0, opts.eps_min, opts.gamma, opts.sigma,
+                        opts.tol, opts.kmax_outer_newton, opts.max_halvings, floor, opts.floor_factor)
+    out = SolveResult()
+    out.Y, out.P = _split(res.x, n)
+    out.outer = res.iterations
+    out.gmres_its = gm
+    out.status = res.status
+    out.newton = res
+    return out
+
+
+def newton_gmres(prob, opts, Y0=None, P0=None):
+    """Alg. 1 with GMRES(m) on the full Jacobian F'_eps(x), no preconditioner."""
+    n = prob.n
+    residual, floor = _global_residual(prob)
+    gm = []
+
+    def solve(v, eps, F):
+        Y, P = _split(v, n)
+
+        def A(w):
+            wY, wP = _split(w, n)
+            return _join(*fd.jacvec(prob, Y, P, eps, wY, wP))
+        g = gmres(A, -F, opts.gmres_restart, opts.gmres_rtol, opts.gmres_maxit)
         gm.append(g.iterations)
         return g.x
 

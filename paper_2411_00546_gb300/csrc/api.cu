@@ -859,8 +859,12 @@ int raspen_internal(ras_problem* h, ras_stats* s) {
     return RAS_OK;
 }
 
-// --------------------------------------------------------------- Newton_RAS
-int newton_ras_internal(ras_problem* h, ras_stats* s) {
+// ------------------------------------------------------- Newton_RAS / Newton
+// Alg. 1 on the global system F_eps(x) = 0; its Newton systems are solved by
+// GMRES, right-preconditioned by the linear RAS preconditioner at x (prec:
+// Newton_RAS) or unpreconditioned (the paper's Newton baseline). With
+// eps0 > eps_min the continuation makes them Newton_RAS,eps / Newton_eps.
+int newton_internal(ras_problem* h, ras_stats* s, bool prec) {
     const long long N = plane(h, 0);
     const ras_opts& o = h->o;
     const double seglen = (double)h->segs[0].len;
@@ -876,7 +880,9 @@ int newton_ras_internal(ras_problem* h, ras_stats* s) {
         }));
         return RAS_OK;
     };
-    auto M = [&](const double* in, double* out, const std::vector<int>&) { return precond_internal(h, in, out); };
+    auto M = [&](const double* in, double* out, const std::vector<int>&) {
+        return prec ? precond_internal(h, in, out) : RAS_OK;
+    };
     for (;;) {
         if (!std::isfinite(nrm)) { status = RAS_ENONFINITE; break; }
         if (eps == o.eps_min) {
@@ -884,14 +890,14 @@ int newton_ras_internal(ras_problem* h, ras_stats* s) {
             if (nrm <= o.floor_factor * 1.1102230246251565e-16 * flr) { status = RAS_OK_FLOOR; break; }
         }
         if (k >= o.kmax_outer_newton) { status = RAS_ENOCONV; break; }
-        TRY(factor_at(h, eps));
+        if (prec) TRY(factor_at(h, eps));
         CK(timed(h, RAS_K_OTHER, 40.0 * N, [&] {
             return ras::launch_coef_global(h->st, h->probs[0], h->X, h->X + N, eps, h->coefG);
         }));
         CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
             return ras::launch_seg_scale(h->st, seg_grid(h, 2), h->d_segs, h->F, nullptr, -1.0, h->T1);
         }));
-        TRY(gmres(h, A, M, true, h->T1, h->Dv, one, its, conv));
+        TRY(gmres(h, A, M, prec, h->T1, h->Dv, one, its, conv));
         if (s) s->gmres_its += its[0];
         double alpha = 1.0, nt = 0.0, ft = 0.0;
         int hh = 0;
@@ -925,9 +931,12 @@ int newton_ras_internal(ras_problem* h, ras_stats* s) {
         s->status = status;
         s->eps_final = eps;
     }
-    if (status < 0) return fail(h, status, "Newton_RAS stopped without convergence");
+    if (status < 0) return fail(h, status, prec ? "Newton_RAS stopped without convergence"
+                                                : "Newton stopped without convergence");
     return status;
 }
+
+int newton_ras_internal(ras_problem* h, ras_stats* s) { return newton_internal(h, s, true); }
 
 int need_single(ras_problem* h) {
     if (h->nprob != 1) return fail(h, RAS_EINVAL, "this entry point takes a single-problem handle");
@@ -1304,9 +1313,23 @@ int ras_newton_ras_solve(ras_problem* h, double* y, double* p, ras_stats* stats)
     return rc;
 }
 
+int ras_newton_solve(ras_problem* h, double* y, double* p, ras_stats* stats) {
+    if (!h || !y || !p) return RAS_EINVAL;
+    TRY(need_single(h));
+    stats_clear(stats, 1);
+    TRY(copy_in(h, h->X, 0, y, p));
+    const int rc = newton_internal(h, stats, false);
+    if (rc == RAS_ECUDA) return rc;
+    TRY(check_err(h));
+    TRY(copy_out(h, h->X, 0, y, p));
+    TRY(sync(h));
+    return rc;
+}
+
 int ras_solve_host(ras_problem* h, int method, const double* y_d_host, double* y_host, double* p_host,
                    ras_stats* stats) {
-    if (!h || !y_host || !p_host || (method != RAS_METHOD_RASPEN && method != RAS_METHOD_NEWTON_RAS))
+    if (!h || !y_host || !p_host ||
+        (method != RAS_METHOD_RASPEN && method != RAS_METHOD_NEWTON_RAS && method != RAS_METHOD_NEWTON))
         return RAS_EINVAL;
     TRY(need_single(h));
     stats_clear(stats, 1);
@@ -1316,7 +1339,9 @@ int ras_solve_host(ras_problem* h, int method, const double* y_d_host, double* y
     CK(cudaMemcpyAsync(h->X, y_host, nb, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->X + N, p_host, nb, cudaMemcpyHostToDevice, h->st));
     h->jvp_ready = false;
-    const int rc = (method == RAS_METHOD_RASPEN) ? raspen_internal(h, stats) : newton_ras_internal(h, stats);
+    const int rc = (method == RAS_METHOD_RASPEN)       ? raspen_internal(h, stats)
+                   : (method == RAS_METHOD_NEWTON_RAS) ? newton_internal(h, stats, true)
+                                                       : newton_internal(h, stats, false);
     if (rc == RAS_ECUDA) return rc;
     TRY(check_err(h));
     CK(cudaMemcpyAsync(y_host, h->X, nb, cudaMemcpyDeviceToHost, h->st));

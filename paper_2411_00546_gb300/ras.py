@@ -33,6 +33,7 @@ RAS_MIXED = 1
 
 RAS_METHOD_RASPEN = 0
 RAS_METHOD_NEWTON_RAS = 1
+RAS_METHOD_NEWTON = 2
 
 
 class ras_opts(ctypes.Structure):
@@ -88,6 +89,7 @@ _SIGS = {
     "ras_precondition": (_I, [_P, _P, _P, _D, _P, _P, _P, _P]),
     "ras_raspen_solve": (_I, [_P, _P, _P, ctypes.POINTER(ras_stats)]),
     "ras_newton_ras_solve": (_I, [_P, _P, _P, ctypes.POINTER(ras_stats)]),
+    "ras_newton_solve": (_I, [_P, _P, _P, ctypes.POINTER(ras_stats)]),
     "ras_solve_host": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(ras_stats)]),
     "ras_local_iterations": (_I, [_P, ctypes.POINTER(_I), _I]),
     "ras_subdomain_count": (_I, [_P]),
@@ -287,6 +289,15 @@ def ras_newton_ras_solve(h, y, p, check=True):
     nn = h.n * h.n
     st = ras_stats()
     rc = lib().ras_newton_ras_solve(h.ptr, _ptr(y, nn), _ptr(p, nn), ctypes.byref(st))
+    if check:
+        h._check(rc)
+    return rc, st
+
+
+def ras_newton_solve(h, y, p, check=True):
+    nn = h.n * h.n
+    st = ras_stats()
+    rc = lib().ras_newton_solve(h.ptr, _ptr(y, nn), _ptr(p, nn), ctypes.byref(st))
     if check:
         h._check(rc)
     return rc, st

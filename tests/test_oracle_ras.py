@@ -211,10 +211,31 @@ def test_all_solvers_reach_the_dense_newton_root(n, s, kind):
     scale_y = np.abs(dense.Y).max()
     scale_p = np.abs(dense.P).max()
     for res in (solvers.raspen(prob, s, s, 1, opts), solvers.newton_ras(prob, s, s, 1, opts),
-                solvers.newton_sparse(prob, opts)):
+                solvers.newton_sparse(prob, opts), solvers.newton_gmres(prob, opts)):
         assert res.status >= 0
         assert np.max(np.abs(res.Y - dense.Y)) <= 1e-12 * scale_y
         assert np.max(np.abs(res.P - dense.P)) <= 1e-12 * scale_p
+
+
+@pytest.mark.parametrize("eps0", [1e-6, 0.1])
+def test_newton_gmres_follows_the_direct_newton_steps(eps0):
+    """Unpreconditioned GMRES solved to a tight tolerance reproduces the Newton
+    steps of the sparse direct solver: same iterate sequence (to the GMRES
+    accuracy), same iteration and halving counts, with (Newton_eps) and
+    without (Newton) continuation."""
+    n = 12
+    x = (np.arange(n) + 1) / (n + 1)
+    yd = 30.0 * np.outer(np.sin(2 * np.pi * x), np.sin(2 * np.pi * x))
+    prob = fd.Problem(n, pw.PHI_CUBIC, 1e-3, 5e-2, yd)
+    opts = ras.Options(eps0=eps0, gamma=0.1, eps_min=1e-6, tol=1e-12, gmres_rtol=1e-13, gmres_maxit=4000)
+    a = solvers.newton_sparse(prob, opts)
+    b = solvers.newton_gmres(prob, opts)
+    assert a.status >= 0 and b.status >= 0
+    assert a.outer == b.outer
+    assert a.newton.halvings == b.newton.halvings
+    assert np.max(np.abs(b.Y - a.Y)) <= 1e-10 * np.abs(a.Y).max()
+    assert np.max(np.abs(b.P - a.P)) <= 1e-10 * np.abs(a.P).max()
+    assert len(b.gmres_its) == b.outer and all(k > 0 for k in b.gmres_its)
 
 
 def test_eps_solutions_converge():
