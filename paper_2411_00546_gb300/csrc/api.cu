@@ -71,6 +71,7 @@ struct ras_problem {
     double* partials = nullptr;
     int nbp = 0;                 // blocks per problem of the segmented kernels
     int sms = 0;                 // SMs of the device (0 until queried)
+    bool own_factors = true;     // factors and coefficients in gpool / coef (else per subdomain pointers)
     int* d_order = nullptr;      // subdomain indices, largest factors first (solve kernels)
     int* d_ticket = nullptr;     // work counter of the persistent solve kernels
     // block tables of the segmented kernels, one per mask row (0: GMRES/JVP,
@@ -1111,7 +1112,18 @@ int ensure_pools(ras_problem* h, bool own_data) {
     return RAS_OK;
 }
 
+// Absolute factor / coefficient pointers of every subdomain into the
+// handle's own pools (handles whose factors live elsewhere set them first).
+void fill_pointers(ras_problem* h) {
+    const size_t es = (h->o.precision == RAS_MIXED) ? sizeof(float) : sizeof(double);
+    for (auto& sd : h->subs) {
+        sd.gptr = static_cast<char*>(h->gpool) + sd.goff * es;
+        sd.cptr = h->coef + 3 * sd.noff;
+    }
+}
+
 int upload_layout(ras_problem* h) {
+    if (h->own_factors) fill_pointers(h);
     TRY(build_grid(h, 2, std::vector<int>(h->nprob, 1)));
     // solve order: largest factor (wy * mp^2) first, ties by index
     std::vector<int> order(h->nsub);
@@ -1199,11 +1211,15 @@ int ras_set_opts(ras_problem* h, const ras_opts* o) {
     h->o = *o;
     h->jvp_ready = false;
     TRY(alloc_factor_pools(h));
+    if (h->own_factors) {
+        fill_pointers(h);
+        CK(cudaMemcpyAsync(h->d_subs, h->subs.data(), h->nsub * sizeof(SubDev), cudaMemcpyHostToDevice, h->st));
+    }
     if (kappa_changed) {
         for (auto& P : h->probs) P.kappa = o->kappa;
         CK(cudaMemcpyAsync(h->d_probs, h->probs.data(), h->nprob * sizeof(ProbDev), cudaMemcpyHostToDevice, h->st));
-        TRY(sync(h));
     }
+    TRY(sync(h));
     return RAS_OK;
 }
 

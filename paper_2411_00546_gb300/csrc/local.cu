@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_local_factor(int nsub, int max
 
     const double eps = ls[i].eps;
     const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu;
-    double* ca = coef + 3 * s.noff;
+    double* ca = s.cptr;
     double* cb = ca + nn;
     double* cc = cb + nn;
     {
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_local_factor(int nsub, int max
     __syncthreads();
 
     const T tbeta = (T)beta, tbeta2 = (T)(beta * beta), tdiag = (T)(4.0 * beta);
-    T* G = gpool + s.goff;
+    T* G = static_cast<T*>(s.gptr);
     for (int j = 0; j < W; ++j) {
         // S_j = D_j - beta^2 G_{j-1}
         const long long blk = (long long)s.mp * s.mp;
@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub
 
     const double eps = ls[i].eps;
     const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu;
-    double* ca = coef + 3 * s.noff;
+    double* ca = s.cptr;
     double* cb = ca + nn;
     double* cc = cb + nn;
     {
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub
 
     const float tbeta = (float)beta, tbeta2 = (float)(beta * beta), tdiag = (float)(4.0 * beta);
     const long long blk = (long long)mp * mp;
-    float* G = gpool + s.goff;
+    float* G = static_cast<float*>(s.gptr);
     float Mr[R][R];
 #pragma unroll
     for (int a = 0; a < R; ++a)
@@ -846,7 +846,7 @@ __global__ void __launch_bounds__(1024, 1) k_local_factor_wide(int nsub, const S
 
     const double eps = ls[i].eps;
     const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu;
-    double* ca = coef + 3 * s.noff;
+    double* ca = s.cptr;
     double* cb = ca + nn;
     double* cc = cb + nn;
     {
@@ -867,7 +867,7 @@ __global__ void __launch_bounds__(1024, 1) k_local_factor_wide(int nsub, const S
 
     const float tbeta = (float)beta, tbeta2 = (float)(beta * beta), tdiag = (float)(4.0 * beta);
     const long long blk = (long long)mp * mp;
-    float* G = gpool + s.goff;
+    float* G = static_cast<float*>(s.gptr);
     float Mr[R][R];
 #pragma unroll
     for (int a = 0; a < R; ++a)

@@ -46,6 +46,8 @@ struct SubDev {
     long long goff;           // factor offset (elements of T); wy blocks of mp*mp
     long long voff;           // local-vector offset (doubles), length 2*wx*wy
     long long noff;           // node-array offset (doubles), length wx*wy
+    void* gptr;               // this subdomain's factor blocks (wy blocks of mp*mp T)
+    double* cptr;             // its Jacobian coefficients (3 arrays of wx*wy doubles)
 };
 
 // Segment of one problem inside a global vector buffer: [ofs, ofs + len).

@@ -258,7 +258,7 @@ __device__ __forceinline__ int next_position(int* ticket, int* slot) {
 __device__ double local_linear_residual(const SubDev& s, double beta, const double* coef, double bsign,
                                         const double* B, const double* z, double* r, double* red) {
     const int wx = s.wx, wy = s.wy, nn = wx * wy;
-    const double* ca = coef + 3 * s.noff;
+    const double* ca = s.cptr;
     const double* cb = ca + nn;
     const double* cc = cb + nn;
     double r2 = 0.0, dummy = 0.0;
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(NT) k_local_direction(int nsub, const SubDev* 
     double* d = dpool + s.voff;
     double* r = rpool + s.voff;
     T* w = wpool + s.voff;
-    const T* G = gpool + s.goff;
+    const T* G = static_cast<const T*>(s.gptr);
     double b2 = 0.0, dummy = 0.0;
     for (int q = threadIdx.x; q < L; q += NT) {
         const double v = -K[q];
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(NT) k_local_jvp(int nsub, const SubDev* __rest
     const double beta = P.beta;
     const double* Dy = D + P.ofs;
     double* Oy = O + P.ofs;
-    const T* G = gpool + s.goff;
+    const T* G = static_cast<const T*>(s.gptr);
     T* w = wpool + s.voff;
     auto bval = [=](int j, int t) -> double {
         const int lx = t >> 1, f = t & 1;
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(NT) k_local_precond(int nsub, const SubDev* __
         if (gx >= s.ox0 && gx < s.ox0 + s.owx && gy >= s.oy0 && gy < s.oy0 + s.owy)
             Zy[f * nn + (long long)gy * n + gx] = (double)z;
     };
-    if (!stream_solve<T>(S, gpool + s.goff, m, s.mp, W, (T)P.beta, wpool + s.voff, vec, tmp, rhs,
+    if (!stream_solve<T>(S, static_cast<const T*>(s.gptr), m, s.mp, W, (T)P.beta, wpool + s.voff, vec, tmp, rhs,
                          [=](int, int) { return 0.0; }, out, err))
         return;
     }
