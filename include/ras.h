@@ -162,15 +162,17 @@ int ras_batch_raspen_solve(ras_problem* h, double* const* y, double* const* p, r
  * Continuous batching of RASPEN_eps solves (Alg. 2): requests of any size and
  * any (nu, mu, phi, y_d, f) are submitted at any time; every ras_server_step
  * admits waiting requests while the budget allows, then advances every
- * admitted request by one outer iteration of Alg. 2 (evaluate the RASPEN
- * function at x_k, with eps-continuation in the local solves when k = 0;
- * test; GMRES and update when the test fails), with the local solves,
- * Jacobian actions and Krylov vectors of all admitted requests in shared
- * launches. A request's iterate x_k = (y, p) and data stay on the device
- * between steps; a request whose test passes (or that fails) is finished
- * and holds its result until fetched. Each request's sequence of operations
- * is that of ras_raspen_solve on the problem alone (same x0 = 0, same
- * options), so its result agrees with the solve alone to rounding.
+ * admitted request by one phase step: a request in its evaluation phase
+ * evaluates the RASPEN function at x_k (eps-continuation in the local solves
+ * when k = 0) and tests it (finished, or on to GMRES); a request in its GMRES
+ * phase runs one restart cycle of GMRES(m), and when GMRES stops takes
+ * x_{k+1} = x_k + d and returns to evaluation. The local solves, Jacobian
+ * actions and Krylov vectors of all requests in a phase share launches. A
+ * request's iterate, data, GMRES state and local factors stay on the device
+ * between steps; a finished request holds its result until fetched. Each
+ * request's sequence of operations is that of ras_raspen_solve on the
+ * problem alone (same x0 = 0, same options), so its result agrees with the
+ * solve alone to rounding.
  *
  * ras_server_create: hbm_budget = device bytes the server may hold (slot
  *   storage of admitted and unfetched requests plus the batch workspace, by
@@ -183,8 +185,7 @@ int ras_batch_raspen_solve(ras_problem* h, double* const* y, double* const* p, r
  *   pointers (n*n doubles, copied before the call returns). Queues the
  *   request (first come, first served); *id receives its id (> 0).
  *   RAS_ENOMEM if the request alone exceeds the budget.
- * ras_server_step: admission, then one outer iteration of every admitted
- *   request; *active = requests still admitted after it, *finished = requests
+ * ras_server_step: admission, then one phase step of every admitted request; *active = requests still admitted after it, *finished = requests
  *   that finished in it (either pointer may be NULL). With nothing admitted it
  *   only admits. Returns RAS_OK, or RAS_ECUDA / RAS_ETIMEOUT (the server must
  *   then be destroyed).

@@ -253,8 +253,10 @@ int alloc_factor_pools(ras_problem* h) {
     const size_t es = (prec == RAS_MIXED) ? sizeof(float) : sizeof(double);
     char* g = static_cast<char*>(h->gpool);
     char* w = static_cast<char*>(h->wpool);
-    TRY(ensure(h, &g, (size_t)h->Gsum * es));
-    h->gpool = g;
+    if (h->own_factors) {
+        TRY(ensure(h, &g, (size_t)h->Gsum * es));
+        h->gpool = g;
+    }
     TRY(ensure(h, &w, (size_t)h->Lsum * es));
     h->wpool = w;
     h->gprec = prec;
@@ -610,9 +612,24 @@ int precond_internal(ras_problem* h, const double* R, double* Zo) {
 // M(in, out, mask) act on the problems flagged in mask (host) = d_mask row 0
 // (device), which this routine keeps equal to the problems still iterating.
 // One host synchronisation per Krylov step for the whole batch.
+// Resumable GMRES for the serving loop: per problem, `fresh` starts from
+// x = 0 and sets its stop target from ||b||; otherwise x holds the iterate of
+// earlier cycles and `target` the target set then. At most max_cycles restart
+// cycles run; `pending` reports the problems still iterating. Restart cycles
+// only carry x, so a solve split over calls is the same sequence of cycles.
+struct GmresResume {
+    std::vector<int> fresh;
+    std::vector<double> target;
+    int max_cycles = 1;
+    std::vector<int> pending;
+};
+
+// GMRES(m) (CGS2, Givens) for the problems with part[p], in lockstep, with
+// right preconditioning when prec. its: steps taken (cumulative when
+// resuming), conv: converged to rtol * ||b||.
 template <class Aop, class Mop>
 int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, const std::vector<int>& part,
-          std::vector<int>& its, std::vector<int>& conv) {
+          std::vector<int>& its, std::vector<int>& conv, GmresResume* res = nullptr) {
     const int P = h->nprob, m = h->o.gmres_restart, maxit = h->o.gmres_maxit;
     const long long L = h->L;
     const double rtol = h->o.gmres_rtol;
@@ -621,26 +638,51 @@ int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, c
     double* V = h->V;
     double* r = h->T2;
     double* upd = h->T3;
-    its.assign(P, 0);
+    if (!res) its.assign(P, 0);
+    its.resize(P, 0);
     conv.assign(P, 0);
-    CK(cudaMemsetAsync(x, 0, L * sizeof(double), h->st));
-    std::vector<int> act(P, 0), cyc(P, 0), steps(P, 0);
+    std::vector<int> act(P, 0), cyc(P, 0), steps(P, 0), cont(P, 0);
     std::vector<double> target(P, 0.0), beta(P, 0.0);
+    if (!res) {
+        CK(cudaMemsetAsync(x, 0, L * sizeof(double), h->st));
+    } else {
+        for (int p = 0; p < P; ++p) {
+            if (part[p] && res->fresh[p])
+                CK(cudaMemsetAsync(x + h->segs[p].ofs, 0, h->segs[p].len * sizeof(double), h->st));
+            cont[p] = part[p] && !res->fresh[p];
+        }
+        res->pending.assign(P, 0);
+        res->target.resize(P, 0.0);
+    }
     TRY(set_mask(h, 0, part));
     TRY(seg_norms2(h, b, 0));
     for (int p = 0; p < P; ++p) {
         if (!part[p]) continue;
         const double bn = std::sqrt(h->h_scal[p * SS]);
+        if (cont[p]) {
+            target[p] = res->target[p];
+            act[p] = 1;
+            continue;
+        }
         target[p] = rtol * bn;
+        if (res) res->target[p] = target[p];
         if (bn == 0.0) conv[p] = 1;
         else act[p] = 1;
     }
     CK(cudaMemcpyAsync(r, b, L * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-    std::vector<double> H((size_t)P * (m + 1) * m), cs((size_t)P * m), sn((size_t)P * m), g((size_t)P * (m + 1)),
-        y((size_t)P * SS, 0.0);
     double seglen = 0.0;
     for (int p = 0; p < P; ++p) seglen += (double)h->segs[p].len;
-    for (;;) {
+    if (std::any_of(cont.begin(), cont.end(), [](int v) { return v != 0; })) {
+        // resumed problems: r = b - A x from the iterate of the earlier cycles
+        TRY(set_mask(h, 0, cont));
+        TRY(A(x, r, cont));
+        CK(timed(h, RAS_K_KRYLOV, 24.0 * seglen, [&] {
+            return ras::launch_seg_add_scaled(h->st, seg_grid(h, 0), h->d_segs, b, r, -1.0, r);
+        }));
+    }
+    std::vector<double> H((size_t)P * (m + 1) * m), cs((size_t)P * m), sn((size_t)P * m), g((size_t)P * (m + 1)),
+        y((size_t)P * SS, 0.0);
+    for (int cycle = 0;; ++cycle) {
         // true residual norms of the problems still iterating
         TRY(set_mask(h, 0, act));
         TRY(seg_norms2(h, r, 0));
@@ -656,6 +698,10 @@ int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, c
             }
         }
         if (!any) return RAS_OK;
+        if (res && cycle >= res->max_cycles) {
+            res->pending = act;
+            return RAS_OK;
+        }
         cyc = act;
         TRY(set_mask(h, 0, cyc));
         // V_0 = r / beta (device-side, from the squared norms in h->scal)
@@ -1076,7 +1122,7 @@ int ensure_pools(ras_problem* h, bool own_data) {
     TRY(ensure(h, &h->d_order, h->nsub));
     TRY(ensure(h, &h->d_ticket, 1));
     for (double** q : {&h->cpool, &h->dpool, &h->Kpool, &h->Ktpool, &h->rpool}) TRY(ensure(h, q, h->Lsum));
-    TRY(ensure(h, &h->coef, 3 * h->Nsum));
+    if (h->own_factors) TRY(ensure(h, &h->coef, 3 * h->Nsum));
     TRY(ensure(h, &h->ls, h->nsub));
     TRY(ensure(h, &h->d_active, 1));
     if (!h->d_err) {
@@ -1395,33 +1441,46 @@ void ras_destroy(ras_problem* h) {
 }
 
 // ------------------------------------------------------------------ serving
-// Continuous batching of RASPEN_eps solves (Alg. 2). A step runs one outer
-// iteration for every admitted request at once: the evaluation of the RASPEN
-// function at x_k (local Newton solves with eps-continuation for k = 0, at
-// eps_min after), the stop test, and for the requests that go on the GMRES
-// solve and the update x_{k+1} = x_k + d, all in the batched kernels. This is
-// the sequence of Alg. 2 for every request (evaluate, test, solve, update),
-// grouped so that only x_k and host counters persist between steps; requests
-// join and leave between steps. Each admitted request owns slot storage
-// (y, p, y_d and f, stream-ordered allocation); the batch workspace is laid
-// out anew for the admitted set when it changes (buffers only grow).
-// Admission is first come, first served while the estimate of slot storage
-// plus workspace stays within the HBM budget.
+// Continuous batching of RASPEN_eps solves (Alg. 2) with restart-cycle
+// granularity. Every admitted request is in one of two phases:
+//   evaluation - the RASPEN function at x_k (local Newton solves, with
+//                eps-continuation for k = 0, at eps_min after), then the stop
+//                test: finished, or on to GMRES with b = -F(x_k);
+//   GMRES      - restart cycles of GMRES(m) on F'(x_k) d = b with the Jacobian
+//                action of Alg. 4; when it stops, x_{k+1} = x_k + d and the
+//                request returns to evaluation.
+// A step runs one evaluation for every request in the evaluation phase and
+// then one restart cycle (at most m Arnoldi steps) for every request in the
+// GMRES phase, each group in shared launches. A hard request therefore holds
+// the others back by at most one cycle, not by its whole GMRES solve. Each
+// request follows the sequence of Alg. 2 (restart cycles only carry the
+// iterate), so its result is that of the solve alone up to rounding.
+//
+// Each admitted request owns one stream-ordered allocation holding what must
+// survive between steps: x_k = (y, p), y_d, f, the GMRES right-hand side and
+// iterate, the Jacobian coefficients and the local factors at x^(i) (the
+// Jacobian action of its GMRES cycles uses them). The batch workspace holds
+// only per-step scratch and is laid out anew for the admitted set when it
+// changes (buffers only grow). Admission is first come, first served while
+// the estimate of request storage plus workspace stays within the budget.
 struct ras_server {
     ras_problem* ws = nullptr;
     size_t budget = 0;
     int max_active = 0;
     ras_opts o{};
     cudaStream_t st = nullptr;
+    enum { EVAL = 0, KRYLOV = 1 };
     struct Req {
         long long id = 0;
         ras_problem_desc d{};
         std::vector<double> yd_h, f_h;   // staged host data until admission
-        double* mem = nullptr;           // slot storage: y | p | y_d [| f]
+        char* mem = nullptr;             // persistent storage (layout below)
+        double *x = nullptr, *yd = nullptr, *f = nullptr, *gb = nullptr, *gx = nullptr, *coef = nullptr;
+        char* fac = nullptr;
         size_t slot = 0, scratch = 0;    // admission estimate
-        int k = 0;
-        bool failed = false;
-        double stop = 0.0;
+        int phase = EVAL, k = 0, its = 0;
+        bool failed = false, fresh = false;
+        double stop = 0.0, target = 0.0;
         ras_stats stats{};
     };
     std::deque<Req*> pending;
@@ -1440,20 +1499,44 @@ int sfail(ras_server* s, int code, const std::string& msg) {
     return code;
 }
 
-// Device bytes a request needs: its slot storage and its share of the batch
-// workspace (local pools, factors, global and Krylov vectors, descriptors).
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Persistent storage of one request (bytes, 256-byte aligned parts):
+// x (2N), y_d (N), f (N if given), b (2N), GMRES iterate (2N), coefficients
+// (3 Nsum), factors (Gsum elements).
+struct ReqLayout {
+    size_t x, yd, f, gb, gx, coef, fac, total;
+};
+
+ReqLayout req_layout(const ras_problem& t, const ras_problem_desc& d, const ras_opts& o) {
+    const size_t N = (size_t)d.n * d.n * sizeof(double);
+    const size_t es = (o.precision == RAS_MIXED) ? sizeof(float) : sizeof(double);
+    ReqLayout L{};
+    size_t at = 0;
+    L.x = at; at += align256(2 * N);
+    L.yd = at; at += align256(N);
+    L.f = at; at += d.f ? align256(N) : 0;
+    L.gb = at; at += align256(2 * N);
+    L.gx = at; at += align256(2 * N);
+    L.coef = at; at += align256((size_t)3 * t.Nsum * sizeof(double));
+    L.fac = at; at += align256((size_t)t.Gsum * es);
+    L.total = at;
+    return L;
+}
+
+// Device bytes a request needs: its persistent storage, and its share of the
+// batch workspace (local pools, global and Krylov vectors, descriptors).
 int request_bytes(const ras_problem_desc& d, const ras_opts& o, size_t& slot, size_t& scratch) {
     ras_problem tmp;
     tmp.o = o;
     if (build_layout(&tmp, 1, &d) != RAS_OK) return RAS_EINVAL;
-    const double n2 = (double)d.n * d.n;
     const size_t es = (o.precision == RAS_MIXED) ? sizeof(float) : sizeof(double);
-    slot = (size_t)((3.0 + (d.f ? 1.0 : 0.0)) * n2 * sizeof(double));
-    double b = 5.0 * tmp.Lsum * sizeof(double) + 3.0 * tmp.Nsum * sizeof(double) +
-               (double)tmp.nsub * (sizeof(LocalState) + sizeof(SubDev) + 2 * sizeof(int)) +
-               (double)tmp.Gsum * es + (double)tmp.Lsum * es +
-               (8.0 + o.gmres_restart + 1.0) * tmp.L * sizeof(double) + 3.0 * n2 * sizeof(double) +
-               (double)SS * ras::VEC_BLOCKS * sizeof(double) + 4.0 * SS * sizeof(double) + 256.0;
+    slot = req_layout(tmp, d, o).total;
+    double b = 5.0 * tmp.Lsum * sizeof(double) + (double)tmp.Lsum * es +
+               (double)tmp.nsub * (sizeof(LocalState) + sizeof(SubDev) + 3 * sizeof(int)) +
+               (8.0 + o.gmres_restart + 1.0) * tmp.L * sizeof(double) + 3.0 * (double)d.n * d.n * sizeof(double) +
+               (double)SS * ras::VEC_BLOCKS * sizeof(double) + 4.0 * SS * sizeof(double) +
+               3.0 * (ras::VEC_BLOCKS + 1) * 2 * sizeof(int) + 256.0;
     scratch = (size_t)b;
     return RAS_OK;
 }
@@ -1463,21 +1546,29 @@ int server_relayout(ras_server* s) {
         s->ws = new ras_problem();
         s->ws->o = s->o;
         s->ws->st = s->st;
+        s->ws->own_factors = false;
     }
     ras_problem* h = s->ws;
     std::vector<ras_problem_desc> descs;
     for (auto* r : s->active) {
         ras_problem_desc d = r->d;
-        const long long N = (long long)d.n * d.n;
-        d.y_d = r->mem + 2 * N;
-        d.f = r->f_h.empty() ? nullptr : r->mem + 3 * N;
+        d.y_d = r->yd;
+        d.f = r->f;
         descs.push_back(d);
     }
     TRY(build_layout(h, (int)descs.size(), descs.data()));
     TRY(ensure_pools(h, false));
+    const size_t es = (s->o.precision == RAS_MIXED) ? sizeof(float) : sizeof(double);
     for (int p = 0; p < h->nprob; ++p) {
         h->probs[p].yd = descs[p].y_d;
         h->probs[p].f = descs[p].f;
+        auto* r = s->active[p];
+        const SubDev& first = h->subs[h->sub_first[p]];
+        for (int k = 0; k < h->sub_count[p]; ++k) {
+            SubDev& sd = h->subs[h->sub_first[p] + k];
+            sd.gptr = r->fac + (sd.goff - first.goff) * es;
+            sd.cptr = r->coef + 3 * (sd.noff - first.noff);
+        }
     }
     TRY(upload_layout(h));
     s->dirty = false;
@@ -1489,19 +1580,31 @@ int server_admit(ras_server* s) {
         auto* r = s->pending.front();
         const size_t cap = std::max(s->ws_cap, s->scratch_active + r->scratch);
         if (cap + s->slot_held + r->slot > s->budget) break;   // first come, first served
+        ras_problem tmp;
+        tmp.o = s->o;
+        if (build_layout(&tmp, 1, &r->d) != RAS_OK) return sfail(s, RAS_EINVAL, "invalid request layout");
+        const ReqLayout L = req_layout(tmp, r->d, s->o);
         void* m = nullptr;
-        if (cudaMallocAsync(&m, r->slot, s->st) != cudaSuccess) {
+        if (cudaMallocAsync(&m, L.total, s->st) != cudaSuccess) {
             cudaGetLastError();
             break;   // retry at a later step
         }
-        r->mem = static_cast<double*>(m);
+        r->mem = static_cast<char*>(m);
+        r->x = reinterpret_cast<double*>(r->mem + L.x);
+        r->yd = reinterpret_cast<double*>(r->mem + L.yd);
+        r->f = r->f_h.empty() ? nullptr : reinterpret_cast<double*>(r->mem + L.f);
+        r->gb = reinterpret_cast<double*>(r->mem + L.gb);
+        r->gx = reinterpret_cast<double*>(r->mem + L.gx);
+        r->coef = reinterpret_cast<double*>(r->mem + L.coef);
+        r->fac = r->mem + L.fac;
         const long long N = (long long)r->d.n * r->d.n;
-        cudaError_t e = cudaMemsetAsync(r->mem, 0, 2 * N * sizeof(double), s->st);   // x0 = 0
+        cudaError_t e = cudaMemsetAsync(r->x, 0, 2 * N * sizeof(double), s->st);   // x0 = 0
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(r->mem + 2 * N, r->yd_h.data(), N * sizeof(double), cudaMemcpyHostToDevice, s->st);
-        if (e == cudaSuccess && !r->f_h.empty())
-            e = cudaMemcpyAsync(r->mem + 3 * N, r->f_h.data(), N * sizeof(double), cudaMemcpyHostToDevice, s->st);
+            e = cudaMemcpyAsync(r->yd, r->yd_h.data(), N * sizeof(double), cudaMemcpyHostToDevice, s->st);
+        if (e == cudaSuccess && r->f)
+            e = cudaMemcpyAsync(r->f, r->f_h.data(), N * sizeof(double), cudaMemcpyHostToDevice, s->st);
         if (e != cudaSuccess) return sfail(s, RAS_ECUDA, std::string("admission copy: ") + cudaGetErrorString(e));
+        r->phase = ras_server::EVAL;
         s->pending.pop_front();
         s->active.push_back(r);
         s->slot_held += r->slot;
@@ -1512,84 +1615,129 @@ int server_admit(ras_server* s) {
     return RAS_OK;
 }
 
-int server_outer_iteration(ras_server* s) {
+// One step for the admitted set: evaluations, then one GMRES restart cycle.
+int server_step_active(ras_server* s) {
     ras_problem* h = s->ws;
     const int P = h->nprob;
     const ras_opts& o = s->o;
-    for (int p = 0; p < P; ++p) {
-        const long long N = plane(h, p);
-        CK(cudaMemcpyAsync(h->X + h->probs[p].ofs, s->active[p]->mem, 2 * N * sizeof(double),
-                           cudaMemcpyDeviceToDevice, h->st));
-    }
-    std::vector<double> pstart(P);
-    std::vector<ras_stats> st(P);
-    for (int p = 0; p < P; ++p) {
-        pstart[p] = (s->active[p]->k == 0) ? o.eps0 : o.eps_min;
-        st[p] = s->active[p]->stats;
-    }
-    const int rc = ras_apply_internal(h, pstart, h->F, st.data());
-    if (rc == RAS_ECUDA || rc == RAS_ETIMEOUT) return rc;
-    for (int p = 0; p < P; ++p) {
-        if (st[p].local_failures > s->active[p]->stats.local_failures) s->active[p]->failed = true;
-        s->active[p]->stats = st[p];
-    }
-    std::vector<int> all(P, 1), need(P, 0), its, conv;
-    TRY(set_mask(h, 1, all));
-    TRY(seg_norms2(h, h->F, 1));
-    bool any = false;
+    std::vector<int> ev(P, 0), kr(P, 0);
     for (int p = 0; p < P; ++p) {
         auto* r = s->active[p];
-        const double nrm = std::sqrt(h->h_scal[p * SS]);
-        if (r->k == 0) {
-            r->stop = std::max(o.tol, o.tol * nrm);
-            r->stats.res0 = nrm;
-        }
-        r->stats.res = nrm;
-        need[p] = (!r->failed && nrm > r->stop && r->k < o.kmax_outer_raspen) ? 1 : 0;
-        any = any || need[p];
-        if (!need[p]) {
-            r->stats.outer_its = r->k;
-            r->stats.status = r->failed ? RAS_ENOCONV : (nrm <= r->stop ? RAS_OK : RAS_ENOCONV);
+        const long long N = plane(h, p), ofs = h->probs[p].ofs;
+        CK(cudaMemcpyAsync(h->X + ofs, r->x, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        if (r->phase == ras_server::EVAL) {
+            ev[p] = 1;
+        } else {
+            kr[p] = 1;
+            CK(cudaMemcpyAsync(h->T1 + ofs, r->gb, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+            CK(cudaMemcpyAsync(h->Dv + ofs, r->gx, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
         }
     }
-    if (any) {
-        double seglen = 0.0;
-        for (int p = 0; p < P; ++p)
-            if (need[p]) seglen += (double)h->segs[p].len;
+    std::vector<int> done(P, 0);
+    // evaluations: the RASPEN function at x_k, the stop test, b = -F
+    if (std::any_of(ev.begin(), ev.end(), [](int v) { return v != 0; })) {
+        std::vector<double> pstart(P, 0.0);
+        std::vector<ras_stats> st(P);
+        for (int p = 0; p < P; ++p) {
+            st[p] = s->active[p]->stats;
+            if (ev[p]) pstart[p] = (s->active[p]->k == 0) ? o.eps0 : o.eps_min;
+        }
+        const int rc = ras_apply_internal(h, pstart, h->F, st.data());
+        if (rc == RAS_ECUDA || rc == RAS_ETIMEOUT) return rc;
+        for (int p = 0; p < P; ++p) {
+            if (!ev[p]) continue;
+            if (st[p].local_failures > s->active[p]->stats.local_failures) s->active[p]->failed = true;
+            s->active[p]->stats = st[p];
+        }
+        TRY(set_mask(h, 1, ev));
+        TRY(seg_norms2(h, h->F, 1));
+        std::vector<int> go(P, 0);
+        for (int p = 0; p < P; ++p) {
+            if (!ev[p]) continue;
+            auto* r = s->active[p];
+            const double nrm = std::sqrt(h->h_scal[p * SS]);
+            if (r->k == 0) {
+                r->stop = std::max(o.tol, o.tol * nrm);
+                r->stats.res0 = nrm;
+            }
+            r->stats.res = nrm;
+            if (!r->failed && nrm > r->stop && r->k < o.kmax_outer_raspen) {
+                go[p] = 1;
+                r->phase = ras_server::KRYLOV;
+                r->fresh = true;
+                r->its = 0;
+                kr[p] = 1;
+            } else {
+                done[p] = 1;
+                r->stats.outer_its = r->k;
+                r->stats.status = r->failed ? RAS_ENOCONV : (nrm <= r->stop ? RAS_OK : RAS_ENOCONV);
+            }
+        }
+        if (std::any_of(go.begin(), go.end(), [](int v) { return v != 0; })) {
+            TRY(set_mask(h, 1, go));
+            CK(timed(h, RAS_K_KRYLOV, 0.0, [&] {
+                return ras::launch_seg_scale(h->st, seg_grid(h, 1), h->d_segs, h->F, nullptr, -1.0, h->T1);
+            }));
+        }
+    }
+    // one GMRES restart cycle for the requests in the GMRES phase
+    if (std::any_of(kr.begin(), kr.end(), [](int v) { return v != 0; })) {
+        GmresResume rs;
+        rs.fresh.assign(P, 0);
+        rs.target.assign(P, 0.0);
+        rs.max_cycles = 1;
+        std::vector<int> its(P, 0), conv;
+        for (int p = 0; p < P; ++p) {
+            if (!kr[p]) continue;
+            rs.fresh[p] = s->active[p]->fresh ? 1 : 0;
+            rs.target[p] = s->active[p]->target;
+            its[p] = s->active[p]->its;
+        }
         auto A = [&](const double* in, double* out, const std::vector<int>& mask) {
             return jvp_internal(h, in, out, &mask);
         };
         auto M = [&](const double*, double*, const std::vector<int>&) { return RAS_OK; };
-        TRY(set_mask(h, 1, need));
-        CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
-            return ras::launch_seg_scale(h->st, seg_grid(h, 1), h->d_segs, h->F, nullptr, -1.0, h->T1);
-        }));
-        TRY(gmres(h, A, M, false, h->T1, h->Dv, need, its, conv));
-        CK(timed(h, RAS_K_KRYLOV, 24.0 * seglen, [&] {
-            return ras::launch_seg_add_scaled(h->st, seg_grid(h, 1), h->d_segs, h->X, h->Dv, 1.0, h->X);
-        }));
+        TRY(gmres(h, A, M, false, h->T1, h->Dv, kr, its, conv, &rs));
+        std::vector<int> upd(P, 0);
         for (int p = 0; p < P; ++p) {
-            if (!need[p]) continue;
-            s->active[p]->k += 1;
-            s->active[p]->stats.gmres_its += its[p];
+            if (!kr[p]) continue;
+            auto* r = s->active[p];
+            r->fresh = false;
+            r->target = rs.target[p];
+            r->its = its[p];
+            if (!rs.pending[p]) {
+                upd[p] = 1;
+                r->stats.gmres_its += r->its;
+                r->k += 1;
+                r->phase = ras_server::EVAL;
+            }
+        }
+        if (std::any_of(upd.begin(), upd.end(), [](int v) { return v != 0; })) {
+            TRY(set_mask(h, 1, upd));
+            CK(timed(h, RAS_K_KRYLOV, 0.0, [&] {
+                return ras::launch_seg_add_scaled(h->st, seg_grid(h, 1), h->d_segs, h->X, h->Dv, 1.0, h->X);
+            }));
         }
     }
     for (int p = 0; p < P; ++p) {
-        const long long N = plane(h, p);
-        CK(cudaMemcpyAsync(s->active[p]->mem, h->X + h->probs[p].ofs, 2 * N * sizeof(double),
-                           cudaMemcpyDeviceToDevice, h->st));
+        auto* r = s->active[p];
+        const long long N = plane(h, p), ofs = h->probs[p].ofs;
+        CK(cudaMemcpyAsync(r->x, h->X + ofs, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        if (r->phase == ras_server::KRYLOV) {
+            CK(cudaMemcpyAsync(r->gb, h->T1 + ofs, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+            CK(cudaMemcpyAsync(r->gx, h->Dv + ofs, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        }
     }
     TRY(sync(h));
-    // retire the requests that stopped
     std::vector<ras_server::Req*> keep;
     for (int p = 0; p < P; ++p) {
         auto* r = s->active[p];
-        if (need[p]) {
-            keep.push_back(r);
-        } else {
+        if (done[p]) {
             s->finished.push_back(r);
             s->scratch_active -= r->scratch;
             s->dirty = true;
+        } else {
+            keep.push_back(r);
         }
     }
     s->active.swap(keep);
@@ -1646,7 +1794,7 @@ int ras_server_submit(ras_server* s, const ras_problem_desc* d, long long* id) {
     r->yd_h.assign(d->y_d, d->y_d + N);
     if (d->f) r->f_h.assign(d->f, d->f + N);
     r->d.y_d = nullptr;
-    r->d.f = nullptr;
+    r->d.f = r->f_h.empty() ? nullptr : d->f;   // only its presence matters for the layout
     r->id = s->next_id++;
     s->pending.push_back(r);
     *id = r->id;
@@ -1659,7 +1807,7 @@ int ras_server_step(ras_server* s, int* active, int* finished) {
     int rc = server_admit(s);
     if (rc == RAS_OK && !s->active.empty()) {
         if (s->dirty) rc = server_relayout(s);
-        if (rc == RAS_OK) rc = server_outer_iteration(s);
+        if (rc == RAS_OK) rc = server_step_active(s);
         if (rc < 0 && s->ws) s->err = s->ws->err;
     }
     if (active) *active = (int)s->active.size();
@@ -1692,9 +1840,9 @@ int ras_server_fetch(ras_server* s, long long id, double* y_host, double* p_host
         if (r->id != id) continue;
         const long long N = (long long)r->d.n * r->d.n;
         cudaError_t e = cudaSuccess;
-        if (y_host) e = cudaMemcpyAsync(y_host, r->mem, N * sizeof(double), cudaMemcpyDeviceToHost, s->st);
+        if (y_host) e = cudaMemcpyAsync(y_host, r->x, N * sizeof(double), cudaMemcpyDeviceToHost, s->st);
         if (e == cudaSuccess && p_host)
-            e = cudaMemcpyAsync(p_host, r->mem + N, N * sizeof(double), cudaMemcpyDeviceToHost, s->st);
+            e = cudaMemcpyAsync(p_host, r->x + N, N * sizeof(double), cudaMemcpyDeviceToHost, s->st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
         if (e != cudaSuccess) return sfail(s, RAS_ECUDA, std::string("fetch: ") + cudaGetErrorString(e));
         if (st) *st = r->stats;

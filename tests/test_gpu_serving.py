@@ -141,3 +141,41 @@ def test_server_rejects_bad_requests():
         assert ras.ras_server_step(s) == (0, 0)
     finally:
         ras.ras_server_destroy(s)
+
+
+def test_easy_request_is_not_held_by_a_hard_one():
+    """A request that needs few GMRES steps, admitted with one that needs many,
+    finishes first (its steps are restart cycles, not the other's whole GMRES
+    solve) and still equals its solve alone."""
+    base = inputs.problem("n63")
+    hard = dict(base, n=63, sx=4, sy=4, overlap=2, phi=0, nu=1e-6, mu=1e-3, yd=("fourier", 77))
+    easy = dict(base, n=24, sx=2, sy=2, overlap=1, phi=0, nu=1e-3, mu=1e-2, yd=("fourier", 78))
+    opts = gpu_opts(base, ras.RAS_MIXED)
+    s = ras.ras_server_create(4 << 30, 8, opts)
+    try:
+        ih = ras.ras_server_submit(s, _req(hard))
+        ie = ras.ras_server_submit(s, _req(easy))
+        order, res = [], {}
+        for _ in range(2000):
+            ras.ras_server_step(s)
+            for rid in ras.ras_server_finished_ids(s):
+                rc, y, p, st = ras.ras_server_fetch(s, rid)
+                assert rc == ras.RAS_OK
+                order.append(rid)
+                res[rid] = (y, p, st.as_dict())
+            if len(order) == 2:
+                break
+        assert order == [ie, ih]
+    finally:
+        ras.ras_server_destroy(s)
+    for rid, c in ((ie, easy), (ih, hard)):
+        h = gpu_problem(c, ras.RAS_MIXED)
+        try:
+            y1, p1 = zeros(c["n"]), zeros(c["n"])
+            rc, st1 = ras.ras_raspen_solve(h, y1, p1)
+            y, p, st = res[rid]
+            assert rel_inf(y, y1.cpu().numpy(), p1.cpu().numpy()) <= MIXED_TOL
+            assert rel_inf(p, p1.cpu().numpy(), y1.cpu().numpy()) <= MIXED_TOL
+            assert st["outer_its"] == st1.outer_its and st["inner_its_sum"] == st1.inner_its_sum
+        finally:
+            ras.ras_destroy(h)
