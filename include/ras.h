@@ -197,6 +197,9 @@ int ras_batch_raspen_solve(ras_problem* h, double* const* y, double* const* p, r
  *   and returns its status (RAS_OK or RAS_ENOCONV); RAS_EINVAL for an unknown
  *   id. An idle server (nothing waiting or admitted) then releases its
  *   workspace.
+ * ras_server_cancel: drops request id wherever it is (waiting, admitted or
+ *   finished), freeing its storage; RAS_EINVAL for an unknown id. Between
+ *   steps only (the server is not thread-safe).
  * ras_server_device_bytes: device bytes held now (workspace + slots).
  * The paper has no serving loop: this is the benchmark spec's continuous-batching
  * use of Alg. 2 and Alg. 3 over independent problems. */
@@ -209,6 +212,7 @@ int ras_server_step(ras_server* s, int* active, int* finished);
 int ras_server_counts(const ras_server* s, int* pending, int* active, int* finished);
 int ras_server_finished_ids(const ras_server* s, long long* ids, int cap);
 int ras_server_fetch(ras_server* s, long long id, double* y_host, double* p_host, ras_stats* st);
+int ras_server_cancel(ras_server* s, long long id);
 size_t ras_server_device_bytes(const ras_server* s);
 const char* ras_server_last_error(const ras_server* s);
 void ras_server_destroy(ras_server* s);
@@ -269,6 +273,36 @@ int ras_newton_solve(ras_problem* h, double* y, double* p, ras_stats* stats);
 #define RAS_METHOD_RASPEN     0
 #define RAS_METHOD_NEWTON_RAS 1
 #define RAS_METHOD_NEWTON     2
+
+/* Checkpoint / resume of an outer iteration (single-problem handles). The
+ * state of an outer solve between outer iterations is its iterate x_k (the
+ * caller's y, p) and:
+ *   method  RAS_METHOD_* of the solve;
+ *   k       outer iterations done;
+ *   eps     eps_k of the continuation (Newton_RAS / Newton; eps_min for
+ *           RASPEN once k > 0, eps0 at k = 0);
+ *   res0    ||F(x^0)|| of the original start, and stop = max(tol, tol*res0),
+ *           which fix the stop test.
+ * ras_get_state: the state at the end of the last ras_raspen_solve /
+ * ras_newton_ras_solve / ras_newton_solve call on h (also when it stopped at
+ * kmax with RAS_ENOCONV); RAS_ESTATE if there was none.
+ * ras_set_state: the next solve call of the same method on h resumes from
+ * the state (one-shot), with y, p = x_k as its initial guess: it continues
+ * the outer count, keeps the stop test, and applies eps-continuation only
+ * where the uninterrupted solve would. Every reduction has a fixed order, so
+ * the resumed solve reproduces the uninterrupted one bit for bit. RAS_EINVAL
+ * for an invalid state; a solve of another method returns RAS_ESTATE.
+ * The paper has no checkpointing; this is the continuation state of Alg. 1
+ * and Alg. 2 made explicit. */
+typedef struct {
+    int method;
+    int k;
+    double eps;
+    double res0;
+    double stop;
+} ras_state;
+int ras_get_state(const ras_problem* h, ras_state* state);
+int ras_set_state(ras_problem* h, const ras_state* state);
 /* End-to-end call on HOST buffers: copies y_d_host (n*n, NULL keeps the
  * current y_d) and the initial guess y_host, p_host to the device, solves with
  * `method`, and copies the solution back into y_host, p_host. */

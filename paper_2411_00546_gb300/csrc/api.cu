@@ -19,6 +19,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ras.h"
 #include "ras_internal.cuh"
 
@@ -72,6 +74,10 @@ struct ras_problem {
     int nbp = 0;                 // blocks per problem of the segmented kernels
     int sms = 0;                 // SMs of the device (0 until queried)
     bool own_factors = true;     // factors and coefficients in gpool / coef (else per subdomain pointers)
+    ras_state last_state{};      // state at the end of the last outer solve (checkpoint)
+    bool have_last = false;
+    ras_state resume{};          // one-shot resume point for the next outer solve
+    bool have_resume = false;
     int* d_order = nullptr;      // subdomain indices, largest factors first (solve kernels)
     int* d_ticket = nullptr;     // work counter of the persistent solve kernels
     // block tables of the segmented kernels, one per mask row (0: GMRES/JVP,
@@ -108,6 +114,12 @@ struct ras_problem {
 namespace {
 
 constexpr int SS = ras::SEG_STRIDE;   // per-problem stride of scalar arrays
+
+// NVTX range for tools (Nsight); costs a few nanoseconds when none is attached.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 constexpr int NTILE = 5;              // register tiles 2, 4, 6, 8, 10
 
 int fail(ras_problem* h, int code, const std::string& msg) {
@@ -446,6 +458,7 @@ int launch_factor(ras_problem* h, int only_active, double flops, int nwork) {
 // local solves start); per-problem counters into stats[p] (may be null).
 template <typename T>
 int ras_apply_T(ras_problem* h, const std::vector<double>& pstart, double* Fout, ras_stats* stats) {
+    Range range("ras: RASPEN function (local Newton solves)");
     const NewtonParams np = inner_params(h->o);
     T* gp = (T*)h->gpool;
     T* wp = (T*)h->wpool;
@@ -630,6 +643,7 @@ struct GmresResume {
 template <class Aop, class Mop>
 int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, const std::vector<int>& part,
           std::vector<int>& its, std::vector<int>& conv, GmresResume* res = nullptr) {
+    Range range("ras: GMRES");
     const int P = h->nprob, m = h->o.gmres_restart, maxit = h->o.gmres_maxit;
     const long long L = h->L;
     const double rtol = h->o.gmres_rtol;
@@ -837,19 +851,25 @@ int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, c
 // RASPEN for every problem of the handle, in lockstep: a problem leaves the
 // loop when its own stop test holds (or at kmax).
 int raspen_internal(ras_problem* h, ras_stats* s) {
+    Range range("ras: RASPEN solve");
     const int P = h->nprob;
     const ras_opts& o = h->o;
-    std::vector<double> pstart(P, o.eps0);
+    const bool resumed = (P == 1 && h->have_resume);
+    const ras_state rs = h->resume;
+    h->have_resume = false;
+    if (resumed && rs.method != RAS_METHOD_RASPEN) return fail(h, RAS_ESTATE, "the state belongs to another method");
+    std::vector<double> pstart(P, (resumed && rs.k > 0) ? o.eps_min : o.eps0);
     int rc = ras_apply_internal(h, pstart, h->F, s);
     if (rc < 0) return rc;
-    std::vector<int> all(P, 1), need(P, 0), k(P, 0), its, conv;
-    std::vector<double> nrm(P), stop(P);
+    std::vector<int> all(P, 1), need(P, 0), k(P, resumed ? rs.k : 0), its, conv;
+    std::vector<double> nrm(P), stop(P), res0(P);
     TRY(set_mask(h, 1, all));
     TRY(seg_norms2(h, h->F, 1));
     for (int p = 0; p < P; ++p) {
         nrm[p] = std::sqrt(h->h_scal[p * SS]);
-        stop[p] = std::max(o.tol, o.tol * nrm[p]);
-        if (s) s[p].res0 = nrm[p];
+        stop[p] = resumed ? rs.stop : std::max(o.tol, o.tol * nrm[p]);
+        res0[p] = resumed ? rs.res0 : nrm[p];
+        if (s) s[p].res0 = res0[p];
     }
     double seglen = 0.0;
     for (auto& sg : h->segs) seglen += (double)sg.len;
@@ -902,6 +922,10 @@ int raspen_internal(ras_problem* h, ras_stats* s) {
         }
         worst = std::min(worst, st);
     }
+    if (P == 1) {
+        h->last_state = ras_state{RAS_METHOD_RASPEN, k[0], k[0] > 0 ? o.eps_min : o.eps0, res0[0], stop[0]};
+        h->have_last = true;
+    }
     if (worst < 0) return fail(h, worst, "RASPEN reached kmax_outer_raspen");
     return RAS_OK;
 }
@@ -912,14 +936,21 @@ int raspen_internal(ras_problem* h, ras_stats* s) {
 // Newton_RAS) or unpreconditioned (the paper's Newton baseline). With
 // eps0 > eps_min the continuation makes them Newton_RAS,eps / Newton_eps.
 int newton_internal(ras_problem* h, ras_stats* s, bool prec) {
+    Range range(prec ? "ras: Newton_RAS solve" : "ras: Newton solve");
     const long long N = plane(h, 0);
     const ras_opts& o = h->o;
     const double seglen = (double)h->segs[0].len;
-    double eps = o.eps0, nrm, flr;
+    const int method = prec ? RAS_METHOD_NEWTON_RAS : RAS_METHOD_NEWTON;
+    const bool resumed = h->have_resume;
+    const ras_state rs = h->resume;
+    h->have_resume = false;
+    if (resumed && rs.method != method) return fail(h, RAS_ESTATE, "the state belongs to another method");
+    double eps = resumed ? rs.eps : o.eps0, nrm, flr;
     TRY(residual_norm(h, h->X, nullptr, 0.0, eps, h->F, nrm, flr));
-    const double stop = std::max(o.tol, o.tol * nrm);
-    if (s) s->res0 = nrm;
-    int k = 0, status = RAS_OK;
+    const double stop = resumed ? rs.stop : std::max(o.tol, o.tol * nrm);
+    const double res0 = resumed ? rs.res0 : nrm;
+    if (s) s->res0 = res0;
+    int k = resumed ? rs.k : 0, status = RAS_OK;
     std::vector<int> one(1, 1), its, conv;
     auto A = [&](const double* in, double* out, const std::vector<int>&) -> int {
         CK(timed(h, RAS_K_OTHER, 56.0 * N, [&] {
@@ -978,6 +1009,8 @@ int newton_internal(ras_problem* h, ras_stats* s, bool prec) {
         s->status = status;
         s->eps_final = eps;
     }
+    h->last_state = ras_state{method, k, eps, res0, stop};
+    h->have_last = true;
     if (status < 0) return fail(h, status, prec ? "Newton_RAS stopped without convergence"
                                                 : "Newton stopped without convergence");
     return status;
@@ -1388,6 +1421,26 @@ int ras_newton_solve(ras_problem* h, double* y, double* p, ras_stats* stats) {
     return rc;
 }
 
+int ras_get_state(const ras_problem* h, ras_state* state) {
+    if (!h || !state) return RAS_EINVAL;
+    if (h->nprob != 1 || !h->have_last) return RAS_ESTATE;
+    *state = h->last_state;
+    return RAS_OK;
+}
+
+int ras_set_state(ras_problem* h, const ras_state* st) {
+    if (!h || !st) return RAS_EINVAL;
+    TRY(need_single(h));
+    if ((st->method != RAS_METHOD_RASPEN && st->method != RAS_METHOD_NEWTON_RAS &&
+         st->method != RAS_METHOD_NEWTON) ||
+        st->k < 0 || !(st->eps > 0) || !std::isfinite(st->eps) || !(st->res0 >= 0) || !std::isfinite(st->res0) ||
+        !(st->stop > 0) || !std::isfinite(st->stop))
+        return fail(h, RAS_EINVAL, "invalid state");
+    h->resume = *st;
+    h->have_resume = true;
+    return RAS_OK;
+}
+
 int ras_solve_host(ras_problem* h, int method, const double* y_d_host, double* y_host, double* p_host,
                    ras_stats* stats) {
     if (!h || !y_host || !p_host ||
@@ -1617,6 +1670,7 @@ int server_admit(ras_server* s) {
 
 // One step for the admitted set: evaluations, then one GMRES restart cycle.
 int server_step_active(ras_server* s) {
+    Range range("ras: server step");
     ras_problem* h = s->ws;
     const int P = h->nprob;
     const ras_opts& o = s->o;
@@ -1862,6 +1916,34 @@ int ras_server_fetch(ras_server* s, long long id, double* y_host, double* p_host
         return status;
     }
     return sfail(s, RAS_EINVAL, "no finished request with this id");
+}
+
+int ras_server_cancel(ras_server* s, long long id) {
+    if (!s) return RAS_EINVAL;
+    for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
+        if ((*it)->id != id) continue;
+        delete *it;
+        s->pending.erase(it);
+        return RAS_OK;
+    }
+    auto drop = [&](std::vector<ras_server::Req*>& v, bool admitted) -> bool {
+        for (auto it = v.begin(); it != v.end(); ++it) {
+            ras_server::Req* r = *it;
+            if (r->id != id) continue;
+            if (r->mem) cudaFreeAsync(r->mem, s->st);
+            s->slot_held -= r->slot;
+            if (admitted) {
+                s->scratch_active -= r->scratch;
+                s->dirty = true;
+            }
+            v.erase(it);
+            delete r;
+            return true;
+        }
+        return false;
+    };
+    if (drop(s->active, true) || drop(s->finished, false)) return RAS_OK;
+    return sfail(s, RAS_EINVAL, "no request with this id");
 }
 
 size_t ras_server_device_bytes(const ras_server* s) {

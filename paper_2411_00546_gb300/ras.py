@@ -64,6 +64,14 @@ class ras_problem_desc(ctypes.Structure):
                 ("y_d", ctypes.c_void_p), ("f", ctypes.c_void_p)]
 
 
+class ras_state(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("k", ctypes.c_int), ("eps", ctypes.c_double), ("res0", ctypes.c_double),
+                ("stop", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class RasError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("ras error %d: %s" % (code, msg))
@@ -90,6 +98,8 @@ _SIGS = {
     "ras_raspen_solve": (_I, [_P, _P, _P, ctypes.POINTER(ras_stats)]),
     "ras_newton_ras_solve": (_I, [_P, _P, _P, ctypes.POINTER(ras_stats)]),
     "ras_newton_solve": (_I, [_P, _P, _P, ctypes.POINTER(ras_stats)]),
+    "ras_get_state": (_I, [_P, ctypes.POINTER(ras_state)]),
+    "ras_set_state": (_I, [_P, ctypes.POINTER(ras_state)]),
     "ras_solve_host": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(ras_stats)]),
     "ras_local_iterations": (_I, [_P, ctypes.POINTER(_I), _I]),
     "ras_subdomain_count": (_I, [_P]),
@@ -108,6 +118,7 @@ _SIGS = {
     "ras_server_counts": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "ras_server_finished_ids": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), _I]),
     "ras_server_fetch": (_I, [_P, ctypes.c_longlong, _P, _P, ctypes.POINTER(ras_stats)]),
+    "ras_server_cancel": (_I, [_P, ctypes.c_longlong]),
     "ras_server_device_bytes": (ctypes.c_size_t, [_P]),
     "ras_server_last_error": (ctypes.c_char_p, [_P]),
     "ras_server_destroy": (None, [_P]),
@@ -301,6 +312,16 @@ def ras_newton_solve(h, y, p, check=True):
     if check:
         h._check(rc)
     return rc, st
+
+
+def ras_get_state(h):
+    st = ras_state()
+    h._check(lib().ras_get_state(h.ptr, ctypes.byref(st)))
+    return st
+
+
+def ras_set_state(h, st):
+    return h._check(lib().ras_set_state(h.ptr, ctypes.byref(st)))
 
 
 def ras_solve_host(h, method, y_d_host, y_host, p_host, check=True):
@@ -505,6 +526,11 @@ def ras_server_fetch(s, rid):
     if rc == RAS_EINVAL:
         raise RasError(rc, lib().ras_server_last_error(s.ptr).decode())
     return rc, y, p, st
+
+
+def ras_server_cancel(s, rid):
+    s._check(lib().ras_server_cancel(s.ptr, rid))
+    s.sizes.pop(rid, None)
 
 
 def ras_server_device_bytes(s):

@@ -179,3 +179,30 @@ def test_easy_request_is_not_held_by_a_hard_one():
             assert st["outer_its"] == st1.outer_its and st["inner_its_sum"] == st1.inner_its_sum
         finally:
             ras.ras_destroy(h)
+
+
+def test_cancel_waiting_and_admitted_requests():
+    """Cancelling a waiting and an admitted request frees them; the others
+    still finish with their solve-alone results."""
+    cfgs = _cfgs()
+    opts = gpu_opts(cfgs[0], ras.RAS_MIXED)
+    s = ras.ras_server_create(4 << 30, 2, opts)   # two admitted at a time
+    try:
+        ids = [ras.ras_server_submit(s, _req(c)) for c in cfgs[:4]]
+        ras.ras_server_step(s)                     # admits ids[0], ids[1]
+        assert ras.ras_server_counts(s)[:2] == (2, 2)
+        ras.ras_server_cancel(s, ids[1])           # admitted
+        ras.ras_server_cancel(s, ids[3])           # waiting
+        with pytest.raises(ras.RasError):
+            ras.ras_server_cancel(s, 999)
+        got = {}
+        for _ in range(2000):
+            ras.ras_server_step(s)
+            for rid in ras.ras_server_finished_ids(s):
+                got[rid] = ras.ras_server_fetch(s, rid)
+            if len(got) == 2:
+                break
+        assert sorted(got) == sorted([ids[0], ids[2]])
+        assert ras.ras_server_counts(s) == (0, 0, 0)
+    finally:
+        ras.ras_server_destroy(s)
