@@ -221,6 +221,23 @@ def measure_methods(ras, torch, dev, stream):
     return out
 
 
+def max_over_ranks(value, dist, device):
+    """Largest per-rank value over all ranks (the value itself without a
+    process group). The whole-job time of a replicated step is the slowest
+    rank's."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, seconds):
+    """Solves per second of the whole job: every rank solves `steps` problems,
+    and the job takes the slowest rank's time."""
+    return world * steps / seconds
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -431,11 +448,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     prof = ras.ras_profile_all(h)
     ras.ras_profile(h, 0)
-    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    value = world * args.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist, dev)
+    value = whole_job_rate(world, args.steps, ms_max / 1e3)
     y_mixed = y.detach().cpu().numpy().copy()
     p_mixed = p.detach().cpu().numpy().copy()
 
@@ -472,8 +486,8 @@ def main():
             ph.zero_()
             ras.ras_solve_host(h, ras.RAS_METHOD_RASPEN, ydh, yh, ph)
         barrier()
-        dt = time.perf_counter() - t0
-        e2e = {"value": world * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": 3 * n * n * 8,
+        dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        e2e = {"value": whole_job_rate(world, args.steps, dt), "unit": UNIT, "h2d_bytes_per_step": 3 * n * n * 8,
                "d2h_bytes_per_step": 2 * n * n * 8}
 
     # roofline of the dominant kernel (by device time in the timed region)
@@ -569,14 +583,16 @@ def main():
     if roof is not None:
         roof["traffic"] = traffic_for(dom, args.workload)
 
+    # the uneven batch, the serving sample and the method comparison describe
+    # one GPU: rank 0 runs them (replicas would only repeat them)
     batch = None
-    if not args.no_batch:
+    if rank == 0 and not args.no_batch:
         batch = measure_batch(ras, torch, dev, stream)
     serving = None
-    if not args.no_serve:
+    if rank == 0 and not args.no_serve:
         serving = measure_serving(ras, torch, dev, stream, args.serve_requests)
     methods = None
-    if not args.no_methods:
+    if rank == 0 and not args.no_methods:
         methods = measure_methods(ras, torch, dev, stream)
 
     cpu = None
