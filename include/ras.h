@@ -174,9 +174,10 @@ int ras_batch_raspen_solve(ras_problem* h, double* const* y, double* const* p, r
  * problem alone (same x0 = 0, same options), so its result agrees with the
  * solve alone to rounding.
  *
- * ras_server_create: hbm_budget = device bytes the server may hold (slot
- *   storage of admitted and unfetched requests plus the batch workspace, by
- *   the estimate of ras_server_request_bytes); max_active = most requests
+ * ras_server_create: hbm_budget = device bytes the server may hold (request
+ *   storage of admitted and unfetched requests plus the two batch workspaces,
+ *   one per phase, each at most the admitted set's workspace estimate: a
+ *   request is charged slot + 2 x workspace bytes of ras_server_request_bytes); max_active = most requests
  *   advanced together (1..4096); o = options shared by all requests (NULL:
  *   defaults); stream = cudaStream_t for all work. RAS_EINVAL on bad values.
  * ras_server_request_bytes: host-only estimate for one request: slot bytes

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <deque>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -1517,11 +1518,13 @@ void ras_destroy(ras_problem* h) {
 // changes (buffers only grow). Admission is first come, first served while
 // the estimate of request storage plus workspace stays within the budget.
 struct ras_server {
-    ras_problem* ws = nullptr;
+    ras_problem* ws = nullptr;        // workspace of the requests in evaluation (stream st)
+    ras_problem* wk = nullptr;        // workspace of the requests in GMRES (stream st2)
     size_t budget = 0;
     int max_active = 0;
     ras_opts o{};
     cudaStream_t st = nullptr;
+    cudaStream_t st2 = nullptr;
     enum { EVAL = 0, KRYLOV = 1 };
     struct Req {
         long long id = 0;
@@ -1537,9 +1540,10 @@ struct ras_server {
         ras_stats stats{};
     };
     std::deque<Req*> pending;
-    std::vector<Req*> active;
+    std::vector<Req*> active;            // every admitted request
     std::vector<Req*> finished;          // result kept until fetched
-    bool dirty = true;
+    std::vector<Req*> ev, kr;            // admitted requests by phase (layouts of ws / wk)
+    bool dirty = true, dirty_k = true;
     long long next_id = 1;
     size_t slot_held = 0, scratch_active = 0, ws_cap = 0;
     std::string err;
@@ -1594,16 +1598,15 @@ int request_bytes(const ras_problem_desc& d, const ras_opts& o, size_t& slot, si
     return RAS_OK;
 }
 
-int server_relayout(ras_server* s) {
-    if (!s->ws) {
-        s->ws = new ras_problem();
-        s->ws->o = s->o;
-        s->ws->st = s->st;
-        s->ws->own_factors = false;
+int server_relayout(ras_server* s, ras_problem*& h, cudaStream_t st, const std::vector<ras_server::Req*>& reqs) {
+    if (!h) {
+        h = new ras_problem();
+        h->o = s->o;
+        h->st = st;
+        h->own_factors = false;
     }
-    ras_problem* h = s->ws;
     std::vector<ras_problem_desc> descs;
-    for (auto* r : s->active) {
+    for (auto* r : reqs) {
         ras_problem_desc d = r->d;
         d.y_d = r->yd;
         d.f = r->f;
@@ -1615,7 +1618,7 @@ int server_relayout(ras_server* s) {
     for (int p = 0; p < h->nprob; ++p) {
         h->probs[p].yd = descs[p].y_d;
         h->probs[p].f = descs[p].f;
-        auto* r = s->active[p];
+        auto* r = reqs[p];
         const SubDev& first = h->subs[h->sub_first[p]];
         for (int k = 0; k < h->sub_count[p]; ++k) {
             SubDev& sd = h->subs[h->sub_first[p] + k];
@@ -1624,14 +1627,15 @@ int server_relayout(ras_server* s) {
         }
     }
     TRY(upload_layout(h));
-    s->dirty = false;
     return RAS_OK;
 }
 
 int server_admit(ras_server* s) {
     while (!s->pending.empty() && (int)s->active.size() < s->max_active) {
         auto* r = s->pending.front();
-        const size_t cap = std::max(s->ws_cap, s->scratch_active + r->scratch);
+        // each of the two workspaces serves part of the admitted set, so
+        // neither needs more than the whole set's scratch
+        const size_t cap = std::max(s->ws_cap, 2 * (s->scratch_active + r->scratch));
         if (cap + s->slot_held + r->slot > s->budget) break;   // first come, first served
         ras_problem tmp;
         tmp.o = s->o;
@@ -1660,6 +1664,7 @@ int server_admit(ras_server* s) {
         r->phase = ras_server::EVAL;
         s->pending.pop_front();
         s->active.push_back(r);
+        s->ev.push_back(r);
         s->slot_held += r->slot;
         s->scratch_active += r->scratch;
         s->ws_cap = cap;
@@ -1668,133 +1673,180 @@ int server_admit(ras_server* s) {
     return RAS_OK;
 }
 
-// One step for the admitted set: evaluations, then one GMRES restart cycle.
-int server_step_active(ras_server* s) {
-    Range range("ras: server step");
-    ras_problem* h = s->ws;
+// The evaluation phase of requests `reqs` (workspace h): the RASPEN function
+// at x_k and the stop test; those that go on store b = -F(x_k) and are marked
+// for GMRES (done[p] = 0, go[p] = 1), the others are finished (done[p] = 1).
+int server_eval(ras_server* s, ras_problem* h, const std::vector<ras_server::Req*>& reqs, std::vector<int>& done,
+                std::vector<int>& go) {
+    Range range("ras: server evaluations");
     const int P = h->nprob;
     const ras_opts& o = s->o;
-    std::vector<int> ev(P, 0), kr(P, 0);
+    done.assign(P, 0);
+    go.assign(P, 0);
+    std::vector<double> pstart(P);
+    std::vector<ras_stats> st(P);
     for (int p = 0; p < P; ++p) {
-        auto* r = s->active[p];
+        auto* r = reqs[p];
+        CK(cudaMemcpyAsync(h->X + h->probs[p].ofs, r->x, 2 * plane(h, p) * sizeof(double), cudaMemcpyDeviceToDevice,
+                           h->st));
+        st[p] = r->stats;
+        pstart[p] = (r->k == 0) ? o.eps0 : o.eps_min;
+    }
+    const int rc = ras_apply_internal(h, pstart, h->F, st.data());
+    if (rc == RAS_ECUDA || rc == RAS_ETIMEOUT) return rc;
+    for (int p = 0; p < P; ++p) {
+        if (st[p].local_failures > reqs[p]->stats.local_failures) reqs[p]->failed = true;
+        reqs[p]->stats = st[p];
+    }
+    TRY(set_mask(h, 1, std::vector<int>(P, 1)));
+    TRY(seg_norms2(h, h->F, 1));
+    for (int p = 0; p < P; ++p) {
+        auto* r = reqs[p];
+        const double nrm = std::sqrt(h->h_scal[p * SS]);
+        if (r->k == 0) {
+            r->stop = std::max(o.tol, o.tol * nrm);
+            r->stats.res0 = nrm;
+        }
+        r->stats.res = nrm;
+        if (!r->failed && nrm > r->stop && r->k < o.kmax_outer_raspen) {
+            go[p] = 1;
+        } else {
+            done[p] = 1;
+            r->stats.outer_its = r->k;
+            r->stats.status = r->failed ? RAS_ENOCONV : (nrm <= r->stop ? RAS_OK : RAS_ENOCONV);
+        }
+    }
+    if (std::any_of(go.begin(), go.end(), [](int v) { return v != 0; })) {
+        TRY(set_mask(h, 1, go));
+        CK(timed(h, RAS_K_KRYLOV, 0.0, [&] {
+            return ras::launch_seg_scale(h->st, seg_grid(h, 1), h->d_segs, h->F, nullptr, -1.0, h->T1);
+        }));
+        for (int p = 0; p < P; ++p)
+            if (go[p])
+                CK(cudaMemcpyAsync(reqs[p]->gb, h->T1 + h->probs[p].ofs, 2 * plane(h, p) * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, h->st));
+    }
+    return sync(h);
+}
+
+// One GMRES restart cycle for requests `reqs` (workspace h); those whose
+// GMRES stopped take x_{k+1} = x_k + d (stopped[p] = 1).
+int server_krylov(ras_server* s, ras_problem* h, const std::vector<ras_server::Req*>& reqs,
+                  std::vector<int>& stopped) {
+    Range range("ras: server GMRES cycles");
+    const int P = h->nprob;
+    stopped.assign(P, 0);
+    GmresResume rs;
+    rs.fresh.assign(P, 0);
+    rs.target.assign(P, 0.0);
+    rs.max_cycles = 1;
+    std::vector<int> its(P, 0), conv, all(P, 1);
+    for (int p = 0; p < P; ++p) {
+        auto* r = reqs[p];
         const long long N = plane(h, p), ofs = h->probs[p].ofs;
         CK(cudaMemcpyAsync(h->X + ofs, r->x, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-        if (r->phase == ras_server::EVAL) {
-            ev[p] = 1;
-        } else {
-            kr[p] = 1;
-            CK(cudaMemcpyAsync(h->T1 + ofs, r->gb, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        CK(cudaMemcpyAsync(h->T1 + ofs, r->gb, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        if (!r->fresh)
             CK(cudaMemcpyAsync(h->Dv + ofs, r->gx, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-        }
+        rs.fresh[p] = r->fresh ? 1 : 0;
+        rs.target[p] = r->target;
+        its[p] = r->its;
     }
-    std::vector<int> done(P, 0);
-    // evaluations: the RASPEN function at x_k, the stop test, b = -F
-    if (std::any_of(ev.begin(), ev.end(), [](int v) { return v != 0; })) {
-        std::vector<double> pstart(P, 0.0);
-        std::vector<ras_stats> st(P);
-        for (int p = 0; p < P; ++p) {
-            st[p] = s->active[p]->stats;
-            if (ev[p]) pstart[p] = (s->active[p]->k == 0) ? o.eps0 : o.eps_min;
-        }
-        const int rc = ras_apply_internal(h, pstart, h->F, st.data());
-        if (rc == RAS_ECUDA || rc == RAS_ETIMEOUT) return rc;
-        for (int p = 0; p < P; ++p) {
-            if (!ev[p]) continue;
-            if (st[p].local_failures > s->active[p]->stats.local_failures) s->active[p]->failed = true;
-            s->active[p]->stats = st[p];
-        }
-        TRY(set_mask(h, 1, ev));
-        TRY(seg_norms2(h, h->F, 1));
-        std::vector<int> go(P, 0);
-        for (int p = 0; p < P; ++p) {
-            if (!ev[p]) continue;
-            auto* r = s->active[p];
-            const double nrm = std::sqrt(h->h_scal[p * SS]);
-            if (r->k == 0) {
-                r->stop = std::max(o.tol, o.tol * nrm);
-                r->stats.res0 = nrm;
-            }
-            r->stats.res = nrm;
-            if (!r->failed && nrm > r->stop && r->k < o.kmax_outer_raspen) {
-                go[p] = 1;
-                r->phase = ras_server::KRYLOV;
-                r->fresh = true;
-                r->its = 0;
-                kr[p] = 1;
-            } else {
-                done[p] = 1;
-                r->stats.outer_its = r->k;
-                r->stats.status = r->failed ? RAS_ENOCONV : (nrm <= r->stop ? RAS_OK : RAS_ENOCONV);
-            }
-        }
-        if (std::any_of(go.begin(), go.end(), [](int v) { return v != 0; })) {
-            TRY(set_mask(h, 1, go));
-            CK(timed(h, RAS_K_KRYLOV, 0.0, [&] {
-                return ras::launch_seg_scale(h->st, seg_grid(h, 1), h->d_segs, h->F, nullptr, -1.0, h->T1);
-            }));
-        }
+    auto A = [&](const double* in, double* out, const std::vector<int>& mask) {
+        return jvp_internal(h, in, out, &mask);
+    };
+    auto M = [&](const double*, double*, const std::vector<int>&) { return RAS_OK; };
+    TRY(gmres(h, A, M, false, h->T1, h->Dv, all, its, conv, &rs));
+    for (int p = 0; p < P; ++p) {
+        auto* r = reqs[p];
+        r->fresh = false;
+        r->target = rs.target[p];
+        r->its = its[p];
+        if (!rs.pending[p]) stopped[p] = 1;
     }
-    // one GMRES restart cycle for the requests in the GMRES phase
-    if (std::any_of(kr.begin(), kr.end(), [](int v) { return v != 0; })) {
-        GmresResume rs;
-        rs.fresh.assign(P, 0);
-        rs.target.assign(P, 0.0);
-        rs.max_cycles = 1;
-        std::vector<int> its(P, 0), conv;
-        for (int p = 0; p < P; ++p) {
-            if (!kr[p]) continue;
-            rs.fresh[p] = s->active[p]->fresh ? 1 : 0;
-            rs.target[p] = s->active[p]->target;
-            its[p] = s->active[p]->its;
-        }
-        auto A = [&](const double* in, double* out, const std::vector<int>& mask) {
-            return jvp_internal(h, in, out, &mask);
-        };
-        auto M = [&](const double*, double*, const std::vector<int>&) { return RAS_OK; };
-        TRY(gmres(h, A, M, false, h->T1, h->Dv, kr, its, conv, &rs));
-        std::vector<int> upd(P, 0);
-        for (int p = 0; p < P; ++p) {
-            if (!kr[p]) continue;
-            auto* r = s->active[p];
-            r->fresh = false;
-            r->target = rs.target[p];
-            r->its = its[p];
-            if (!rs.pending[p]) {
-                upd[p] = 1;
-                r->stats.gmres_its += r->its;
-                r->k += 1;
-                r->phase = ras_server::EVAL;
-            }
-        }
-        if (std::any_of(upd.begin(), upd.end(), [](int v) { return v != 0; })) {
-            TRY(set_mask(h, 1, upd));
-            CK(timed(h, RAS_K_KRYLOV, 0.0, [&] {
-                return ras::launch_seg_add_scaled(h->st, seg_grid(h, 1), h->d_segs, h->X, h->Dv, 1.0, h->X);
-            }));
-        }
+    if (std::any_of(stopped.begin(), stopped.end(), [](int v) { return v != 0; })) {
+        TRY(set_mask(h, 1, stopped));
+        CK(timed(h, RAS_K_KRYLOV, 0.0, [&] {
+            return ras::launch_seg_add_scaled(h->st, seg_grid(h, 1), h->d_segs, h->X, h->Dv, 1.0, h->X);
+        }));
     }
     for (int p = 0; p < P; ++p) {
-        auto* r = s->active[p];
+        auto* r = reqs[p];
         const long long N = plane(h, p), ofs = h->probs[p].ofs;
-        CK(cudaMemcpyAsync(r->x, h->X + ofs, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-        if (r->phase == ras_server::KRYLOV) {
-            CK(cudaMemcpyAsync(r->gb, h->T1 + ofs, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        if (stopped[p])
+            CK(cudaMemcpyAsync(r->x, h->X + ofs, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        else
             CK(cudaMemcpyAsync(r->gx, h->Dv + ofs, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    }
+    return sync(h);
+}
+
+// One step: the evaluations (workspace ws, stream st) and the GMRES cycles
+// (workspace wk, stream st2) run at the same time on two host threads, then
+// the requests change phase. A request entering GMRES runs its first cycle
+// in the next step; one whose GMRES stopped is evaluated in the next step.
+int server_step_active(ras_server* s) {
+    Range range("ras: server step");
+    if (s->dirty && !s->ev.empty()) TRY(server_relayout(s, s->ws, s->st, s->ev));
+    if (s->dirty_k && !s->kr.empty()) TRY(server_relayout(s, s->wk, s->st2, s->kr));
+    s->dirty = s->dirty_k = false;
+    std::vector<int> done, go, stopped;
+    int rk = RAS_OK, re = RAS_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(s, RAS_ECUDA, "cudaGetDevice failed");
+    }
+    std::thread worker;
+    if (!s->kr.empty()) {
+        worker = std::thread([&] {
+            if (cudaSetDevice(dev) != cudaSuccess) {
+                rk = RAS_ECUDA;
+                return;
+            }
+            rk = server_krylov(s, s->wk, s->kr, stopped);
+        });
+    }
+    if (!s->ev.empty()) re = server_eval(s, s->ws, s->ev, done, go);
+    if (worker.joinable()) worker.join();
+    if (re < 0) {
+        if (s->ws) s->err = s->ws->err;
+        return re;
+    }
+    if (rk < 0) {
+        if (s->wk) s->err = s->wk->err;
+        return rk;
+    }
+    std::vector<ras_server::Req*> ev2, kr2;
+    for (size_t p = 0; p < s->kr.size(); ++p) {
+        auto* r = s->kr[p];
+        if (stopped[p]) {
+            r->stats.gmres_its += r->its;
+            r->k += 1;
+            r->phase = ras_server::EVAL;
+            ev2.push_back(r);
+        } else {
+            kr2.push_back(r);
         }
     }
-    TRY(sync(h));
-    std::vector<ras_server::Req*> keep;
-    for (int p = 0; p < P; ++p) {
-        auto* r = s->active[p];
+    for (size_t p = 0; p < s->ev.size(); ++p) {
+        auto* r = s->ev[p];
         if (done[p]) {
             s->finished.push_back(r);
             s->scratch_active -= r->scratch;
-            s->dirty = true;
-        } else {
-            keep.push_back(r);
+            s->active.erase(std::find(s->active.begin(), s->active.end(), r));
+        } else if (go[p]) {
+            r->phase = ras_server::KRYLOV;
+            r->fresh = true;
+            r->its = 0;
+            kr2.push_back(r);
         }
     }
-    s->active.swap(keep);
+    // layouts change when a phase group changes
+    s->dirty = !s->ev.empty() || !ev2.empty();
+    s->dirty_k = (kr2.size() != s->kr.size()) || !std::equal(kr2.begin(), kr2.end(), s->kr.begin());
+    s->ev.swap(ev2);
+    s->kr.swap(kr2);
     return RAS_OK;
 }
 
@@ -1815,6 +1867,11 @@ int ras_server_create(size_t hbm_budget, int max_active, const ras_opts* o, void
     s->budget = hbm_budget;
     s->max_active = max_active;
     s->st = (cudaStream_t)stream;
+    if (cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return RAS_ECUDA;
+    }
     *out = s;
     return RAS_OK;
 }
@@ -1840,7 +1897,7 @@ int ras_server_submit(ras_server* s, const ras_problem_desc* d, long long* id) {
         delete r;
         return sfail(s, RAS_EINVAL, "a subdomain is wider than 80 nodes (2 wx > 160)");
     }
-    if (r->slot + r->scratch > s->budget) {
+    if (r->slot + 2 * r->scratch > s->budget) {
         delete r;
         return sfail(s, RAS_ENOMEM, "the request alone exceeds the HBM budget");
     }
@@ -1860,9 +1917,14 @@ int ras_server_step(ras_server* s, int* active, int* finished) {
     const size_t fin0 = s->finished.size();
     int rc = server_admit(s);
     if (rc == RAS_OK && !s->active.empty()) {
-        if (s->dirty) rc = server_relayout(s);
-        if (rc == RAS_OK) rc = server_step_active(s);
-        if (rc < 0 && s->ws) s->err = s->ws->err;
+        // admission writes request storage on st; the GMRES stream waits for it
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(ev, s->st);
+            cudaStreamWaitEvent(s->st2, ev, 0);
+            cudaEventDestroy(ev);
+        }
+        rc = server_step_active(s);
     }
     if (active) *active = (int)s->active.size();
     if (finished) *finished = (int)(s->finished.size() - fin0);
@@ -1905,13 +1967,14 @@ int ras_server_fetch(ras_server* s, long long id, double* y_host, double* p_host
         s->finished.erase(it);
         const int status = r->stats.status;
         delete r;
-        // an idle server gives its workspace back
-        if (s->active.empty() && s->pending.empty() && s->ws) {
+        // an idle server gives its workspaces back
+        if (s->active.empty() && s->pending.empty()) {
             cudaStreamSynchronize(s->st);
-            ras_destroy(s->ws);
-            s->ws = nullptr;
+            if (s->ws) ras_destroy(s->ws);
+            if (s->wk) ras_destroy(s->wk);
+            s->ws = s->wk = nullptr;
             s->ws_cap = 0;
-            s->dirty = true;
+            s->dirty = s->dirty_k = true;
         }
         return status;
     }
@@ -1942,13 +2005,21 @@ int ras_server_cancel(ras_server* s, long long id) {
         }
         return false;
     };
+    for (auto* v : {&s->ev, &s->kr}) {
+        for (auto it = v->begin(); it != v->end(); ++it) {
+            if ((*it)->id != id) continue;
+            v->erase(it);
+            s->dirty = s->dirty_k = true;
+            break;
+        }
+    }
     if (drop(s->active, true) || drop(s->finished, false)) return RAS_OK;
     return sfail(s, RAS_EINVAL, "no request with this id");
 }
 
 size_t ras_server_device_bytes(const ras_server* s) {
     if (!s) return 0;
-    return (s->ws ? s->ws->bytes : 0) + s->slot_held;
+    return (s->ws ? s->ws->bytes : 0) + (s->wk ? s->wk->bytes : 0) + s->slot_held;
 }
 
 const char* ras_server_last_error(const ras_server* s) {
@@ -1969,7 +2040,12 @@ void ras_server_destroy(ras_server* s) {
     }
     for (auto* r : s->pending) delete r;
     if (s->ws) ras_destroy(s->ws);
+    if (s->wk) ras_destroy(s->wk);
     cudaStreamSynchronize(s->st);
+    if (s->st2) {
+        cudaStreamSynchronize(s->st2);
+        cudaStreamDestroy(s->st2);
+    }
     delete s;
 }
 

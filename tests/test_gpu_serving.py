@@ -105,7 +105,7 @@ def test_budget_limits_admission(alone):
     memory, the held bytes stay within the budget, every request finishes."""
     cfgs = _cfgs()
     opts = gpu_opts(cfgs[0], ras.RAS_MIXED)
-    need = [sum(ras.ras_server_request_bytes(_req(c), opts)) for c in cfgs]
+    need = [a + 2 * b for a, b in (ras.ras_server_request_bytes(_req(c), opts) for c in cfgs)]
     budget = int(sorted(need)[-1] + sorted(need)[-2] + 1)
     s = ras.ras_server_create(budget, 16, opts)
     try:
