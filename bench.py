@@ -77,11 +77,12 @@ def traffic_for(kind, workload):
     return t["bytes_per_launch"]
 
 
-def measure_batch(ras, torch, dev, stream):
+def measure_batch(ras, torch, dev, stream, autotune=True):
     """Uneven batch (64 independent problems, seed 4): one batched RASPEN solve
-    in mixed precision, timed with CUDA events after one warm-up solve, and
-    the same problems solved one after another in their own handles; the
-    results of the two agree to the mixed tolerance (reported)."""
+    in mixed precision (launch shapes autotuned on the batch first), timed
+    with CUDA events after one warm-up solve, and the same problems solved one
+    after another in their own handles (default launch shapes); the results
+    of the two agree to the mixed tolerance (reported)."""
     import numpy as np
     from paper_2411_00546_gb300 import inputs
     cfgs = inputs.uneven_batch()
@@ -91,6 +92,7 @@ def measure_batch(ras, torch, dev, stream):
     probs = [dict(n=c["n"], sx=c["sx"], sy=c["sy"], overlap=c["overlap"], phi=c["phi"], nu=c["nu"], mu=c["mu"],
                   y_d=yd) for c, yd in zip(cfgs, yds)]
     h = ras.ras_batch_create(probs, o, stream=stream.cuda_stream)
+    tuned = ras.ras_autotune(h)[0].as_dict() if autotune else None
     ys = [torch.zeros((c["n"], c["n"]), dtype=torch.float64, device=dev) for c in cfgs]
     ps = [torch.zeros_like(y) for y in ys]
 
@@ -132,7 +134,7 @@ def measure_batch(ras, torch, dev, stream):
             "problems_per_s": len(cfgs) / (ms / 1e3), "ms": ms, "status": rc,
             "outer_its_max": max(x.outer_its for x in st), "device_bytes": bytes_,
             "sequential_problems_per_s": len(cfgs) / (seq_ms / 1e3), "sequential_ms": seq_ms,
-            "max_err_batched_vs_alone": err}
+            "max_err_batched_vs_alone": err, "autotune": tuned}
 
 
 def measure_serving(ras, torch, dev, stream, count):
@@ -251,6 +253,7 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-methods", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)
     return ap.parse_args()
 
@@ -416,7 +419,16 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    def tune(hh):
+        """Launch shapes timed on the handle's own subdomains (setup, not timed)."""
+        if args.no_autotune:
+            return None
+        t0 = time.perf_counter()
+        t, rep = ras.ras_autotune(hh)
+        return {"chosen": t.as_dict(), "s": round(time.perf_counter() - t0, 3), "timed": rep.as_dict()}
+
     h = make(ras.RAS_MIXED)
+    autotune = tune(h)
     y = torch.zeros((n, n), dtype=torch.float64, device=dev)
     p = torch.zeros_like(y)
 
@@ -457,6 +469,7 @@ def main():
     fp64 = None
     if not args.no_fp64:
         h64 = make(ras.RAS_FP64)
+        tune64 = tune(h64)
         y64 = torch.zeros_like(y)
         p64 = torch.zeros_like(y)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -470,7 +483,8 @@ def main():
                 "outer_its": st64.outer_its, "gmres_its": st64.gmres_its,
                 "err_mixed_vs_fp64_y": field_err(y_mixed, y64n, p64n),
                 "err_mixed_vs_fp64_p": field_err(p_mixed, p64n, y64n),
-                "err_rule": "max|a-b| / max(max|b|, 1e-2 * joint scale of (y, p))"}
+                "err_rule": "max|a-b| / max(max|b|, 1e-2 * joint scale of (y, p))",
+                "autotune": tune64["chosen"] if tune64 else None}
         ras.ras_destroy(h64)
 
     # end to end through the host-buffer entry point (pinned host memory)
@@ -587,7 +601,7 @@ def main():
     # one GPU: rank 0 runs them (replicas would only repeat them)
     batch = None
     if rank == 0 and not args.no_batch:
-        batch = measure_batch(ras, torch, dev, stream)
+        batch = measure_batch(ras, torch, dev, stream, autotune=not args.no_autotune)
     serving = None
     if rank == 0 and not args.no_serve:
         serving = measure_serving(ras, torch, dev, stream, args.serve_requests)
@@ -629,6 +643,7 @@ def main():
                           "solve_stats": stats[-1], "fp64": fp64, "kernel_share": kernel_share,
                           "kernels": kernels, "kernel_rooflines": kernel_rooflines,
                           "uneven_batch": batch, "serving": serving, "methods": methods,
+                          "autotune": autotune,
                           "y_max": float(np.abs(y_mixed).max()),
                           "p_max": float(np.abs(p_mixed).max())},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

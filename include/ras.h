@@ -352,6 +352,77 @@ long long ras_launch_count(void);
 int ras_profile(ras_problem* h, int enable);
 int ras_profile_read(ras_problem* h, int kind, double* ms, long long* launches, double* work);
 
+/* Launch-shape tuning (not part of the paper's method: how the kernels are
+ * shaped on this device, never what they compute beyond rounding order).
+ * ras_tuning holds the three launch shapes a handle uses:
+ *   factor_wide_max[c]  register-tile class c (padded block size
+ *                       mp = 32 (c + 1): 32, 64, 96, 128, 160): the FP32
+ *                       factorisation of the class runs one 1024-thread CTA
+ *                       per subdomain when at most this many of its
+ *                       subdomains factorise in a sweep, else one 256-thread
+ *                       CTA per subdomain. -1 (default): the SM count (the
+ *                       1024-thread kernel when the sweep fits one wave).
+ *                       The two kernels sweep pivot panels of mp/32 and
+ *                       mp/16 columns, so their factors agree to FP32
+ *                       rounding, not bit for bit.
+ *   solve_ctas_per_sm   CTAs per SM of the persistent local-solve kernels
+ *                       (direction, Jacobian action, linear RAS); 0
+ *                       (default): as many as fit. Results are identical
+ *                       (one CTA computes each subdomain whatever the grid).
+ *   vec_blocks          CTAs of the segmented vector kernels (GMRES dot
+ *                       products, AXPYs), 1..RAS_VEC_BLOCKS_MAX (default
+ *                       RAS_VEC_BLOCKS_MAX). This fixes the summation order
+ *                       of every inner product, so results can differ in
+ *                       the last bits between two settings; one setting
+ *                       always gives the same result.
+ * ras_autotune times the candidates with CUDA events on the handle's stream,
+ * on the handle's own subdomains (all problems of a batch), and installs the
+ * fastest (a candidate replaces the default only when at least 2% faster):
+ *   factor   per class with subdomains, both kernels at the class's counts
+ *            1, 8, 38, 76, 152, 304 (those below its subdomain count) and
+ *            its subdomain count, factorising the Jacobians at x = 0,
+ *            eps = eps0. At each count the default rule's kernel is kept
+ *            unless the other is 2% faster; if that changes the kernel at
+ *            any count, factor_wide_max[c] becomes the largest count up to
+ *            which the 1024-thread kernel is kept at every timed count (0
+ *            if not even at 1), else it stays -1. FP64 handles keep -1 (one
+ *            FP64 kernel).
+ *   solve    every CTAs-per-SM value up to the number that fits, timing one
+ *            linear RAS application (ras_precondition's local solves) with
+ *            every subdomain factorised.
+ *   vectors  vec_blocks in {152, 304, 456, 608} (multiples of 152, at most
+ *            RAS_VEC_BLOCKS_MAX), timing one CGS step of a 16-vector basis
+ *            (segmented dot products, reduction, AXPY).
+ * It overwrites the handle's internal iterate and local factorisations (a
+ * following ras_jvp returns RAS_ESTATE until the next ras_apply); solve
+ * results, the caller's buffers and the checkpoint state are untouched.
+ * Call it between solves. Takes milliseconds to about a second. `chosen`
+ * (may be NULL) receives the installed tuning, `report` (may be NULL) the
+ * timings: per launch, in ms; entries after the last timed one are 0.
+ * ras_get_tuning / ras_set_tuning read and install a tuning (for example one
+ * saved from an earlier ras_autotune of the same shapes); RAS_EINVAL for
+ * factor_wide_max[c] < -1, solve_ctas_per_sm < 0 or > 64, or vec_blocks
+ * outside 1..RAS_VEC_BLOCKS_MAX. */
+#define RAS_NTILE          5
+#define RAS_TUNE_MAX       8
+#define RAS_VEC_BLOCKS_MAX 608
+typedef struct {
+    int factor_wide_max[RAS_NTILE];
+    int solve_ctas_per_sm;
+    int vec_blocks;
+} ras_tuning;
+typedef struct {
+    int factor_count[RAS_NTILE][RAS_TUNE_MAX];      /* subdomains factorised   */
+    double factor_ms[RAS_NTILE][RAS_TUNE_MAX][2];   /* [256, 1024 threads]     */
+    int solve_ctas_per_sm[RAS_TUNE_MAX];
+    double solve_ms[RAS_TUNE_MAX];
+    int vec_blocks[RAS_TUNE_MAX];
+    double vec_ms[RAS_TUNE_MAX];
+} ras_tune_report;
+int ras_autotune(ras_problem* h, ras_tuning* chosen, ras_tune_report* report);
+int ras_get_tuning(const ras_problem* h, ras_tuning* t);
+int ras_set_tuning(ras_problem* h, const ras_tuning* t);
+
 /* Residual without a handle and without any device allocation.
  * The paper has no counterpart: this entry point serves callers that cannot
  * call cudaMalloc or cudaFree, e.g. code running while another allocator (a

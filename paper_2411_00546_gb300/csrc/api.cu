@@ -73,6 +73,7 @@ struct ras_problem {
     double* coefG = nullptr;
     double* partials = nullptr;
     int nbp = 0;                 // blocks per problem of the segmented kernels
+    ras_tuning tune{{-1, -1, -1, -1, -1}, 0, ras::VEC_BLOCKS};   // launch shapes (ras_autotune)
     int sms = 0;                 // SMs of the device (0 until queried)
     bool own_factors = true;     // factors and coefficients in gpool / coef (else per subdomain pointers)
     ras_state last_state{};      // state at the end of the last outer solve (checkpoint)
@@ -122,6 +123,8 @@ struct Range {
     ~Range() { nvtxRangePop(); }
 };
 constexpr int NTILE = 5;              // register tiles 2, 4, 6, 8, 10
+static_assert(NTILE == RAS_NTILE, "tile classes of the header");
+static_assert(ras::VEC_BLOCKS == RAS_VEC_BLOCKS_MAX, "vector-kernel grid of the header");
 
 int fail(ras_problem* h, int code, const std::string& msg) {
     if (h) h->err = msg;
@@ -326,7 +329,7 @@ long long plane(const ras_problem* h, int p) { return (long long)h->probs[p].n *
 
 double resid_bytes(const ras_problem* h) { return (h->f ? 48.0 : 40.0) * (double)plane(h, 0); }
 
-// Block table of row `row`: VEC_BLOCKS blocks spread over the problems with
+// Block table of row `row`: tune.vec_blocks blocks spread over the problems with
 // m[p] != 0 in proportion to their segment lengths (at least one each, and
 // no more than one per 512 elements).
 int build_grid(ras_problem* h, int row, const std::vector<int>& m) {
@@ -341,8 +344,9 @@ int build_grid(ras_problem* h, int row, const std::vector<int>& m) {
         if (!m[p]) continue;
         const double len = (double)h->segs[p].len;
         const int most = (int)std::max(1.0, std::ceil(len / 512.0));
-        int nb = (int)std::floor(ras::VEC_BLOCKS * len / tot + 0.5);
-        nb = std::max(1, std::min(nb, std::min(most, (int)ras::VEC_BLOCKS)));
+        const int vb = h->tune.vec_blocks;
+        int nb = (int)std::floor(vb * len / tot + 0.5);
+        nb = std::max(1, std::min(nb, std::min(most, vb)));
         nbps[p] = nb;
         for (int b = 0; b < nb; ++b) tab.push_back(make_int2(p, b));
     }
@@ -426,7 +430,8 @@ void stats_clear(ras_stats* s, int count) {
 // Factorisation launches: FP32 one per register-tile class, FP64 one.
 template <typename T>
 // nwork: most subdomains that factorise in this sweep (the active count, or
-// every subdomain); with at most one per SM the 1024-thread kernel is used.
+// every subdomain); up to tune.factor_wide_max of a class (default: one per
+// SM) the 1024-thread kernel is used.
 int launch_factor(ras_problem* h, int only_active, double flops, int nwork) {
     if (sizeof(T) == sizeof(float)) {
         if (h->sms == 0) {
@@ -437,7 +442,8 @@ int launch_factor(ras_problem* h, int only_active, double flops, int nwork) {
         bool first = true;   // the profile books the flops on the first launch of the sweep
         for (int c = 0; c < NTILE; ++c) {
             if (h->tile_cnt[c] == 0) continue;
-            const int wide = std::min(nwork, h->tile_cnt[c]) <= h->sms ? 1 : 0;
+            const int thr = h->tune.factor_wide_max[c] < 0 ? h->sms : h->tune.factor_wide_max[c];
+            const int wide = std::min(nwork, h->tile_cnt[c]) <= thr ? 1 : 0;
             CK(timed(h, RAS_K_FACTOR, first ? flops : 0.0, [&] {
                 return ras::launch_local_factor_f32(h->st, 2 * (c + 1), h->tile_cnt[c], h->d_lists + h->tile_off[c],
                                                     h->d_subs, h->d_probs, h->X, h->ls, h->cpool, h->coef,
@@ -486,7 +492,7 @@ int ras_apply_T(ras_problem* h, const std::vector<double>& pstart, double* Fout,
         }
         TRY(launch_factor<T>(h, 1, fl, *h->h_active));
         CK(timed(h, RAS_K_DIRECTION, 0.0, [&] {
-            return ras::launch_local_direction<T>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs, h->ls, np,
+            return ras::launch_local_direction<T>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs, h->ls, np,
                                                   h->coef, gp, h->Kpool, h->dpool, h->rpool, wp, h->d_err,
                                                   h->d_order, h->d_ticket);
         }));
@@ -572,10 +578,10 @@ int jvp_internal(ras_problem* h, const double* D, double* O, const std::vector<i
     const int* dm = mask ? h->d_mask : nullptr;
     CK(timed(h, RAS_K_JVP, solve_bytes(h, mask) * (1 + nir), [&] {
         if (h->o.precision == RAS_MIXED)
-            return ras::launch_local_jvp<float>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs,
+            return ras::launch_local_jvp<float>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs,
                                                 (const float*)h->gpool, (float*)h->wpool, h->coef, h->dpool,
                                                 h->rpool, h->Ktpool, nir, D, O, dm, h->d_err, h->d_order, h->d_ticket);
-        return ras::launch_local_jvp<double>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs,
+        return ras::launch_local_jvp<double>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs,
                                              (const double*)h->gpool, (double*)h->wpool, h->coef, h->dpool,
                                              h->rpool, h->Ktpool, 0, D, O, dm, h->d_err, h->d_order, h->d_ticket);
     }));
@@ -609,10 +615,10 @@ int factor_at(ras_problem* h, double eps) {
 int precond_internal(ras_problem* h, const double* R, double* Zo) {
     CK(timed(h, RAS_K_PRECOND, solve_bytes(h, nullptr), [&] {
         if (h->o.precision == RAS_MIXED)
-            return ras::launch_local_precond<float>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs,
+            return ras::launch_local_precond<float>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs,
                                                     (const float*)h->gpool, (float*)h->wpool, R, Zo, h->d_err,
                                                     h->d_order, h->d_ticket);
-        return ras::launch_local_precond<double>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs,
+        return ras::launch_local_precond<double>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs,
                                                  (const double*)h->gpool, (double*)h->wpool, R, Zo, h->d_err,
                                                  h->d_order, h->d_ticket);
     }));
@@ -1018,6 +1024,202 @@ int newton_internal(ras_problem* h, ras_stats* s, bool prec) {
 }
 
 int newton_ras_internal(ras_problem* h, ras_stats* s) { return newton_internal(h, s, true); }
+
+// ------------------------------------------------------------ launch shapes
+// Rebuild the block tables of the segmented kernels for the current
+// tune.vec_blocks, each row for the problems it was last built for.
+int rebuild_grids(ras_problem* h) {
+    for (int row = 0; row < 3; ++row) {
+        if (h->last_mask[row].empty()) continue;
+        const std::vector<int> m = h->last_mask[row];
+        h->last_mask[row].clear();
+        TRY(build_grid(h, row, m));
+    }
+    return RAS_OK;
+}
+
+// Mean device time (ms) of one fn() over `reps` calls after one untimed call,
+// from CUDA events on the handle's stream.
+template <class Fn>
+int time_launches(ras_problem* h, int reps, Fn fn, double& ms) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    cudaError_t e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = fn();
+    if (e == cudaSuccess) e = cudaEventRecord(a, h->st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = fn();
+    if (e == cudaSuccess) e = cudaEventRecord(b, h->st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    CK(e);
+    ms = (double)t / reps;
+    return RAS_OK;
+}
+
+// Index of the candidate to install: the default `d` unless another one is
+// at least 2% faster (timing noise does not flip a choice).
+int pick_faster(const std::vector<double>& ms, int d) {
+    int best = d;
+    for (int i = 0; i < (int)ms.size(); ++i)
+        if (ms[i] < ms[best]) best = i;
+    return ms[best] <= 0.98 * ms[d] ? best : d;
+}
+
+// FP32 factorisation: per tile class, both kernels at a ladder of subdomain
+// counts (a prefix of the class's list, every listed subdomain factorised).
+int tune_factor(ras_problem* h, ras_tune_report* rep, int* wide_max) {
+    static const int ladder[] = {1, 8, 38, 76, 152, 304};
+    for (int c = 0; c < NTILE; ++c) {
+        wide_max[c] = -1;
+        const int cnt = h->tile_cnt[c];
+        if (cnt == 0) continue;
+        std::vector<int> ks;
+        for (int k : ladder)
+            if (k < cnt) ks.push_back(k);
+        ks.push_back(cnt);
+        bool differs = false, run = true;
+        int thr = 0;
+        for (size_t i = 0; i < ks.size(); ++i) {
+            std::vector<double> t(2, 0.0);
+            for (int w = 0; w < 2; ++w) {
+                TRY(time_launches(h, 3, [&] {
+                    return ras::launch_local_factor_f32(h->st, 2 * (c + 1), ks[i], h->d_lists + h->tile_off[c],
+                                                        h->d_subs, h->d_probs, h->X, h->ls, h->cpool, h->coef,
+                                                        (float*)h->gpool, 0, w);
+                }, t[w]));
+            }
+            rep->factor_count[c][i] = ks[i];
+            rep->factor_ms[c][i][0] = t[0];
+            rep->factor_ms[c][i][1] = t[1];
+            const int def = ks[i] <= h->sms ? 1 : 0;      // the default rule's kernel
+            const int use = pick_faster(t, def);
+            differs = differs || use != def;
+            if (run && use == 1) thr = ks[i];
+            else run = false;
+        }
+        if (differs) wide_max[c] = thr;
+    }
+    return RAS_OK;
+}
+
+// Persistent local-solve kernels: one linear RAS application per CTAs-per-SM
+// value that gives a different grid.
+int tune_solve(ras_problem* h, ras_tune_report* rep, int& chosen) {
+    const bool f32 = h->o.precision == RAS_MIXED;
+    int fit = 0;
+    CK(ras::solve_ctas_per_sm_max(f32, &fit));
+    fit = std::max(1, std::min(fit, RAS_TUNE_MAX));
+    std::vector<int> vals;
+    std::vector<double> ms;
+    int last_grid = -1;
+    for (int c = 1; c <= fit; ++c) {
+        const int grid = std::min(h->nsub, c * h->sms);
+        if (grid == last_grid) break;                  // more CTAs than subdomains: same launch
+        last_grid = grid;
+        double t = 0.0;
+        TRY(time_launches(h, 3, [&] {
+            if (f32)
+                return ras::launch_local_precond<float>(h->st, h->nsub, c, h->d_subs, h->d_probs,
+                                                        (const float*)h->gpool, (float*)h->wpool, h->X, h->T1,
+                                                        h->d_err, h->d_order, h->d_ticket);
+            return ras::launch_local_precond<double>(h->st, h->nsub, c, h->d_subs, h->d_probs,
+                                                     (const double*)h->gpool, (double*)h->wpool, h->X, h->T1,
+                                                     h->d_err, h->d_order, h->d_ticket);
+        }, t));
+        TRY(check_err(h));
+        rep->solve_ctas_per_sm[vals.size()] = c;
+        rep->solve_ms[vals.size()] = t;
+        vals.push_back(c);
+        ms.push_back(t);
+    }
+    const int k = pick_faster(ms, (int)ms.size() - 1);  // default: as many as fit = the last grid
+    chosen = k == (int)ms.size() - 1 ? 0 : vals[k];
+    return RAS_OK;
+}
+
+// Segmented vector kernels: one CGS step (dot products against a 16-vector
+// basis, their reduction, the AXPY) per block count, every problem taking part.
+int tune_vectors(ras_problem* h, ras_tune_report* rep, int& chosen) {
+    const int P = h->nprob, m = h->o.gmres_restart;
+    const long long L = h->L;
+    TRY(ensure(h, &h->V, (size_t)(m + 1) * L));
+    h->Vm = m;
+    const int nv = std::min(16, m);
+    double* w = h->V + (long long)nv * L;
+    CK(cudaMemsetAsync(h->V, 0, (size_t)(nv + 1) * L * sizeof(double), h->st));
+    const int saved = h->tune.vec_blocks;
+    std::vector<int> vals;
+    std::vector<double> ms;
+    int def = 0;
+    for (int vb = 152; vb <= ras::VEC_BLOCKS; vb += 152) {
+        h->tune.vec_blocks = vb;
+        h->last_mask[0].clear();
+        TRY(set_mask(h, 0, std::vector<int>(P, 1)));
+        double t = 0.0;
+        TRY(time_launches(h, 5, [&] {
+            cudaError_t e = ras::launch_seg_dot(h->st, seg_grid(h, 0), h->d_segs, h->V, L, nv, w, h->partials);
+            if (e == cudaSuccess) e = ras::launch_seg_reduce(h->st, P, seg_grid(h, 0).nbps, nv, h->partials, h->scal);
+            if (e == cudaSuccess)
+                e = ras::launch_seg_axpy(h->st, seg_grid(h, 0), h->d_segs, h->V, L, nv, h->scal, -1.0, w);
+            return e;
+        }, t));
+        if (vb == ras::VEC_BLOCKS) def = (int)vals.size();
+        rep->vec_blocks[vals.size()] = vb;
+        rep->vec_ms[vals.size()] = t;
+        vals.push_back(vb);
+        ms.push_back(t);
+    }
+    h->tune.vec_blocks = saved;
+    chosen = vals[pick_faster(ms, def)];
+    return RAS_OK;
+}
+
+int validate_tuning(ras_problem* h, const ras_tuning& t) {
+    for (int c = 0; c < NTILE; ++c)
+        if (t.factor_wide_max[c] < -1) return fail(h, RAS_EINVAL, "factor_wide_max below -1");
+    if (t.solve_ctas_per_sm < 0 || t.solve_ctas_per_sm > 64)
+        return fail(h, RAS_EINVAL, "solve_ctas_per_sm outside 0..64");
+    if (t.vec_blocks < 1 || t.vec_blocks > ras::VEC_BLOCKS)
+        return fail(h, RAS_EINVAL, "vec_blocks outside 1..RAS_VEC_BLOCKS_MAX");
+    return RAS_OK;
+}
+
+int install_tuning(ras_problem* h, const ras_tuning& t) {
+    TRY(validate_tuning(h, t));
+    h->tune = t;
+    TRY(rebuild_grids(h));
+    return sync(h);
+}
+
+int autotune_internal(ras_problem* h, ras_tuning* chosen, ras_tune_report* rep) {
+    Range range("ras: autotune");
+    ras_tune_report local{};
+    if (!rep) rep = &local;
+    std::memset(rep, 0, sizeof(*rep));
+    if (h->sms == 0) {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const bool prof = h->prof_on;
+    h->prof_on = false;
+    ras_tuning t = h->tune;
+    // every subdomain factorised at x = 0, eps = eps0 (the start of a solve)
+    CK(cudaMemsetAsync(h->X, 0, (size_t)h->L * sizeof(double), h->st));
+    int rc = factor_at(h, h->o.eps0);
+    if (rc >= 0 && h->o.precision == RAS_MIXED) rc = tune_factor(h, rep, t.factor_wide_max);
+    if (rc >= 0) rc = tune_solve(h, rep, t.solve_ctas_per_sm);
+    if (rc >= 0) rc = tune_vectors(h, rep, t.vec_blocks);
+    h->prof_on = prof;
+    h->jvp_ready = false;
+    TRY(rc);
+    TRY(install_tuning(h, t));
+    if (chosen) *chosen = h->tune;
+    return RAS_OK;
+}
 
 int need_single(ras_problem* h) {
     if (h->nprob != 1) return fail(h, RAS_EINVAL, "this entry point takes a single-problem handle");
@@ -1440,6 +1642,22 @@ int ras_set_state(ras_problem* h, const ras_state* st) {
     h->resume = *st;
     h->have_resume = true;
     return RAS_OK;
+}
+
+int ras_autotune(ras_problem* h, ras_tuning* chosen, ras_tune_report* report) {
+    if (!h) return RAS_EINVAL;
+    return autotune_internal(h, chosen, report);
+}
+
+int ras_get_tuning(const ras_problem* h, ras_tuning* t) {
+    if (!h || !t) return RAS_EINVAL;
+    *t = h->tune;
+    return RAS_OK;
+}
+
+int ras_set_tuning(ras_problem* h, const ras_tuning* t) {
+    if (!h || !t) return RAS_EINVAL;
+    return install_tuning(h, *t);
 }
 
 int ras_solve_host(ras_problem* h, int method, const double* y_d_host, double* y_host, double* p_host,

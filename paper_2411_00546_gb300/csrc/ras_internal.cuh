@@ -236,9 +236,10 @@ cudaError_t launch_local_factor(cudaStream_t st, int nsub, int maxm, const SubDe
 // The local-solve kernels (direction, Jacobian action, linear RAS) are
 // persistent: the grid holds as many CTAs as fit at once, and each takes the
 // next of the nsub positions of `order` (subdomain indices, largest factors
-// first) from *ticket, which the launcher zeroes on the stream.
+// first) from *ticket, which the launcher zeroes on the stream. ctas_per_sm
+// caps the CTAs per SM (0: as many as fit).
 template <typename T>
-cudaError_t launch_local_direction(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
+cudaError_t launch_local_direction(cudaStream_t st, int nsub, int ctas_per_sm, const SubDev* subs,
                                    const ProbDev* probs, LocalState* ls, NewtonParams np,
                                    const double* coef, const T* gpool, const double* Kpool,
                                    double* dpool, double* rpool, T* wpool, int* err, const int* order,
@@ -250,12 +251,13 @@ cudaError_t launch_local_linesearch(cudaStream_t st, int nsub, const SubDev* sub
 cudaError_t launch_local_prolong(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,
                                  const LocalState* ls, const double* cpool, double* F);
 template <typename T>
-cudaError_t launch_local_jvp(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
+cudaError_t launch_local_jvp(cudaStream_t st, int nsub, int ctas_per_sm, const SubDev* subs,
                              const ProbDev* probs, const T* gpool, T* wpool, const double* coef,
                              double* zpool, double* rpool, double* bpool, int nir, const double* D,
                              double* O, const int* pmask, int* err, const int* order, int* ticket);
 template <typename T>
-cudaError_t launch_local_precond(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
+cudaError_t launch_local_precond(cudaStream_t st, int nsub, int ctas_per_sm, const SubDev* subs,
                                  const ProbDev* probs, const T* gpool, T* wpool, const double* R,
                                  double* Z, int* err, const int* order, int* ticket);
+cudaError_t solve_ctas_per_sm_max(bool f32, int* per_sm);
 }  // namespace ras

@@ -480,30 +480,32 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 // Grid of a persistent solve kernel: as many CTAs as fit on the device at
 // once, at most one per subdomain; the ticket is zeroed on the stream first.
 template <class K>
-cudaError_t persistent_grid(K kernel, size_t smem, int nsub, cudaStream_t st, int* ticket, int& grid) {
+cudaError_t persistent_grid(K kernel, size_t smem, int nsub, int ctas_per_sm, cudaStream_t st, int* ticket,
+                            int& grid) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem);
     if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    grid = std::max(1, std::min(nsub, std::max(1, per_sm) * sms));
+    per_sm = std::max(1, per_sm);
+    if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
+    grid = std::max(1, std::min(nsub, per_sm * sms));
     return cudaSuccess;
 }
 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_local_direction(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
+cudaError_t launch_local_direction(cudaStream_t st, int nsub, int ctas_per_sm, const SubDev* subs,
                                    const ProbDev* probs, LocalState* ls, NewtonParams np,
                                    const double* coef, const T* gpool, const double* Kpool,
                                    double* dpool, double* rpool, T* wpool, int* err, const int* order,
                                    int* ticket) {
-    (void)maxm;
     const size_t sm = solve_smem<T>();
     cudaError_t e = set_smem(k_local_direction<T>, sm);
     int grid = 0;
-    if (e == cudaSuccess) e = persistent_grid(k_local_direction<T>, sm, nsub, st, ticket, grid);
+    if (e == cudaSuccess) e = persistent_grid(k_local_direction<T>, sm, nsub, ctas_per_sm, st, ticket, grid);
     if (e != cudaSuccess) return e;
     count_launch();
     k_local_direction<T><<<grid, NT, sm, st>>>(nsub, subs, probs, ls, np, coef, gpool, Kpool, dpool, rpool,
@@ -512,15 +514,14 @@ cudaError_t launch_local_direction(cudaStream_t st, int nsub, int maxm, const Su
 }
 
 template <typename T>
-cudaError_t launch_local_jvp(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
+cudaError_t launch_local_jvp(cudaStream_t st, int nsub, int ctas_per_sm, const SubDev* subs,
                              const ProbDev* probs, const T* gpool, T* wpool, const double* coef,
                              double* zpool, double* rpool, double* bpool, int nir, const double* D,
                              double* O, const int* pmask, int* err, const int* order, int* ticket) {
-    (void)maxm;
     const size_t sm = solve_smem<T>();
     cudaError_t e = set_smem(k_local_jvp<T>, sm);
     int grid = 0;
-    if (e == cudaSuccess) e = persistent_grid(k_local_jvp<T>, sm, nsub, st, ticket, grid);
+    if (e == cudaSuccess) e = persistent_grid(k_local_jvp<T>, sm, nsub, ctas_per_sm, st, ticket, grid);
     if (e != cudaSuccess) return e;
     count_launch();
     k_local_jvp<T><<<grid, NT, sm, st>>>(nsub, subs, probs, gpool, wpool, coef, zpool, rpool, bpool, nir, D, O,
@@ -529,18 +530,30 @@ cudaError_t launch_local_jvp(cudaStream_t st, int nsub, int maxm, const SubDev* 
 }
 
 template <typename T>
-cudaError_t launch_local_precond(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
+cudaError_t launch_local_precond(cudaStream_t st, int nsub, int ctas_per_sm, const SubDev* subs,
                                  const ProbDev* probs, const T* gpool, T* wpool, const double* R,
                                  double* Z, int* err, const int* order, int* ticket) {
-    (void)maxm;
     const size_t sm = solve_smem<T>();
     cudaError_t e = set_smem(k_local_precond<T>, sm);
     int grid = 0;
-    if (e == cudaSuccess) e = persistent_grid(k_local_precond<T>, sm, nsub, st, ticket, grid);
+    if (e == cudaSuccess) e = persistent_grid(k_local_precond<T>, sm, nsub, ctas_per_sm, st, ticket, grid);
     if (e != cudaSuccess) return e;
     count_launch();
     k_local_precond<T><<<grid, NT, sm, st>>>(nsub, subs, probs, gpool, wpool, R, Z, err, order, ticket);
     return cudaGetLastError();
+}
+
+// CTAs of the local-solve kernels that fit on one SM (FP32 or FP64 factors).
+cudaError_t solve_ctas_per_sm_max(bool f32, int* per_sm) {
+    *per_sm = 0;
+    if (f32) {
+        cudaError_t e = set_smem(k_local_precond<float>, solve_smem<float>());
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_precond<float>, NT, solve_smem<float>());
+    }
+    cudaError_t e = set_smem(k_local_precond<double>, solve_smem<double>());
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_precond<double>, NT, solve_smem<double>());
 }
 
 #define RAS_INSTANTIATE(T)                                                                              \

@@ -72,6 +72,40 @@ class ras_state(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+RAS_NTILE = 5
+RAS_TUNE_MAX = 8
+RAS_VEC_BLOCKS_MAX = 608
+
+
+class ras_tuning(ctypes.Structure):
+    _fields_ = [("factor_wide_max", ctypes.c_int * RAS_NTILE), ("solve_ctas_per_sm", ctypes.c_int),
+                ("vec_blocks", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"factor_wide_max": list(self.factor_wide_max), "solve_ctas_per_sm": self.solve_ctas_per_sm,
+                "vec_blocks": self.vec_blocks}
+
+
+class ras_tune_report(ctypes.Structure):
+    _fields_ = [("factor_count", (ctypes.c_int * RAS_TUNE_MAX) * RAS_NTILE),
+                ("factor_ms", ((ctypes.c_double * 2) * RAS_TUNE_MAX) * RAS_NTILE),
+                ("solve_ctas_per_sm", ctypes.c_int * RAS_TUNE_MAX), ("solve_ms", ctypes.c_double * RAS_TUNE_MAX),
+                ("vec_blocks", ctypes.c_int * RAS_TUNE_MAX), ("vec_ms", ctypes.c_double * RAS_TUNE_MAX)]
+
+    def as_dict(self):
+        """Timed candidates only (entries with a zero count are unused)."""
+        fac = {}
+        for c in range(RAS_NTILE):
+            rows = [(self.factor_count[c][i], self.factor_ms[c][i][0], self.factor_ms[c][i][1])
+                    for i in range(RAS_TUNE_MAX) if self.factor_count[c][i] > 0]
+            if rows:
+                fac[32 * (c + 1)] = rows
+        solve = [(self.solve_ctas_per_sm[i], self.solve_ms[i]) for i in range(RAS_TUNE_MAX)
+                 if self.solve_ctas_per_sm[i] > 0]
+        vec = [(self.vec_blocks[i], self.vec_ms[i]) for i in range(RAS_TUNE_MAX) if self.vec_blocks[i] > 0]
+        return {"factor": fac, "solve": solve, "vectors": vec}
+
+
 class RasError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("ras error %d: %s" % (code, msg))
@@ -100,6 +134,9 @@ _SIGS = {
     "ras_newton_solve": (_I, [_P, _P, _P, ctypes.POINTER(ras_stats)]),
     "ras_get_state": (_I, [_P, ctypes.POINTER(ras_state)]),
     "ras_set_state": (_I, [_P, ctypes.POINTER(ras_state)]),
+    "ras_autotune": (_I, [_P, ctypes.POINTER(ras_tuning), ctypes.POINTER(ras_tune_report)]),
+    "ras_get_tuning": (_I, [_P, ctypes.POINTER(ras_tuning)]),
+    "ras_set_tuning": (_I, [_P, ctypes.POINTER(ras_tuning)]),
     "ras_solve_host": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(ras_stats)]),
     "ras_local_iterations": (_I, [_P, ctypes.POINTER(_I), _I]),
     "ras_subdomain_count": (_I, [_P]),
@@ -322,6 +359,36 @@ def ras_get_state(h):
 
 def ras_set_state(h, st):
     return h._check(lib().ras_set_state(h.ptr, ctypes.byref(st)))
+
+
+def ras_autotune(h):
+    """Time the launch-shape candidates on h's subdomains and install the
+    fastest; returns (ras_tuning, ras_tune_report)."""
+    t, rep = ras_tuning(), ras_tune_report()
+    h._check(lib().ras_autotune(h.ptr, ctypes.byref(t), ctypes.byref(rep)))
+    return t, rep
+
+
+def ras_get_tuning(h):
+    t = ras_tuning()
+    h._check(lib().ras_get_tuning(h.ptr, ctypes.byref(t)))
+    return t
+
+
+def ras_set_tuning(h, t, check=True):
+    rc = lib().ras_set_tuning(h.ptr, ctypes.byref(t))
+    if check:
+        h._check(rc)
+    return rc
+
+
+def make_tuning(factor_wide_max=(-1,) * RAS_NTILE, solve_ctas_per_sm=0, vec_blocks=RAS_VEC_BLOCKS_MAX):
+    t = ras_tuning()
+    for c, v in enumerate(factor_wide_max):
+        t.factor_wide_max[c] = int(v)
+    t.solve_ctas_per_sm = int(solve_ctas_per_sm)
+    t.vec_blocks = int(vec_blocks)
+    return t
 
 
 def ras_solve_host(h, method, y_d_host, y_host, p_host, check=True):
