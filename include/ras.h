@@ -352,6 +352,19 @@ long long ras_launch_count(void);
 int ras_profile(ras_problem* h, int enable);
 int ras_profile_read(ras_problem* h, int kind, double* ms, long long* launches, double* work);
 
+/* CUDA-graph execution of the GMRES restart cycles (not part of the paper's
+ * method; default on). Every Arnoldi step (the operator, the CGS2 products,
+ * the Givens update of the Hessenberg column and the stop test) runs on the
+ * device; with graphs on, a whole cycle is one graph launch (one IF node per
+ * step, skipped once every problem has stopped) and the host reads the cycle
+ * once, instead of once per step. The graph of each operator is captured on
+ * first use and again after the handle's buffers, layout, options or tuning
+ * change. Both modes run the same kernels in the same order and give
+ * identical results. While ras_profile is on, cycles run step by step (the
+ * per-kernel events cannot sit inside a graph's conditional bodies).
+ * RAS_EINVAL on a NULL handle. */
+int ras_use_graphs(ras_problem* h, int enable);
+
 /* Launch-shape tuning (not part of the paper's method: how the kernels are
  * shaped on this device, never what they compute beyond rounding order).
  * ras_tuning holds the three launch shapes a handle uses:

@@ -27,7 +27,14 @@
 
 namespace ras {
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// While a thread captures a graph its launches are counted here instead (a
+// graph's kernels count when the graph runs).
+static thread_local long long* t_capture_count = nullptr;
+void count_launch() {
+    if (t_capture_count) ++*t_capture_count;
+    else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace ras
 
 using ras::LocalState;
@@ -84,8 +91,9 @@ struct ras_problem {
     int* d_ticket = nullptr;     // work counter of the persistent solve kernels
     // block tables of the segmented kernels, one per mask row (0: GMRES/JVP,
     // 1: outer loop, 2: every problem), VEC_BLOCKS + nprob entries each
-    int2* d_tab = nullptr;
-    int* d_nbps = nullptr;       // 3 rows of nprob block counts
+    int2* d_tab = nullptr;       // row 3: the GMRES cycle's table, built on the device from d_mask row 0
+    int* d_nbps = nullptr;       // 4 rows of nprob block counts
+    int* d_toff = nullptr;       // nprob + 1 ints: scratch of the device-built table
     int ntab[3] = {0, 0, 0};
     std::vector<int> last_mask[3];
     double* scal = nullptr;      // device scalars, 4 * 32 per problem
@@ -102,6 +110,23 @@ struct ras_problem {
     };
     bool prof_on = false;
     std::vector<ProfRec> prof_recs;
+    // GMRES restart cycles: per-problem Arnoldi state on the device, and one
+    // graph per operator kind with an IF node per Arnoldi step
+    double *gm_H = nullptr, *gm_cs = nullptr, *gm_sn = nullptr, *gm_g = nullptr, *gm_target = nullptr;
+    int *gm_its = nullptr, *gm_steps = nullptr, *gm_any = nullptr;
+    int* h_any = nullptr;            // pinned
+    bool use_graphs = true;
+    unsigned long long gen = 1;      // bumped whenever a buffer, the layout, the options or the tuning change
+    struct CycleGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long gen = 0;
+        const double* V = nullptr;
+        int m = 0;
+        std::vector<long long> kps;                 // kernels per step
+    };
+    CycleGraph cg[3];                // by operator: 0 Jacobian action of Alg. 4, 1 global Jacobian, 2 with RAS
+    cudaStream_t cap_st = nullptr;   // capture stream
     std::vector<cudaEvent_t> ev_pool;
     double prof_ms[RAS_K_COUNT] = {};
     long long prof_n[RAS_K_COUNT] = {};
@@ -194,11 +219,13 @@ int dalloc(ras_problem* h, T** p, size_t count) {
     }
     h->allocs.emplace_back((void*)*p, count * sizeof(T));
     h->bytes += count * sizeof(T);
+    ++h->gen;
     return RAS_OK;
 }
 
 void dfree(ras_problem* h, void* p) {
     if (!p) return;
+    ++h->gen;
     for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it) {
         if (it->first == p) {
             h->bytes -= it->second;
@@ -366,6 +393,26 @@ ras::SegGrid seg_grid(const ras_problem* h, int row) {
     g.nbps = h->d_nbps + row * h->nprob;
     g.nblocks = h->ntab[row];
     return g;
+}
+
+// The GMRES cycle's table (row 3): every entry launched, unused ones idle.
+ras::SegGrid cycle_grid(const ras_problem* h) {
+    ras::SegGrid g;
+    const int cap = ras::VEC_BLOCKS + h->nprob;
+    g.tab = h->d_tab + (size_t)3 * cap;
+    g.nbps = h->d_nbps + 3 * h->nprob;
+    g.nblocks = cap;
+    return g;
+}
+
+// Rebuild row 3 on the device for the problems flagged in d_mask row 0.
+int cycle_table(ras_problem* h) {
+    const int cap = ras::VEC_BLOCKS + h->nprob;
+    CK(timed(h, RAS_K_OTHER, 0.0, [&] {
+        return ras::launch_seg_table(h->st, h->nprob, h->d_mask, h->d_segs, h->tune.vec_blocks, cap,
+                                     h->d_tab + (size_t)3 * cap, h->d_nbps + 3 * h->nprob, h->d_toff);
+    }));
+    return RAS_OK;
 }
 
 int set_mask(ras_problem* h, int row, const std::vector<int>& m) {
@@ -644,19 +691,191 @@ struct GmresResume {
     std::vector<int> pending;
 };
 
+// Arnoldi step j of a GMRES(m) cycle for the problems flagged in d_mask row
+// 0 (the device flags that the Givens kernel clears): the operator
+// (w = A v_j, or A M v_j), two CGS passes against v_0 .. v_j, the norm, the
+// Givens update of the Hessenberg column and the stop test (device state
+// gm_*), and v_{j+1} = w / ||w||. Only enqueues work: nothing reads the host,
+// so the same sequence runs step by step or captured in a graph. The
+// segmented kernels use the cycle's table (row 3), which is rebuilt on the
+// device for the problems still iterating after every Givens update.
+template <class Aop, class Mop>
+int enqueue_step(ras_problem* h, int j, bool prec, Aop& A, Mop& M, const std::vector<int>& cyc, double seglen) {
+    const int P = h->nprob, m = h->o.gmres_restart;
+    const long long L = h->L;
+    double* V = h->V;
+    double* vj = V + (long long)j * L;
+    double* w = V + (long long)(j + 1) * L;
+    if (prec) {
+        TRY(M(vj, h->Z, cyc));
+        TRY(A(h->Z, w, cyc));
+    } else {
+        TRY(A(vj, w, cyc));
+    }
+    const ras::SegGrid gr = cycle_grid(h);
+    const double dbytes = 8.0 * seglen * (j + 2), abytes = 8.0 * seglen * (j + 3);
+    double* h1 = h->scal;
+    double* h2 = h->scal + (size_t)P * SS;
+    double* n2 = h->scal + (size_t)2 * P * SS;
+    CK(timed(h, RAS_K_KRYLOV, dbytes,
+             [&] { return ras::launch_seg_dot(h->st, gr, h->d_segs, V, L, j + 1, w, h->partials); }));
+    CK(timed(h, RAS_K_OTHER, 0.0, [&] { return ras::launch_seg_reduce(h->st, P, gr.nbps, j + 1, h->partials, h1); }));
+    CK(timed(h, RAS_K_KRYLOV, abytes,
+             [&] { return ras::launch_seg_axpy(h->st, gr, h->d_segs, V, L, j + 1, h1, -1.0, w); }));
+    CK(timed(h, RAS_K_KRYLOV, dbytes,
+             [&] { return ras::launch_seg_dot(h->st, gr, h->d_segs, V, L, j + 1, w, h->partials); }));
+    CK(timed(h, RAS_K_OTHER, 0.0, [&] { return ras::launch_seg_reduce(h->st, P, gr.nbps, j + 1, h->partials, h2); }));
+    CK(timed(h, RAS_K_KRYLOV, abytes,
+             [&] { return ras::launch_seg_axpy(h->st, gr, h->d_segs, V, L, j + 1, h2, -1.0, w); }));
+    CK(timed(h, RAS_K_KRYLOV, 8.0 * seglen,
+             [&] { return ras::launch_seg_dot(h->st, gr, h->d_segs, w, L, 1, w, h->partials); }));
+    CK(timed(h, RAS_K_OTHER, 0.0, [&] { return ras::launch_seg_reduce(h->st, P, gr.nbps, 1, h->partials, n2); }));
+    CK(timed(h, RAS_K_OTHER, 0.0, [&] {
+        return ras::launch_gmres_givens(h->st, P, m, j, h->d_mask, h1, h2, n2, h->gm_H, h->gm_cs, h->gm_sn, h->gm_g,
+                                        h->gm_its, h->gm_steps, h->gm_target, h->o.gmres_maxit, h->gm_any);
+    }));
+    TRY(cycle_table(h));
+    CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen,
+             [&] { return ras::launch_seg_scale(h->st, gr, h->d_segs, w, n2, 1.0, w); }));
+    return RAS_OK;
+}
+
+void destroy_cycle_graph(ras_problem::CycleGraph& G) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G = ras_problem::CycleGraph{};
+}
+
+// One GMRES(m) cycle as a graph: for j = 0 .. m-1 an IF node holding Arnoldi
+// step j (captured from enqueue_step), its condition set by a one-thread
+// kernel after step j-1 from the flag the Givens kernel leaves (step 0 always
+// runs). A cycle that stops after k steps runs k bodies and skips the rest.
+template <class Aop, class Mop>
+int build_cycle_graph(ras_problem* h, int op, bool prec, Aop& A, Mop& M, const std::vector<int>& cyc,
+                      double seglen) {
+    auto& G = h->cg[op];
+    destroy_cycle_graph(G);
+    const int m = h->o.gmres_restart;
+    if (!h->cap_st) CK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+    CK(cudaGraphCreate(&G.graph, 0));
+    std::vector<cudaGraphConditionalHandle> cond(m);
+    for (int j = 0; j < m; ++j)
+        CK(cudaGraphConditionalHandleCreate(&cond[j], G.graph, j == 0 ? 1u : 0u, cudaGraphCondAssignDefault));
+    G.kps.assign(m, 0);
+    cudaGraphNode_t prev = nullptr;
+    const cudaStream_t saved = h->st;
+    int rc = RAS_OK;
+    for (int j = 0; j < m && rc == RAS_OK; ++j) {
+        cudaError_t e = cudaSuccess;
+        if (j > 0) {
+            cudaGraphNode_t sc = nullptr;
+            e = ras::add_set_conditional_node(G.graph, prev, cond[j], h->gm_any, &sc);
+            prev = sc;
+        }
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond[j];
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&node, G.graph, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &cp);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(h->cap_st, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) {
+            rc = fail(h, RAS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            break;
+        }
+        long long count = 0;
+        h->st = h->cap_st;
+        ras::t_capture_count = &count;
+        rc = enqueue_step(h, j, prec, A, M, cyc, seglen);
+        ras::t_capture_count = nullptr;
+        h->st = saved;
+        cudaGraph_t body = nullptr;
+        e = cudaStreamEndCapture(h->cap_st, &body);
+        if (rc == RAS_OK && e != cudaSuccess)
+            rc = fail(h, RAS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        G.kps[j] = count;
+        prev = node;
+    }
+    if (rc == RAS_OK) {
+        const cudaError_t e = cudaGraphInstantiate(&G.exec, G.graph, 0);
+        if (e != cudaSuccess) rc = fail(h, RAS_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    cudaGetLastError();
+    if (rc != RAS_OK) {
+        destroy_cycle_graph(G);
+        return rc;
+    }
+    G.gen = h->gen;
+    G.V = h->V;
+    G.m = m;
+    return RAS_OK;
+}
+
+// Run the Arnoldi steps of one cycle (device state set up by the caller):
+// as one graph launch, or step by step with a read of the flag after each
+// (always so while profiling: per-kernel events cannot sit inside the
+// conditional bodies of a graph). *ran: the graph that ran, else nullptr.
+template <class Aop, class Mop>
+int run_cycle(ras_problem* h, int op, bool prec, Aop& A, Mop& M, const std::vector<int>& cyc, double seglen,
+              ras_problem::CycleGraph** ran) {
+    const int m = h->o.gmres_restart;
+    *ran = nullptr;
+    if (h->use_graphs && !h->prof_on) {
+        auto& G = h->cg[op];
+        if (!G.exec || G.gen != h->gen || G.V != h->V || G.m != m)
+            TRY(build_cycle_graph(h, op, prec, A, M, cyc, seglen));
+        CK(cudaGraphLaunch(G.exec, h->st));
+        *ran = &G;
+        return RAS_OK;
+    }
+    for (int j = 0; j < m; ++j) {
+        TRY(enqueue_step(h, j, prec, A, M, cyc, seglen));
+        CK(cudaMemcpyAsync(h->h_any, h->gm_any, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        TRY(sync(h));
+        if (!*h->h_any) break;
+    }
+    return RAS_OK;
+}
+
+// After a graph launch that ran `steps` Arnoldi steps: count its kernels.
+void account_graph(const ras_problem::CycleGraph& G, int steps) {
+    long long n = (long long)G.m - 1;   // condition kernels
+    for (int j = 0; j < steps; ++j) n += G.kps[j];
+    ras::add_launches(n);
+}
+
 // GMRES(m) (CGS2, Givens) for the problems with part[p], in lockstep, with
 // right preconditioning when prec. its: steps taken (cumulative when
-// resuming), conv: converged to rtol * ||b||.
+// resuming), conv: converged to rtol * ||b||. op: operator kind (the cycle
+// graph of each kind is kept on the handle).
 template <class Aop, class Mop>
-int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, const std::vector<int>& part,
+int gmres(ras_problem* h, int op, Aop A, Mop M, bool prec, const double* b, double* x, const std::vector<int>& part,
           std::vector<int>& its, std::vector<int>& conv, GmresResume* res = nullptr) {
     Range range("ras: GMRES");
     const int P = h->nprob, m = h->o.gmres_restart, maxit = h->o.gmres_maxit;
     const long long L = h->L;
     const double rtol = h->o.gmres_rtol;
+    const double* V_before = h->V;
     TRY(ensure(h, &h->V, (size_t)(m + 1) * L));
+    if (h->V != V_before)   // basis vectors past a problem's last step must stay finite
+        CK(cudaMemsetAsync(h->V, 0, (size_t)(m + 1) * L * sizeof(double), h->st));
     h->Vm = m;
     double* V = h->V;
+    TRY(ensure(h, &h->gm_H, (size_t)P * (m + 1) * m));
+    TRY(ensure(h, &h->gm_cs, (size_t)P * m));
+    TRY(ensure(h, &h->gm_sn, (size_t)P * m));
+    TRY(ensure(h, &h->gm_g, (size_t)P * (m + 1)));
+    TRY(ensure(h, &h->gm_target, (size_t)P));
+    TRY(ensure(h, &h->gm_its, (size_t)P));
+    TRY(ensure(h, &h->gm_steps, (size_t)P));
+    TRY(ensure(h, &h->gm_any, (size_t)1));
+    if (!h->h_any && cudaMallocHost((void**)&h->h_any, sizeof(int)) != cudaSuccess) {
+        h->h_any = nullptr;
+        return fail(h, RAS_ENOMEM, "pinned host allocation failed");
+    }
     double* r = h->T2;
     double* upd = h->T3;
     if (!res) its.assign(P, 0);
@@ -701,8 +920,7 @@ int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, c
             return ras::launch_seg_add_scaled(h->st, seg_grid(h, 0), h->d_segs, b, r, -1.0, r);
         }));
     }
-    std::vector<double> H((size_t)P * (m + 1) * m), cs((size_t)P * m), sn((size_t)P * m), g((size_t)P * (m + 1)),
-        y((size_t)P * SS, 0.0);
+    std::vector<double> H((size_t)P * (m + 1) * m), g((size_t)P * (m + 1)), y((size_t)P * SS, 0.0);
     for (int cycle = 0;; ++cycle) {
         // true residual norms of the problems still iterating
         TRY(set_mask(h, 0, act));
@@ -729,88 +947,25 @@ int gmres(ras_problem* h, Aop A, Mop M, bool prec, const double* b, double* x, c
         CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
             return ras::launch_seg_scale(h->st, seg_grid(h, 0), h->d_segs, r, h->scal, 1.0, V);
         }));
-        std::fill(H.begin(), H.end(), 0.0);
+        // device state of the cycle: g = beta e_1, step counters, targets
         std::fill(g.begin(), g.end(), 0.0);
         for (int p = 0; p < P; ++p) {
             g[(size_t)p * (m + 1)] = beta[p];
             steps[p] = 0;
         }
-        for (int j = 0; j < m; ++j) {
-            if (std::none_of(cyc.begin(), cyc.end(), [](int v) { return v != 0; })) break;
-            double* vj = V + (long long)j * L;
-            double* w = V + (long long)(j + 1) * L;
-            if (prec) {
-                TRY(M(vj, h->Z, cyc));
-                TRY(A(h->Z, w, cyc));
-            } else {
-                TRY(A(vj, w, cyc));
-            }
-            // CGS2: two passes of classical Gram-Schmidt, then the norm
-            const double dbytes = 8.0 * seglen * (j + 2), abytes = 8.0 * seglen * (j + 3);
-            double* h1 = h->scal;
-            double* h2 = h->scal + (size_t)P * SS;
-            double* n2 = h->scal + (size_t)2 * P * SS;
-            CK(timed(h, RAS_K_KRYLOV, dbytes, [&] {
-                return ras::launch_seg_dot(h->st, seg_grid(h, 0), h->d_segs, V, L, j + 1, w, h->partials);
-            }));
-            CK(timed(h, RAS_K_OTHER, 0.0,
-                     [&] { return ras::launch_seg_reduce(h->st, P, seg_grid(h, 0).nbps, j + 1, h->partials, h1); }));
-            CK(timed(h, RAS_K_KRYLOV, abytes, [&] {
-                return ras::launch_seg_axpy(h->st, seg_grid(h, 0), h->d_segs, V, L, j + 1, h1, -1.0, w);
-            }));
-            CK(timed(h, RAS_K_KRYLOV, dbytes, [&] {
-                return ras::launch_seg_dot(h->st, seg_grid(h, 0), h->d_segs, V, L, j + 1, w, h->partials);
-            }));
-            CK(timed(h, RAS_K_OTHER, 0.0,
-                     [&] { return ras::launch_seg_reduce(h->st, P, seg_grid(h, 0).nbps, j + 1, h->partials, h2); }));
-            CK(timed(h, RAS_K_KRYLOV, abytes, [&] {
-                return ras::launch_seg_axpy(h->st, seg_grid(h, 0), h->d_segs, V, L, j + 1, h2, -1.0, w);
-            }));
-            CK(timed(h, RAS_K_KRYLOV, 8.0 * seglen, [&] {
-                return ras::launch_seg_dot(h->st, seg_grid(h, 0), h->d_segs, w, L, 1, w, h->partials);
-            }));
-            CK(timed(h, RAS_K_OTHER, 0.0,
-                     [&] { return ras::launch_seg_reduce(h->st, P, seg_grid(h, 0).nbps, 1, h->partials, n2); }));
-            CK(cudaMemcpyAsync(h->h_scal, h->scal, (size_t)3 * P * SS * sizeof(double), cudaMemcpyDeviceToHost,
-                               h->st));
-            TRY(sync(h));
-            bool changed = false;
-            for (int p = 0; p < P; ++p) {
-                if (!cyc[p]) continue;
-                double* Hp = H.data() + (size_t)p * (m + 1) * m;
-                double* csp = cs.data() + (size_t)p * m;
-                double* snp = sn.data() + (size_t)p * m;
-                double* gp = g.data() + (size_t)p * (m + 1);
-                for (int i = 0; i <= j; ++i)
-                    Hp[i * m + j] = h->h_scal[p * SS + i] + h->h_scal[(size_t)P * SS + p * SS + i];
-                const double hn = std::sqrt(h->h_scal[(size_t)2 * P * SS + p * SS]);
-                Hp[(j + 1) * m + j] = hn;
-                for (int i = 0; i < j; ++i) {
-                    const double t = csp[i] * Hp[i * m + j] + snp[i] * Hp[(i + 1) * m + j];
-                    Hp[(i + 1) * m + j] = -snp[i] * Hp[i * m + j] + csp[i] * Hp[(i + 1) * m + j];
-                    Hp[i * m + j] = t;
-                }
-                const double den = std::hypot(Hp[j * m + j], Hp[(j + 1) * m + j]);
-                csp[j] = Hp[j * m + j] / den;
-                snp[j] = Hp[(j + 1) * m + j] / den;
-                Hp[j * m + j] = den;
-                Hp[(j + 1) * m + j] = 0.0;
-                gp[j + 1] = -snp[j] * gp[j];
-                gp[j] = csp[j] * gp[j];
-                its[p] += 1;
-                steps[p] = j + 1;
-                if (hn == 0.0 || std::fabs(gp[j + 1]) <= target[p] || its[p] >= maxit) {
-                    cyc[p] = 0;
-                    changed = true;
-                }
-            }
-            if (changed) TRY(set_mask(h, 0, cyc));
-            if (std::any_of(cyc.begin(), cyc.end(), [](int v) { return v != 0; })) {
-                CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
-                    return ras::launch_seg_scale(h->st, seg_grid(h, 0), h->d_segs, w, n2, 1.0, w);
-                }));
-            }
-        }
+        CK(cudaMemcpyAsync(h->gm_g, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice, h->st));
+        CK(cudaMemcpyAsync(h->gm_its, its.data(), (size_t)P * sizeof(int), cudaMemcpyHostToDevice, h->st));
+        CK(cudaMemcpyAsync(h->gm_target, target.data(), (size_t)P * sizeof(double), cudaMemcpyHostToDevice, h->st));
+        CK(cudaMemsetAsync(h->gm_steps, 0, (size_t)P * sizeof(int), h->st));
+        TRY(cycle_table(h));
+        ras_problem::CycleGraph* ran = nullptr;
+        TRY(run_cycle(h, op, prec, A, M, cyc, seglen, &ran));
+        CK(cudaMemcpyAsync(H.data(), h->gm_H, H.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(g.data(), h->gm_g, g.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(its.data(), h->gm_its, (size_t)P * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(steps.data(), h->gm_steps, (size_t)P * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        TRY(sync(h));
+        if (ran) account_graph(*ran, *std::max_element(steps.begin(), steps.end()));
         // x += M (V y) for the problems that took steps in this cycle
         int maxsteps = 0;
         std::vector<int> took(P, 0);
@@ -896,7 +1051,7 @@ int raspen_internal(ras_problem* h, ras_stats* s) {
         CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
             return ras::launch_seg_scale(h->st, seg_grid(h, 1), h->d_segs, h->F, nullptr, -1.0, h->T1);
         }));
-        TRY(gmres(h, A, M, false, h->T1, h->Dv, need, its, conv));
+        TRY(gmres(h, 0, A, M, false, h->T1, h->Dv, need, its, conv));
         CK(timed(h, RAS_K_KRYLOV, 24.0 * seglen, [&] {
             return ras::launch_seg_add_scaled(h->st, seg_grid(h, 1), h->d_segs, h->X, h->Dv, 1.0, h->X);
         }));
@@ -982,7 +1137,7 @@ int newton_internal(ras_problem* h, ras_stats* s, bool prec) {
         CK(timed(h, RAS_K_KRYLOV, 16.0 * seglen, [&] {
             return ras::launch_seg_scale(h->st, seg_grid(h, 2), h->d_segs, h->F, nullptr, -1.0, h->T1);
         }));
-        TRY(gmres(h, A, M, prec, h->T1, h->Dv, one, its, conv));
+        TRY(gmres(h, prec ? 2 : 1, A, M, prec, h->T1, h->Dv, one, its, conv));
         if (s) s->gmres_its += its[0];
         double alpha = 1.0, nt = 0.0, ft = 0.0;
         int hh = 0;
@@ -1190,6 +1345,7 @@ int validate_tuning(ras_problem* h, const ras_tuning& t) {
 int install_tuning(ras_problem* h, const ras_tuning& t) {
     TRY(validate_tuning(h, t));
     h->tune = t;
+    ++h->gen;
     TRY(rebuild_grids(h));
     return sync(h);
 }
@@ -1366,8 +1522,9 @@ int ensure_pools(ras_problem* h, bool own_data) {
         CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st));
     }
     TRY(ensure(h, &h->d_mask, 2 * count));
-    TRY(ensure(h, &h->d_tab, (size_t)3 * (ras::VEC_BLOCKS + count)));
-    TRY(ensure(h, &h->d_nbps, (size_t)3 * count));
+    TRY(ensure(h, &h->d_tab, (size_t)4 * (ras::VEC_BLOCKS + count)));
+    TRY(ensure(h, &h->d_nbps, (size_t)4 * count));
+    TRY(ensure(h, &h->d_toff, (size_t)count + 1));
     TRY(ensure(h, &h->d_pstart, count));
     for (double** q : {&h->X, &h->F, &h->Dv, &h->Ov, &h->T1, &h->T2, &h->T3, &h->Z}) TRY(ensure(h, q, h->L));
     if (count == 1) TRY(ensure(h, &h->coefG, 3 * nn_tot));
@@ -1405,6 +1562,7 @@ void fill_pointers(ras_problem* h) {
 }
 
 int upload_layout(ras_problem* h) {
+    ++h->gen;
     if (h->own_factors) fill_pointers(h);
     TRY(build_grid(h, 2, std::vector<int>(h->nprob, 1)));
     // solve order: largest factor (wy * mp^2) first, ties by index
@@ -1492,6 +1650,7 @@ int ras_set_opts(ras_problem* h, const ras_opts* o) {
     const bool kappa_changed = (o->kappa != h->o.kappa);
     h->o = *o;
     h->jvp_ready = false;
+    ++h->gen;
     TRY(alloc_factor_pools(h));
     if (h->own_factors) {
         fill_pointers(h);
@@ -1649,6 +1808,12 @@ int ras_autotune(ras_problem* h, ras_tuning* chosen, ras_tune_report* report) {
     return autotune_internal(h, chosen, report);
 }
 
+int ras_use_graphs(ras_problem* h, int enable) {
+    if (!h) return RAS_EINVAL;
+    h->use_graphs = enable != 0;
+    return RAS_OK;
+}
+
 int ras_get_tuning(const ras_problem* h, ras_tuning* t) {
     if (!h || !t) return RAS_EINVAL;
     *t = h->tune;
@@ -1704,6 +1869,9 @@ void ras_destroy(ras_problem* h) {
     if (!h) return;
     cudaStreamSynchronize(h->st);
     prof_flush(h);
+    for (auto& G : h->cg) destroy_cycle_graph(G);
+    if (h->cap_st) cudaStreamDestroy(h->cap_st);
+    if (h->h_any) cudaFreeHost(h->h_any);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     for (auto& a : h->allocs) cudaFree(a.first);
     h->allocs.clear();
@@ -1811,7 +1979,8 @@ int request_bytes(const ras_problem_desc& d, const ras_opts& o, size_t& slot, si
                (double)tmp.nsub * (sizeof(LocalState) + sizeof(SubDev) + 3 * sizeof(int)) +
                (8.0 + o.gmres_restart + 1.0) * tmp.L * sizeof(double) + 3.0 * (double)d.n * d.n * sizeof(double) +
                (double)SS * ras::VEC_BLOCKS * sizeof(double) + 4.0 * SS * sizeof(double) +
-               3.0 * (ras::VEC_BLOCKS + 1) * 2 * sizeof(int) + 256.0;
+               4.0 * (ras::VEC_BLOCKS + 1) * 2 * sizeof(int) + 8.0 * sizeof(int) +
+               ((o.gmres_restart + 1.0) * (o.gmres_restart + 3.0) + 1.0) * sizeof(double) + 256.0;
     scratch = (size_t)b;
     return RAS_OK;
 }
@@ -1974,7 +2143,7 @@ int server_krylov(ras_server* s, ras_problem* h, const std::vector<ras_server::R
         return jvp_internal(h, in, out, &mask);
     };
     auto M = [&](const double*, double*, const std::vector<int>&) { return RAS_OK; };
-    TRY(gmres(h, A, M, false, h->T1, h->Dv, all, its, conv, &rs));
+    TRY(gmres(h, 0, A, M, false, h->T1, h->Dv, all, its, conv, &rs));
     for (int p = 0; p < P; ++p) {
         auto* r = reqs[p];
         r->fresh = false;

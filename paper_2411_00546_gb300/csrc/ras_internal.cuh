@@ -199,6 +199,7 @@ constexpr int SEG_STRIDE = 32;
 // tab[b].y-th of nbps[problem] blocks (problems left out have nbps = 0). The
 // host spreads VEC_BLOCKS blocks over the taking-part problems in proportion
 // to their segment lengths; partial sums use the stride VEC_BLOCKS.
+// Entries with tab[b].x < 0 are unused (their blocks do nothing).
 struct SegGrid {
     const int2* tab;
     const int* nbps;
@@ -214,6 +215,30 @@ cudaError_t launch_seg_scale(cudaStream_t st, SegGrid g, const Seg* segs, const 
                              double sign, double* dst);
 cudaError_t launch_seg_add_scaled(cudaStream_t st, SegGrid g, const Seg* segs, const double* x, const double* d,
                                   double alpha, double* out);
+
+// Block table of the problems p with act[p] built on the device (one CTA):
+// the same split as the host's (vec_blocks blocks in proportion to the
+// segment lengths, at least one and at most one per 512 elements each), in
+// tab[0 .. cap) with unused entries (-1, 0), nbps[p] blocks per problem (0
+// for the others); offs: nprob + 1 ints of scratch.
+cudaError_t launch_seg_table(cudaStream_t st, int nprob, const int* act, const Seg* segs, int vec_blocks, int cap,
+                             int2* tab, int* nbps, int* offs);
+
+// Arnoldi step j of GMRES(m) for every problem p with act[p] (one CTA, one
+// thread per problem): column j of the Hessenberg matrix H_p from the CGS2
+// coefficients h1 + h2 ([problem][32]) and hn = sqrt(n2), the earlier Givens
+// rotations applied to it, the new rotation (cs, sn) and the rotated
+// right-hand side g_p; its[p] and steps[p] advance, and act[p] is cleared
+// when hn = 0, |g_p[j+1]| <= target[p] or its[p] >= maxit. *any: some problem
+// still iterates. Layouts: H [p][(m+1) m] row-major, cs/sn [p][m], g [p][m+1].
+cudaError_t launch_gmres_givens(cudaStream_t st, int nprob, int m, int j, int* act, const double* h1,
+                                const double* h2, const double* n2, double* H, double* cs, double* sn, double* g,
+                                int* its, int* steps, const double* target, int maxit, int* any);
+// Kernel node (in graph `g`, after `dep`) that sets conditional handle `c` to
+// (*any != 0).
+cudaError_t add_set_conditional_node(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle c,
+                                     const int* any, cudaGraphNode_t* out);
+void add_launches(long long n);   // kernels a graph launch ran (counted once at capture)
 
 // per-subdomain kernels: local.cu. X, F, D, O, R, Z are global vector bases
 // (problem k at ProbDev.ofs); pools are indexed by SubDev offsets.

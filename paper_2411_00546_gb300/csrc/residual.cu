@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(NT) k_seg_dot(SegGrid sg_, const Seg* __restri
     constexpr int P = pow2_ceil(NVC);   // values per lane, padded with zeros
     __shared__ double red[NT / 32][NVC];
     const int2 e = sg_.tab[blockIdx.x];
+    if (e.x < 0) return;
     const int pb = e.x, bi = e.y, nb = sg_.nbps[pb];
     const Seg sg = segs[pb];
     double acc[P];
@@ -269,6 +270,7 @@ __global__ void __launch_bounds__(NT) k_seg_axpy(SegGrid sg_, const Seg* __restr
                                                  const double* __restrict__ h, double sign, double* w) {
     __shared__ double hs[SEG_STRIDE];
     const int2 e = sg_.tab[blockIdx.x];
+    if (e.x < 0) return;
     const int pb = e.x, bi = e.y, nb = sg_.nbps[pb];
     if (threadIdx.x < nv) hs[threadIdx.x] = sign * h[pb * SEG_STRIDE + threadIdx.x];
     __syncthreads();
@@ -285,6 +287,7 @@ __global__ void __launch_bounds__(NT) k_seg_axpy(SegGrid sg_, const Seg* __restr
 __global__ void __launch_bounds__(NT) k_seg_scale(SegGrid sg_, const Seg* __restrict__ segs, const double* src,
                                                   const double* __restrict__ n2, double sign, double* dst) {
     const int2 e = sg_.tab[blockIdx.x];
+    if (e.x < 0) return;
     const int pb = e.x, bi = e.y, nb = sg_.nbps[pb];
     const double s = n2 ? sign / sqrt(n2[pb * SEG_STRIDE]) : sign;
     const Seg sg = segs[pb];
@@ -302,7 +305,114 @@ __global__ void __launch_bounds__(NT) k_seg_add_scaled(SegGrid sg_, const Seg* _
         out[sg.ofs + g] = fma(alpha, d[sg.ofs + g], x[sg.ofs + g]);
 }
 
+// One Arnoldi step's Hessenberg column, Givens rotation and stop test per
+// problem (see launch_gmres_givens); the same operations in the same order
+// as the textbook GMRES least-squares update.
+__global__ void __launch_bounds__(NT) k_gmres_givens(int nprob, int m, int j, int* act, const double* h1,
+                                                     const double* h2, const double* n2, double* H, double* cs,
+                                                     double* sn, double* g, int* its, int* steps,
+                                                     const double* target, int maxit, int* any_out) {
+    int any = 0;
+    for (int p = threadIdx.x; p < nprob; p += NT) {
+        if (!act[p]) continue;
+        double* Hp = H + (long long)p * (m + 1) * m;
+        double* csp = cs + (long long)p * m;
+        double* snp = sn + (long long)p * m;
+        double* gp = g + (long long)p * (m + 1);
+        for (int i = 0; i <= j; ++i) Hp[i * m + j] = h1[p * SEG_STRIDE + i] + h2[p * SEG_STRIDE + i];
+        const double hn = sqrt(n2[p * SEG_STRIDE]);
+        Hp[(j + 1) * m + j] = hn;
+        for (int i = 0; i < j; ++i) {
+            const double t = csp[i] * Hp[i * m + j] + snp[i] * Hp[(i + 1) * m + j];
+            Hp[(i + 1) * m + j] = -snp[i] * Hp[i * m + j] + csp[i] * Hp[(i + 1) * m + j];
+            Hp[i * m + j] = t;
+        }
+        const double den = hypot(Hp[j * m + j], Hp[(j + 1) * m + j]);
+        csp[j] = Hp[j * m + j] / den;
+        snp[j] = Hp[(j + 1) * m + j] / den;
+        Hp[j * m + j] = den;
+        Hp[(j + 1) * m + j] = 0.0;
+        gp[j + 1] = -snp[j] * gp[j];
+        gp[j] = csp[j] * gp[j];
+        its[p] += 1;
+        steps[p] = j + 1;
+        if (hn == 0.0 || fabs(gp[j + 1]) <= target[p] || its[p] >= maxit) act[p] = 0;
+        else any = 1;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) *any_out = any;
+}
+
+__global__ void __launch_bounds__(NT) k_seg_table(int nprob, const int* act, const Seg* segs, int vb, int cap,
+                                                  int2* tab, int* nbps, int* offs) {
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int p = 0; p < nprob; ++p)
+            if (act[p]) tot += (double)segs[p].len;
+        int o = 0;
+        for (int p = 0; p < nprob; ++p) {
+            int nb = 0;
+            if (act[p]) {
+                const double len = (double)segs[p].len;
+                const int most = (int)fmax(1.0, ceil(len / 512.0));
+                nb = (int)floor(vb * len / tot + 0.5);
+                nb = max(1, min(nb, min(most, vb)));
+            }
+            nbps[p] = nb;
+            offs[p] = o;
+            o += nb;
+        }
+        offs[nprob] = o;
+    }
+    __syncthreads();
+    const int used = offs[nprob];
+    for (int b = threadIdx.x; b < cap; b += NT) {
+        if (b >= used) {
+            tab[b] = make_int2(-1, 0);
+            continue;
+        }
+        int lo = 0, hi = nprob - 1;   // the problem p with offs[p] <= b < offs[p + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (offs[mid] <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        tab[b] = make_int2(lo, b - offs[lo]);
+    }
+}
+
+__global__ void k_set_conditional(cudaGraphConditionalHandle c, const int* any) {
+    cudaGraphSetConditional(c, *any ? 1u : 0u);
+}
+
 }  // namespace
+
+cudaError_t launch_seg_table(cudaStream_t st, int nprob, const int* act, const Seg* segs, int vec_blocks, int cap,
+                             int2* tab, int* nbps, int* offs) {
+    count_launch();
+    k_seg_table<<<1, NT, 0, st>>>(nprob, act, segs, vec_blocks, cap, tab, nbps, offs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_givens(cudaStream_t st, int nprob, int m, int j, int* act, const double* h1,
+                                const double* h2, const double* n2, double* H, double* cs, double* sn, double* g,
+                                int* its, int* steps, const double* target, int maxit, int* any) {
+    count_launch();
+    k_gmres_givens<<<1, NT, 0, st>>>(nprob, m, j, act, h1, h2, n2, H, cs, sn, g, its, steps, target, maxit, any);
+    return cudaGetLastError();
+}
+
+cudaError_t add_set_conditional_node(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle c,
+                                     const int* any, cudaGraphNode_t* out) {
+    cudaKernelNodeParams kp{};
+    void* args[] = {&c, &any};
+    kp.func = reinterpret_cast<void*>(k_set_conditional);
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(out, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
+}
 
 cudaError_t launch_seg_dot(cudaStream_t st, SegGrid g, const Seg* segs, const double* V, long long ld, int nv,
                            const double* w, double* partials) {

@@ -134,6 +134,7 @@ _SIGS = {
     "ras_newton_solve": (_I, [_P, _P, _P, ctypes.POINTER(ras_stats)]),
     "ras_get_state": (_I, [_P, ctypes.POINTER(ras_state)]),
     "ras_set_state": (_I, [_P, ctypes.POINTER(ras_state)]),
+    "ras_use_graphs": (_I, [_P, _I]),
     "ras_autotune": (_I, [_P, ctypes.POINTER(ras_tuning), ctypes.POINTER(ras_tune_report)]),
     "ras_get_tuning": (_I, [_P, ctypes.POINTER(ras_tuning)]),
     "ras_set_tuning": (_I, [_P, ctypes.POINTER(ras_tuning)]),
@@ -359,6 +360,11 @@ def ras_get_state(h):
 
 def ras_set_state(h, st):
     return h._check(lib().ras_set_state(h.ptr, ctypes.byref(st)))
+
+
+def ras_use_graphs(h, enable):
+    """CUDA-graph execution of the GMRES restart cycles on (default) or off."""
+    return h._check(lib().ras_use_graphs(h.ptr, 1 if enable else 0))
 
 
 def ras_autotune(h):
