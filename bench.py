@@ -39,11 +39,11 @@ FP64_LANES = 2       # FP64 FMA per clock per SM on GB300 (1.2 TFLOP/s class)
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the n1023 workload (profiles/dram_jvp_n1023.md), valid
 # while the kernel's sources are unchanged since that capture.
-TRAFFIC = {"jvp": {"bytes_per_launch": 8545434453.3, "workload": "n1023",
+TRAFFIC = {"jvp": {"bytes_per_launch": 8546142720.0, "workload": "n1023",
                    "sources": ["paper_2411_00546_gb300/csrc/solve.cu",
                                "paper_2411_00546_gb300/csrc/ras_internal.cuh"],
-                   "sha256": ["e6a725b53c9fa6fd5be1d63c47be3a9f8fba74c98487c6719fcebc01fb0e2a7f",
-                              "1174ab519f130c8c51685596a1939d589bf997d74280e9e42af51f6822c54263"]}}
+                   "sha256": ["f0efb1a3e01960cc4d101288c0db55eba4c15b8da07803980d579ed27e86b951",
+                              "ccfa73f34b78ead301799f60fed26bf6fd42c2b110916fd3091479f33d5d3ae9"]}}
 
 NEWTON_CAP = 25      # outer iterations of the unpreconditioned Newton baselines in the bench
 
@@ -184,6 +184,60 @@ def measure_serving(ras, torch, dev, stream, count):
     return res
 
 
+def measure_cfg2(ras, torch, dev, stream):
+    """The n = 255 family: phi in {exp, y^3} x mu in {1e-3, 5e-3} x Fourier
+    seeds {1, 2, 3}, RASPEN_eps in FP64 and in mixed precision. One handle
+    per (phi, mu, precision), warmed by one solve, then each seed's y_d
+    (ras_set_data) solved once from x0 = 0 and timed with CUDA events."""
+    from paper_2411_00546_gb300 import inputs
+    rows = []
+    for phi in (1, 0):
+        for mu in (1e-3, 5e-3):
+            sol = {}
+            for prec in (ras.RAS_FP64, ras.RAS_MIXED):
+                cfg = inputs.problem("n255", phi=phi, mu=mu)
+                n = cfg["n"]
+                o = ras.make_opts(tol=cfg["tol"], inner_tol=cfg["inner_tol"], sigma=cfg["sigma"], eps0=cfg["eps0"],
+                                  gamma=cfg["gamma"], eps_min=cfg["eps_min"], precision=prec)
+                yds = {seed: torch.tensor(inputs.make_yd(dict(cfg, yd=("fourier", seed))), dtype=torch.float64,
+                                          device=dev) for seed in (1, 2, 3)}
+                h = ras.ras_create(n, cfg["sx"], cfg["sy"], cfg["overlap"], phi, cfg["nu"], mu, yds[1], None, o,
+                                   stream=stream.cuda_stream)
+                y = torch.zeros((n, n), dtype=torch.float64, device=dev)
+                p = torch.zeros_like(y)
+                ras.ras_raspen_solve(h, y, p, check=False)   # warm-up (allocations, graph capture)
+                for seed in (1, 2, 3):
+                    ras.ras_set_data(h, yds[seed], None)
+                    with torch.cuda.stream(stream):
+                        y.zero_()
+                        p.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    rc, st = ras.ras_raspen_solve(h, y, p, check=False)
+                    b.record(stream)
+                    torch.cuda.synchronize(dev)
+                    sol[(prec, seed)] = (y.cpu().numpy(), p.cpu().numpy())
+                    rows.append({"phi": "exp" if phi == 1 else "y^3", "mu": mu, "seed": seed,
+                                 "precision": "fp64" if prec == ras.RAS_FP64 else "mixed", "ms": a.elapsed_time(b),
+                                 "status": rc, "outer_its": st.outer_its, "gmres_its": st.gmres_its,
+                                 "inner_its_sum": st.inner_its_sum})
+                ras.ras_destroy(h)
+            for seed in (1, 2, 3):
+                Y64, P64 = sol[(ras.RAS_FP64, seed)]
+                Ym, Pm = sol[(ras.RAS_MIXED, seed)]
+                for r in rows:
+                    if r["phi"] == ("exp" if phi == 1 else "y^3") and r["mu"] == mu and r["seed"] == seed \
+                            and r["precision"] == "mixed":
+                        r["err_vs_fp64_y"] = field_err(Ym, Y64, P64)
+                        r["err_vs_fp64_p"] = field_err(Pm, P64, Y64)
+    t64 = sum(r["ms"] for r in rows if r["precision"] == "fp64")
+    tmx = sum(r["ms"] for r in rows if r["precision"] == "mixed")
+    return {"workload": "n255: 8x8 subdomains, overlap 4, nu=1e-5, GMRES(30), eps 0.1->1e-6; phi x mu x seed",
+            "runs": rows, "fp64_ms_total": t64, "mixed_ms_total": tmx, "mixed_speedup": t64 / tmx if tmx else None,
+            "max_err_mixed_vs_fp64": max(max(r.get("err_vs_fp64_y", 0.0), r.get("err_vs_fp64_p", 0.0))
+                                        for r in rows)}
+
+
 def measure_methods(ras, torch, dev, stream):
     """The paper's method comparison (Sec. 5, its tables of outer / GMRES /
     inner counts and times) on the n255 workload in mixed precision: RASPEN,
@@ -254,6 +308,9 @@ def parse_args():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-methods", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-cfg2", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="GMRES cycles step by step (every kernel visible to a profiler's launch list)")
     ap.add_argument("--serve-requests", type=int, default=32)
     return ap.parse_args()
 
@@ -428,6 +485,8 @@ def main():
         return {"chosen": t.as_dict(), "s": round(time.perf_counter() - t0, 3), "timed": rep.as_dict()}
 
     h = make(ras.RAS_MIXED)
+    if args.no_graphs:
+        ras.ras_use_graphs(h, False)
     autotune = tune(h)
     y = torch.zeros((n, n), dtype=torch.float64, device=dev)
     p = torch.zeros_like(y)
@@ -620,6 +679,9 @@ def main():
     methods = None
     if rank == 0 and not args.no_methods:
         methods = measure_methods(ras, torch, dev, stream)
+    cfg2 = None
+    if rank == 0 and not args.no_cfg2:
+        cfg2 = measure_cfg2(ras, torch, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -658,7 +720,7 @@ def main():
                                            "GMRES cycles step by step); the timed region runs the GMRES "
                                            "cycles as CUDA graphs" % (args.steps, prof_ms / args.steps),
                           "kernels": kernels, "kernel_rooflines": kernel_rooflines,
-                          "uneven_batch": batch, "serving": serving, "methods": methods,
+                          "uneven_batch": batch, "serving": serving, "methods": methods, "n255_family": cfg2,
                           "autotune": autotune,
                           "y_max": float(np.abs(y_mixed).max()),
                           "p_max": float(np.abs(p_mixed).max())},

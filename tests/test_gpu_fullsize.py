@@ -126,3 +126,33 @@ def test_n1023_solution_properties(n1023, n1023_solves):
     Ym, Pm, _ = n1023_solves[ras.RAS_MIXED]
     assert rel_inf(Ym, Y64, P64) <= MIXED_TOL
     assert rel_inf(Pm, P64, Y64) <= MIXED_TOL
+
+
+# The other members of the n = 255 family (phi in {exp, y^3}, mu in {1e-3,
+# 5e-3}, Fourier seeds 1-3): one variant per changed factor, full RASPEN
+# solves against the oracle in FP64 and mixed precision.
+N255_VARIANTS = [(1, 1e-3, 2), (0, 5e-3, 3), (1, 5e-3, 1)]
+
+
+@pytest.fixture(scope="module", params=N255_VARIANTS, ids=lambda v: "phi%d-mu%g-seed%d" % v)
+def n255_variant(request):
+    phi, mu, seed = request.param
+    cfg = inputs.problem("n255", phi=phi, mu=mu, yd=("fourier", seed))
+    prob = oracle_problem(cfg)
+    return cfg, solvers.raspen(prob, cfg["sx"], cfg["sy"], cfg["overlap"], oracle_opts(cfg))
+
+
+@pytest.mark.parametrize("prec,tol", PRECS)
+def test_n255_variant_raspen_solve(n255_variant, prec, tol):
+    cfg, ref = n255_variant
+    n = cfg["n"]
+    h = gpu_problem(cfg, prec)
+    try:
+        y, p = zeros(n), zeros(n)
+        rc, st = ras.ras_raspen_solve(h, y, p)
+        assert rel_inf(y.cpu().numpy(), ref.Y, ref.P) <= tol
+        assert rel_inf(p.cpu().numpy(), ref.P, ref.Y) <= tol
+        assert st.outer_its == ref.outer
+        assert st.inner_its_sum == sum(sum(i) for i in ref.inner_its)
+    finally:
+        ras.ras_destroy(h)
