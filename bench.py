@@ -38,12 +38,15 @@ FP64_LANES = 2       # FP64 FMA per clock per SM on GB300 (1.2 TFLOP/s class)
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the n1023 workload (profiles/dram_jvp_n1023.md), valid
-# while the kernel's sources are unchanged since that capture.
+# while what the kernel is built from is unchanged since that capture: its
+# source file, and the data layouts it reads (the header from ProbDev to the
+# status values).
 TRAFFIC = {"jvp": {"bytes_per_launch": 8546142720.0, "workload": "n1023",
-                   "sources": ["paper_2411_00546_gb300/csrc/solve.cu",
-                               "paper_2411_00546_gb300/csrc/ras_internal.cuh"],
+                   "sources": [("paper_2411_00546_gb300/csrc/solve.cu", None, None),
+                               ("paper_2411_00546_gb300/csrc/ras_internal.cuh", "struct ProbDev {",
+                                "// Status values")],
                    "sha256": ["f0efb1a3e01960cc4d101288c0db55eba4c15b8da07803980d579ed27e86b951",
-                              "ccfa73f34b78ead301799f60fed26bf6fd42c2b110916fd3091479f33d5d3ae9"]}}
+                              "28382610a57d0127f35485ec44db715ade6772f607ad44839b39d271bd0f8d38"]}}
 
 NEWTON_CAP = 25      # outer iterations of the unpreconditioned Newton baselines in the bench
 
@@ -67,12 +70,18 @@ def traffic_for(kind, workload):
     t = TRAFFIC.get(kind)
     if t is None or t["workload"] != workload:
         return None
-    for path, sha in zip(t["sources"], t["sha256"]):
+    for (path, start, end), sha in zip(t["sources"], t["sha256"]):
         try:
             with open(os.path.join(ROOT, path), "rb") as fh:
-                if hashlib.sha256(fh.read()).hexdigest() != sha:
-                    return None
+                data = fh.read()
         except OSError:
+            return None
+        if start is not None:
+            text = data.decode()
+            if start not in text or end not in text:
+                return None
+            data = text[text.index(start):text.index(end)].encode()
+        if hashlib.sha256(data).hexdigest() != sha:
             return None
     return t["bytes_per_launch"]
 

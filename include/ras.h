@@ -352,14 +352,18 @@ long long ras_launch_count(void);
 int ras_profile(ras_problem* h, int enable);
 int ras_profile_read(ras_problem* h, int kind, double* ms, long long* launches, double* work);
 
-/* CUDA-graph execution of the GMRES restart cycles (not part of the paper's
- * method; default on). Every Arnoldi step (the operator, the CGS2 products,
- * the Givens update of the Hessenberg column and the stop test) runs on the
- * device; with graphs on, a whole cycle is one graph launch (one IF node per
- * step, skipped once every problem has stopped) and the host reads the cycle
- * once, instead of once per step. The graph of each operator is captured on
- * first use and again after the handle's buffers, layout, options or tuning
- * change. Both modes run the same kernels in the same order and give
+/* CUDA-graph execution (not part of the paper's method; default on).
+ * Every Arnoldi step (the operator, the CGS2 products, the Givens update of
+ * the Hessenberg column and the stop test) and every local Newton sweep step
+ * runs on the device; with graphs on, a GMRES restart cycle is one graph
+ * launch (one IF node per step, skipped once every problem has stopped), and
+ * so is a RASPEN-function evaluation (Alg. 3: init, a WHILE node over the
+ * sweep steps of Alg. 1 in all subdomains, with the factor kernel of each
+ * register-tile class chosen on the device from the active count, then the
+ * factors at the local solutions and the prolongation). The host reads a
+ * cycle or an evaluation once, instead of once per step. Each graph is
+ * captured on first use and again after the handle's buffers, layout,
+ * options or tuning change. Both modes run the same kernels in the same order and give
  * identical results. While ras_profile is on, cycles run step by step (the
  * per-kernel events cannot sit inside a graph's conditional bodies).
  * RAS_EINVAL on a NULL handle. */

@@ -126,6 +126,20 @@ struct ras_problem {
         std::vector<long long> kps;                 // kernels per step
     };
     CycleGraph cg[3];                // by operator: 0 Jacobian action of Alg. 4, 1 global Jacobian, 2 with RAS
+    // the RASPEN-function evaluation (Alg. 3: the local Newton sweeps of Alg. 1
+    // in every subdomain) as one graph: init, a WHILE node over the sweep
+    // steps, the factors at the local solutions and the prolongation
+    struct SweepGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long gen = 0;
+        const double* Fout = nullptr;
+        int prec = -1;
+        long long k_pre = 0, k_body = 0, k_post = 0;   // kernels of each part
+    };
+    SweepGraph sg;
+    int* d_guard = nullptr;          // sweep steps taken + 1 (device)
+    int* h_guard = nullptr;          // pinned
     cudaStream_t cap_st = nullptr;   // capture stream
     std::vector<cudaEvent_t> ev_pool;
     double prof_ms[RAS_K_COUNT] = {};
@@ -507,6 +521,150 @@ int launch_factor(ras_problem* h, int only_active, double flops, int nwork) {
     return RAS_OK;
 }
 
+// Sweep-step factorisation for a graph: both FP32 kernels of every class,
+// the device's active count choosing which one works (the rule of
+// launch_factor).
+template <typename T>
+int launch_factor_sel(ras_problem* h) {
+    if (sizeof(T) == sizeof(float)) {
+        for (int c = 0; c < NTILE; ++c) {
+            if (h->tile_cnt[c] == 0) continue;
+            const int thr = h->tune.factor_wide_max[c] < 0 ? h->sms : h->tune.factor_wide_max[c];
+            for (int wide = 0; wide < 2; ++wide)
+                CK(ras::launch_local_factor_f32(h->st, 2 * (c + 1), h->tile_cnt[c], h->d_lists + h->tile_off[c],
+                                                h->d_subs, h->d_probs, h->X, h->ls, h->cpool, h->coef,
+                                                (float*)h->gpool, 1, wide, ras::FactorSel{h->d_active, thr}));
+        }
+        return RAS_OK;
+    }
+    CK(ras::launch_local_factor<T>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs, h->X, h->ls, h->cpool, h->coef,
+                                   (T*)h->gpool, 1));
+    return RAS_OK;
+}
+
+// Capture what fn enqueues on h->st into a new graph (*out); *count: the
+// kernels it launched.
+template <class Fn>
+int capture_graph(ras_problem* h, Fn fn, cudaGraph_t* out, long long* count) {
+    *out = nullptr;
+    CK(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeRelaxed));
+    const cudaStream_t saved = h->st;
+    long long c = 0;
+    h->st = h->cap_st;
+    ras::t_capture_count = &c;
+    const int rc = fn();
+    ras::t_capture_count = nullptr;
+    h->st = saved;
+    const cudaError_t e = cudaStreamEndCapture(h->cap_st, out);
+    *count = c;
+    if (rc < 0) {
+        if (*out) cudaGraphDestroy(*out);
+        *out = nullptr;
+        cudaGetLastError();
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(h, RAS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    return RAS_OK;
+}
+
+void destroy_sweep_graph(ras_problem::SweepGraph& G) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G = ras_problem::SweepGraph{};
+}
+
+// The evaluation as one graph: [init] -> [condition] -> WHILE { factor
+// (device choice of kernel), direction, line search, condition } ->
+// [factors at x^(i), prolongation into Fout]. The condition is the host
+// loop's: active subdomains left and at most kmax_inner + 2 steps.
+template <typename T>
+int build_sweep_graph(ras_problem* h, double* Fout, const NewtonParams& np) {
+    auto& G = h->sg;
+    destroy_sweep_graph(G);
+    if (!h->cap_st) CK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+    CK(cudaGraphCreate(&G.graph, 0));
+    T* gp = (T*)h->gpool;
+    T* wp = (T*)h->wpool;
+    const int limit = h->o.kmax_inner + 1;
+    int rc = RAS_OK;
+    cudaGraph_t part = nullptr;
+    cudaGraphNode_t n_pre = nullptr, n_c0 = nullptr, n_w = nullptr, n_post = nullptr;
+    cudaGraphConditionalHandle w{};
+    cudaError_t e = cudaGraphConditionalHandleCreate(&w, G.graph, 0u, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) rc = fail(h, RAS_ECUDA, std::string("graph: ") + cudaGetErrorString(e));
+    if (rc == RAS_OK)
+        rc = capture_graph(h, [&]() -> int {
+            CK(cudaMemsetAsync(h->d_active, 0, sizeof(int), h->st));
+            CK(ras::launch_local_init(h->st, h->nsub, h->d_subs, h->d_probs, h->X, h->ls, h->d_pstart, np, h->cpool,
+                                      h->Kpool, h->d_active));
+            return RAS_OK;
+        }, &part, &G.k_pre);
+    if (rc == RAS_OK) {
+        e = cudaGraphAddChildGraphNode(&n_pre, G.graph, nullptr, 0, part);
+        cudaGraphDestroy(part);
+        part = nullptr;
+        if (e == cudaSuccess)
+            e = ras::add_sweep_cond_node(G.graph, n_pre, w, h->d_active, h->d_guard, limit, 1, &n_c0);
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = w;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&n_w, G.graph, &n_c0, nullptr, 1, &cp);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(h->cap_st, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) rc = fail(h, RAS_ECUDA, std::string("graph: ") + cudaGetErrorString(e));
+        if (rc == RAS_OK) {
+            const cudaStream_t saved = h->st;
+            long long c = 0;
+            h->st = h->cap_st;
+            ras::t_capture_count = &c;
+            rc = [&]() -> int {
+                TRY(launch_factor_sel<T>(h));
+                CK(ras::launch_local_direction<T>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs,
+                                                  h->ls, np, h->coef, gp, h->Kpool, h->dpool, h->rpool, wp, h->d_err,
+                                                  h->d_order, h->d_ticket));
+                CK(cudaMemsetAsync(h->d_active, 0, sizeof(int), h->st));
+                CK(ras::launch_local_linesearch(h->st, h->nsub, h->d_subs, h->d_probs, h->X, h->ls, np, h->cpool,
+                                                h->dpool, h->Kpool, h->Ktpool, h->d_active));
+                CK(ras::launch_sweep_cond(h->st, w, h->d_active, h->d_guard, limit, 0));
+                return RAS_OK;
+            }();
+            ras::t_capture_count = nullptr;
+            h->st = saved;
+            cudaGraph_t body = nullptr;
+            e = cudaStreamEndCapture(h->cap_st, &body);
+            if (rc == RAS_OK && e != cudaSuccess)
+                rc = fail(h, RAS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            G.k_body = c;
+        }
+    }
+    if (rc == RAS_OK)
+        rc = capture_graph(h, [&]() -> int {
+            TRY(launch_factor<T>(h, 0, 0.0, h->nsub));
+            CK(ras::launch_local_prolong(h->st, h->nsub, h->d_subs, h->d_probs, h->ls, h->cpool, Fout));
+            return RAS_OK;
+        }, &part, &G.k_post);
+    if (rc == RAS_OK) {
+        e = cudaGraphAddChildGraphNode(&n_post, G.graph, &n_w, 1, part);
+        cudaGraphDestroy(part);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, G.graph, 0);
+        if (e != cudaSuccess) rc = fail(h, RAS_ECUDA, std::string("graph: ") + cudaGetErrorString(e));
+    }
+    cudaGetLastError();
+    if (rc != RAS_OK) {
+        destroy_sweep_graph(G);
+        return rc;
+    }
+    G.gen = h->gen;
+    G.Fout = Fout;
+    G.prec = h->o.precision;
+    return RAS_OK;
+}
+
+int evaluation_results(ras_problem* h, const std::vector<double>& pstart, ras_stats* stats);
+
 // --------------------------------------------------------------- Alg. 3
 // RASPEN function of the problems with pstart[p] > 0 (eps at which their
 // local solves start); per-problem counters into stats[p] (may be null).
@@ -517,6 +675,27 @@ int ras_apply_T(ras_problem* h, const std::vector<double>& pstart, double* Fout,
     T* gp = (T*)h->gpool;
     T* wp = (T*)h->wpool;
     CK(cudaMemcpyAsync(h->d_pstart, pstart.data(), h->nprob * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    if (h->use_graphs && !h->prof_on) {
+        // the whole evaluation as one graph launch (profiled runs take the loop below)
+        if (h->sms == 0) {
+            int dev = 0;
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
+        }
+        TRY(ensure(h, &h->d_guard, (size_t)1));
+        if (!h->h_guard && cudaMallocHost((void**)&h->h_guard, sizeof(int)) != cudaSuccess) {
+            h->h_guard = nullptr;
+            return fail(h, RAS_ENOMEM, "pinned host allocation failed");
+        }
+        auto& G = h->sg;
+        if (!G.exec || G.gen != h->gen || G.Fout != Fout || G.prec != h->o.precision)
+            TRY(build_sweep_graph<T>(h, Fout, np));
+        CK(cudaGraphLaunch(G.exec, h->st));
+        CK(cudaMemcpyAsync(h->h_guard, h->d_guard, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        TRY(sync(h));
+        ras::add_launches(G.k_pre + 1 + (long long)std::max(0, *h->h_guard - 1) * G.k_body + G.k_post);
+        return evaluation_results(h, pstart, stats);
+    }
     CK(cudaMemsetAsync(h->d_active, 0, sizeof(int), h->st));
     CK(timed(h, RAS_K_INIT, 0.0, [&] {
         return ras::launch_local_init(h->st, h->nsub, h->d_subs, h->d_probs, h->X, h->ls, h->d_pstart, np,
@@ -571,6 +750,12 @@ int ras_apply_T(ras_problem* h, const std::vector<double>& pstart, double* Fout,
     CK(timed(h, RAS_K_OTHER, 0.0, [&] {
         return ras::launch_local_prolong(h->st, h->nsub, h->d_subs, h->d_probs, h->ls, h->cpool, Fout);
     }));
+    return evaluation_results(h, pstart, stats);
+}
+
+// Local states after an evaluation: counters into stats, the local
+// iteration counts, and the first local failure.
+int evaluation_results(ras_problem* h, const std::vector<double>& pstart, ras_stats* stats) {
     std::vector<LocalState> ls(h->nsub);
     CK(cudaMemcpyAsync(ls.data(), h->ls, h->nsub * sizeof(LocalState), cudaMemcpyDeviceToHost, h->st));
     TRY(sync(h));
@@ -1870,6 +2055,9 @@ void ras_destroy(ras_problem* h) {
     cudaStreamSynchronize(h->st);
     prof_flush(h);
     for (auto& G : h->cg) destroy_cycle_graph(G);
+    if (h->sg.exec) cudaGraphExecDestroy(h->sg.exec);
+    if (h->sg.graph) cudaGraphDestroy(h->sg.graph);
+    if (h->h_guard) cudaFreeHost(h->h_guard);
     if (h->cap_st) cudaStreamDestroy(h->cap_st);
     if (h->h_any) cudaFreeHost(h->h_any);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);

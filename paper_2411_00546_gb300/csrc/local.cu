@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub
                                                                         const double* X, LocalState* ls,
                                                                         const double* cpool, double* coef,
                                                                         float* gpool, int only_active,
-                                                                        const int* __restrict__ list) {
+                                                                        const int* __restrict__ list, FactorSel sel) {
     constexpr int MM = 16 * R;
     constexpr int PAD = ((R + 3) / 4) * 4;   // owner stride in the panel buffers
     constexpr int LDC = 16 * PAD;            // one panel column (or row) of 16 owners
@@ -543,6 +543,7 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub
     __shared__ float sh_piv;
     extern __shared__ __align__(16) float Ms[];
     if ((int)blockIdx.x >= nsub) return;
+    if (sel.nwork && min(*sel.nwork, nsub) <= sel.thr) return;   // the 1024-thread kernel's turn
     const int i = list ? list[blockIdx.x] : (int)blockIdx.x;
     if (only_active && !ls[i].active) return;
     if (ls[i].status == ST_SKIP) return;
@@ -818,7 +819,7 @@ __global__ void __launch_bounds__(1024, 1) k_local_factor_wide(int nsub, const S
                                                                const double* X, LocalState* ls,
                                                                const double* cpool, double* coef,
                                                                float* gpool, int only_active,
-                                                               const int* __restrict__ list) {
+                                                               const int* __restrict__ list, FactorSel sel) {
     constexpr int NTH = 1024, NWARP = 32;
     constexpr int MM = 32 * R;
     constexpr int PAD = ((R + 3) / 4) * 4;   // owner stride of the row panel
@@ -836,6 +837,7 @@ __global__ void __launch_bounds__(1024, 1) k_local_factor_wide(int nsub, const S
     __shared__ float sh_piv;
     extern __shared__ __align__(16) float Ms[];
     if ((int)blockIdx.x >= nsub) return;
+    if (sel.nwork && min(*sel.nwork, nsub) > sel.thr) return;    // the 256-thread kernel's turn
     const int i = list ? list[blockIdx.x] : (int)blockIdx.x;
     if (only_active && !ls[i].active) return;
     if (ls[i].status == ST_SKIP) return;
@@ -1059,6 +1061,13 @@ size_t factor_smem(int maxm) {
     return (size_t)maxm * (maxm + 1) * sizeof(T) + (size_t)maxm * sizeof(T) + 3 * (size_t)maxm * sizeof(int);
 }
 
+// Loop condition of the local Newton sweep (see launch_sweep_cond).
+__global__ void k_sweep_cond(cudaGraphConditionalHandle c, const int* active, int* guard, int limit, int reset) {
+    const int g = reset ? 0 : *guard;
+    *guard = g + 1;
+    cudaGraphSetConditional(c, (*active > 0 && g <= limit) ? 1u : 0u);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
@@ -1073,48 +1082,48 @@ cudaError_t launch_local_init(cudaStream_t st, int nsub, const SubDev* subs, con
 template <int R>
 cudaError_t launch_factor_panel(cudaStream_t st, int count, const SubDev* subs, const ProbDev* probs,
                               const double* X, LocalState* ls, const double* cpool, double* coef,
-                              float* gpool, int only_active, const int* list) {
+                              float* gpool, int only_active, const int* list, FactorSel fs) {
     const size_t sm = (size_t)(16 * R) * (16 * R + 4) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_local_factor_panel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     count_launch();
     k_local_factor_panel<R><<<count, FACT_THREADS, sm, st>>>(count, subs, probs, X, ls, cpool, coef, gpool,
-                                                           only_active, list);
+                                                           only_active, list, fs);
     return cudaGetLastError();
 }
 
 template <int R>
 cudaError_t launch_factor_wide(cudaStream_t st, int count, const SubDev* subs, const ProbDev* probs,
                                const double* X, LocalState* ls, const double* cpool, double* coef,
-                               float* gpool, int only_active, const int* list) {
+                               float* gpool, int only_active, const int* list, FactorSel fs) {
     const size_t sm = (size_t)(32 * R) * (32 * R + 4) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_local_factor_wide<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     count_launch();
     k_local_factor_wide<R><<<count, 1024, sm, st>>>(count, subs, probs, X, ls, cpool, coef, gpool, only_active,
-                                                    list);
+                                                    list, fs);
     return cudaGetLastError();
 }
 
 cudaError_t launch_local_factor_f32(cudaStream_t st, int tile, int count, const int* list, const SubDev* subs,
                                     const ProbDev* probs, const double* X, LocalState* ls, const double* cpool,
-                                    double* coef, float* gpool, int only_active, int wide) {
+                                    double* coef, float* gpool, int only_active, int wide, FactorSel fs) {
     if (wide) {
         switch (tile) {
-            case 2: return launch_factor_wide<1>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
-            case 4: return launch_factor_wide<2>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
-            case 6: return launch_factor_wide<3>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
-            case 8: return launch_factor_wide<4>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
-            case 10: return launch_factor_wide<5>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+            case 2: return launch_factor_wide<1>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list, fs);
+            case 4: return launch_factor_wide<2>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list, fs);
+            case 6: return launch_factor_wide<3>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list, fs);
+            case 8: return launch_factor_wide<4>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list, fs);
+            case 10: return launch_factor_wide<5>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list, fs);
             default: return cudaErrorInvalidValue;
         }
     }
     switch (tile) {
-        case 2: return launch_factor_panel<2>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
-        case 4: return launch_factor_panel<4>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
-        case 6: return launch_factor_panel<6>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
-        case 8: return launch_factor_panel<8>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
-        case 10: return launch_factor_panel<10>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list);
+        case 2: return launch_factor_panel<2>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list, fs);
+        case 4: return launch_factor_panel<4>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list, fs);
+        case 6: return launch_factor_panel<6>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list, fs);
+        case 8: return launch_factor_panel<8>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list, fs);
+        case 10: return launch_factor_panel<10>(st, count, subs, probs, X, ls, cpool, coef, gpool, only_active, list, fs);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1145,6 +1154,25 @@ cudaError_t launch_local_linesearch(cudaStream_t st, int nsub, const SubDev* sub
     k_local_linesearch<<<nsub, NT, 0, st>>>(nsub, subs, probs, X, ls, np, cpool, dpool, Kpool, Ktpool,
                                             active_count);
     return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_cond(cudaStream_t st, cudaGraphConditionalHandle c, const int* active, int* guard,
+                              int limit, int reset) {
+    count_launch();
+    k_sweep_cond<<<1, 1, 0, st>>>(c, active, guard, limit, reset);
+    return cudaGetLastError();
+}
+
+cudaError_t add_sweep_cond_node(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle c,
+                                const int* active, int* guard, int limit, int reset, cudaGraphNode_t* out) {
+    cudaKernelNodeParams kp{};
+    void* args[] = {&c, &active, &guard, &limit, &reset};
+    kp.func = reinterpret_cast<void*>(k_sweep_cond);
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(out, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
 }
 
 cudaError_t launch_local_prolong(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,

@@ -247,13 +247,29 @@ cudaError_t launch_local_init(cudaStream_t st, int nsub, const SubDev* subs, con
                               double* cpool, double* Kpool, int* active_count);
 // FP32 register-tile factorisation of the `count` subdomains in `list`
 // (device indices; null = 0..count-1), all with packed size mp <= 16*tile.
+// Device-side choice between the two FP32 factor kernels of a class: with
+// nwork set, the 1024-thread kernel works when min(*nwork, count) <= thr and
+// the 256-thread one otherwise (the other returns at once), so one graph can
+// hold both launches. nwork null: the launched kernel always works.
+struct FactorSel {
+    const int* nwork;
+    int thr;
+};
 // FP32 factorisation of one register-tile class (tile = mp / 16) over the
 // `count` subdomains of `list`: 256-thread CTAs (two per SM) by default;
 // wide != 0 selects 1024-thread CTAs (one per SM), faster when at most one
 // CTA per SM has work.
 cudaError_t launch_local_factor_f32(cudaStream_t st, int tile, int count, const int* list, const SubDev* subs,
                                     const ProbDev* probs, const double* X, LocalState* ls, const double* cpool,
-                                    double* coef, float* gpool, int only_active, int wide);
+                                    double* coef, float* gpool, int only_active, int wide,
+                                    FactorSel sel = FactorSel{nullptr, 0});
+// Loop condition of the local Newton sweep (Alg. 1 in every subdomain) as a
+// graph WHILE node: c = (*active > 0 && g <= limit) with g the number of
+// earlier evaluations (*guard, 0 when reset), which it then increments.
+cudaError_t launch_sweep_cond(cudaStream_t st, cudaGraphConditionalHandle c, const int* active, int* guard,
+                              int limit, int reset);
+cudaError_t add_sweep_cond_node(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle c,
+                                const int* active, int* guard, int limit, int reset, cudaGraphNode_t* out);
 template <typename T>
 cudaError_t launch_local_factor(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                                 const ProbDev* probs, const double* X, LocalState* ls,

@@ -91,3 +91,23 @@ def test_profiled_solve_equals_graph_solve():
         assert kr_n >= 5 * st.gmres_its and kr_ms > 0
     finally:
         ras.ras_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [ras.RAS_FP64, ras.RAS_MIXED])
+def test_graph_evaluation_equals_step_by_step(prec):
+    """The RASPEN-function evaluation (local Newton sweeps under a graph WHILE
+    node, the factor kernel chosen on the device) equals the host-driven loop."""
+    cfg = inputs.problem("n255")
+    n = cfg["n"]
+    out = []
+    for graphs in (False, True):
+        h = gpu_problem(cfg, prec)
+        try:
+            ras.ras_use_graphs(h, graphs)
+            Fy, Fp = zeros(n), zeros(n)
+            ras.ras_apply(h, zeros(n), zeros(n), 1, Fy, Fp)
+            out.append((Fy.cpu().numpy(), Fp.cpu().numpy(), list(ras.ras_local_iterations(h))))
+        finally:
+            ras.ras_destroy(h)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2] and max(out[0][2]) > 1
