@@ -247,6 +247,74 @@ def measure_cfg2(ras, torch, dev, stream):
                                         for r in rows)}
 
 
+def measure_sweeps(ras, torch, dev, stream):
+    """Sensitivity studies in mixed precision. Weak scaling: s x s subdomains
+    of 50^2 nodes (n = 50 s, overlap 2, s = 2..11), RASPEN and Newton_RAS with
+    and without eps-continuation: outer iterations, time, mean GMRES steps
+    per outer iteration. Continuation schedules at n = 255: RASPEN_eps for
+    eps0 in {1, 1e-3, 1e-5} x gamma in {1/2, 1/5, 1/10}. Every handle is
+    warmed by one solve; each entry is one timed solve from x0 = 0."""
+    from paper_2411_00546_gb300 import inputs
+
+    def opts(cfg, **over):
+        kw = dict(tol=cfg["tol"], inner_tol=cfg["inner_tol"], sigma=cfg["sigma"], eps0=cfg["eps0"],
+                  gamma=cfg["gamma"], eps_min=cfg["eps_min"], precision=ras.RAS_MIXED)
+        kw.update(over)
+        return ras.make_opts(**kw)
+
+    def timed_solve(h, fn, y, p):
+        with torch.cuda.stream(stream):
+            y.zero_()
+            p.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rc, st = fn(h, y, p, check=False)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return {"status": rc, "outer": st.outer_its, "ms": round(a.elapsed_time(b), 2),
+                "gmres_per_outer": round(st.gmres_its / max(st.outer_its, 1), 1), "inner_its_sum": st.inner_its_sum}
+
+    weak = []
+    for sd in range(2, 12):
+        cfg = inputs.problem("weak%d" % sd)
+        n = cfg["n"]
+        yd = torch.tensor(inputs.make_yd(cfg), dtype=torch.float64, device=dev)
+        h = ras.ras_create(n, sd, sd, cfg["overlap"], cfg["phi"], cfg["nu"], cfg["mu"], yd, None, opts(cfg),
+                           stream=stream.cuda_stream)
+        y = torch.zeros((n, n), dtype=torch.float64, device=dev)
+        p = torch.zeros_like(y)
+        timed_solve(h, ras.ras_raspen_solve, y, p)   # warm-up
+        row = {"s": sd, "n": n}
+        for label, fn, cont in (("RASPEN_eps", ras.ras_raspen_solve, True), ("RASPEN", ras.ras_raspen_solve, False),
+                                ("Newton_RAS_eps", ras.ras_newton_ras_solve, True),
+                                ("Newton_RAS", ras.ras_newton_ras_solve, False)):
+            ras.ras_set_opts(h, opts(cfg) if cont else opts(cfg, eps0=cfg["eps_min"]))
+            row[label] = timed_solve(h, fn, y, p)
+        ras.ras_destroy(h)
+        weak.append(row)
+    cont = []
+    cfg = inputs.problem("n255")
+    n = cfg["n"]
+    yd = torch.tensor(inputs.make_yd(cfg), dtype=torch.float64, device=dev)
+    h = ras.ras_create(n, cfg["sx"], cfg["sy"], cfg["overlap"], cfg["phi"], cfg["nu"], cfg["mu"], yd, None,
+                       opts(cfg), stream=stream.cuda_stream)
+    y = torch.zeros((n, n), dtype=torch.float64, device=dev)
+    p = torch.zeros_like(y)
+    timed_solve(h, ras.ras_raspen_solve, y, p)
+    for eps0 in (1.0, 1e-3, 1e-5):
+        for gamma in (0.5, 0.2, 0.1):
+            ras.ras_set_opts(h, opts(cfg, eps0=eps0, gamma=gamma))
+            r = timed_solve(h, ras.ras_raspen_solve, y, p)
+            r.update(eps0=eps0, gamma=gamma)
+            cont.append(r)
+    ras.ras_destroy(h)
+    return {"weak_scaling": {"workload": "s x s subdomains of 50^2 nodes (n = 50 s), overlap 2, phi=y^3, "
+                                         "nu=1e-6, mu=1e-2, Fourier y_d seed 1, eps 0.1->1e-6 (gamma 0.1); "
+                                         "without continuation eps0 = eps_min", "rows": weak},
+            "continuation": {"workload": "n255 (8x8, overlap 4, nu=1e-5, mu=1e-3), RASPEN_eps, eps_min 1e-6",
+                             "rows": cont}}
+
+
 def measure_methods(ras, torch, dev, stream):
     """The paper's method comparison (Sec. 5, its tables of outer / GMRES /
     inner counts and times) on the n255 workload in mixed precision: RASPEN,
@@ -318,6 +386,7 @@ def parse_args():
     ap.add_argument("--no-methods", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cfg2", action="store_true")
+    ap.add_argument("--no-sweeps", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",
                     help="GMRES cycles step by step (every kernel visible to a profiler's launch list)")
     ap.add_argument("--serve-requests", type=int, default=32)
@@ -691,6 +760,9 @@ def main():
     cfg2 = None
     if rank == 0 and not args.no_cfg2:
         cfg2 = measure_cfg2(ras, torch, dev, stream)
+    sweeps = None
+    if rank == 0 and not args.no_sweeps:
+        sweeps = measure_sweeps(ras, torch, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -730,6 +802,7 @@ def main():
                                            "cycles as CUDA graphs" % (args.steps, prof_ms / args.steps),
                           "kernels": kernels, "kernel_rooflines": kernel_rooflines,
                           "uneven_batch": batch, "serving": serving, "methods": methods, "n255_family": cfg2,
+                          "sweeps": sweeps,
                           "autotune": autotune,
                           "y_max": float(np.abs(y_mixed).max()),
                           "p_max": float(np.abs(p_mixed).max())},

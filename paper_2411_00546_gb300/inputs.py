@@ -93,6 +93,9 @@ def problem(name, **over):
         cfg = dict(n=511, sx=8, sy=8, overlap=8, phi=PHI_CUBIC, nu=1e-6, mu=1e-2, yd=("fourier", 1))
     elif name == "n1023_active":  # n1023 with mu = 1e-3: the L1 term is active (nonzero control)
         cfg = dict(n=1023, sx=16, sy=16, overlap=8, phi=PHI_CUBIC, nu=1e-6, mu=1e-3, yd=("fourier", 1))
+    elif name.startswith("weak"):  # weak-scaling layout: s x s subdomains of 50^2 nodes, overlap 2
+        s_ = int(name[4:])
+        cfg = dict(n=50 * s_, sx=s_, sy=s_, overlap=2, phi=PHI_CUBIC, nu=1e-6, mu=1e-2, yd=("fourier", 1))
     else:
         raise KeyError(name)
     base.update(cfg)
