@@ -859,11 +859,12 @@ int precond_internal(ras_problem* h, const double* R, double* Zo) {
 
 // --------------------------------------------------------------- GMRES
 // Restarted GMRES(m) for every problem p with part[p] != 0, in lockstep:
-// CGS2 Arnoldi with segmented (per-problem) reductions, Givens rotations on
-// the host, x0 = 0, right preconditioning when `prec`. A(in, out, mask) and
-// M(in, out, mask) act on the problems flagged in mask (host) = d_mask row 0
-// (device), which this routine keeps equal to the problems still iterating.
-// One host synchronisation per Krylov step for the whole batch.
+// CGS2 Arnoldi with segmented (per-problem) reductions, Givens rotations and
+// stop tests on the device, x0 = 0, right preconditioning when `prec`.
+// A(in, out, mask) and M(in, out, mask) act on the problems flagged in
+// d_mask row 0, which the Givens kernel keeps equal to the problems still
+// iterating. The host reads each restart cycle once (back-substitution and
+// update); the cycle itself is one graph launch or a step-by-step loop.
 // Resumable GMRES for the serving loop: per problem, `fresh` starts from
 // x = 0 and sets its stop target from ||b||; otherwise x holds the iterate of
 // earlier cycles and `target` the target set then. At most max_cycles restart
