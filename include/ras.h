@@ -214,6 +214,12 @@ int ras_server_counts(const ras_server* s, int* pending, int* active, int* finis
 int ras_server_finished_ids(const ras_server* s, long long* ids, int cap);
 int ras_server_fetch(ras_server* s, long long id, double* y_host, double* p_host, ras_stats* st);
 int ras_server_cancel(ras_server* s, long long id);
+/* CUDA graphs (ras_use_graphs) in the server's workspaces, default off: a
+ * workspace's graphs would be captured again after every relayout (whenever
+ * the set of requests in a phase changes), which costs more than the
+ * per-step host reads they save (on the 32-request stream sample: p50
+ * latency 14.5 s with graphs, 13.0 s without). RAS_EINVAL on a NULL server. */
+int ras_server_use_graphs(ras_server* s, int enable);
 size_t ras_server_device_bytes(const ras_server* s);
 const char* ras_server_last_error(const ras_server* s);
 void ras_server_destroy(ras_server* s);

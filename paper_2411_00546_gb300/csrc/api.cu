@@ -2119,6 +2119,7 @@ struct ras_server {
     std::vector<Req*> finished;          // result kept until fetched
     std::vector<Req*> ev, kr;            // admitted requests by phase (layouts of ws / wk)
     bool dirty = true, dirty_k = true;
+    bool use_graphs = false;             // CUDA graphs in the two workspaces (re-captured per relayout)
     long long next_id = 1;
     size_t slot_held = 0, scratch_active = 0, ws_cap = 0;
     std::string err;
@@ -2180,6 +2181,7 @@ int server_relayout(ras_server* s, ras_problem*& h, cudaStream_t st, const std::
         h->o = s->o;
         h->st = st;
         h->own_factors = false;
+        h->use_graphs = s->use_graphs;
     }
     std::vector<ras_problem_desc> descs;
     for (auto* r : reqs) {
@@ -2555,6 +2557,14 @@ int ras_server_fetch(ras_server* s, long long id, double* y_host, double* p_host
         return status;
     }
     return sfail(s, RAS_EINVAL, "no finished request with this id");
+}
+
+int ras_server_use_graphs(ras_server* s, int enable) {
+    if (!s) return RAS_EINVAL;
+    s->use_graphs = enable != 0;
+    if (s->ws) s->ws->use_graphs = s->use_graphs;
+    if (s->wk) s->wk->use_graphs = s->use_graphs;
+    return RAS_OK;
 }
 
 int ras_server_cancel(ras_server* s, long long id) {

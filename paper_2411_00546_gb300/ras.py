@@ -157,6 +157,7 @@ _SIGS = {
     "ras_server_finished_ids": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), _I]),
     "ras_server_fetch": (_I, [_P, ctypes.c_longlong, _P, _P, ctypes.POINTER(ras_stats)]),
     "ras_server_cancel": (_I, [_P, ctypes.c_longlong]),
+    "ras_server_use_graphs": (_I, [_P, _I]),
     "ras_server_device_bytes": (ctypes.c_size_t, [_P]),
     "ras_server_last_error": (ctypes.c_char_p, [_P]),
     "ras_server_destroy": (None, [_P]),
@@ -604,6 +605,10 @@ def ras_server_fetch(s, rid):
 def ras_server_cancel(s, rid):
     s._check(lib().ras_server_cancel(s.ptr, rid))
     s.sizes.pop(rid, None)
+
+
+def ras_server_use_graphs(s, enable):
+    s._check(lib().ras_server_use_graphs(s.ptr, 1 if enable else 0))
 
 
 def ras_server_device_bytes(s):

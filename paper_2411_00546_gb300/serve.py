@@ -22,11 +22,13 @@ def percentile(values, q):
     return v[lo] + (v[hi] - v[lo]) * (x - lo)
 
 
-def run_stream(requests, hbm_budget, max_active, opts=None, stream=None, keep_results=False):
+def run_stream(requests, hbm_budget, max_active, opts=None, stream=None, keep_results=False, graphs=False):
     """requests: list of (t_arrival_s, problem dict with host y_d), sorted by
     arrival. Returns a dict with per-request latency (s), status, stats, the
-    steps taken, the largest admitted set and (optionally) the results."""
+    steps taken, the largest admitted set and (optionally) the results.
+    graphs: CUDA graphs in the server's workspaces."""
     s = ras.ras_server_create(hbm_budget, max_active, opts, stream)
+    ras.ras_server_use_graphs(s, graphs)
     try:
         order = sorted(range(len(requests)), key=lambda i: requests[i][0])
         rid_of, arrival, done_at, status, stats, results = {}, {}, {}, {}, {}, {}
