@@ -247,6 +247,58 @@ def measure_cfg2(ras, torch, dev, stream):
                                         for r in rows)}
 
 
+def measure_paper_workload(ras, torch, dev, stream):
+    """The paper's model problem (Sec. 4): n = 450, phi = kappa (y^3 +
+    exp(kappa y)), kappa = 0.1, nu = 1e-6, mu = 1, f = 0, pbar = 1.3 mu
+    sin(10 pi x1) sin(10 pi x2), ybar and y_d from ras_manufacture at eps =
+    1e-15 (timed once). RASPEN_eps (eps 0.1 -> 1e-6, gamma 0.1) in mixed
+    precision on layouts sx x sy with overlap 2 (sx >= 6: local blocks of at
+    most 80 nodes per row); each solve timed after one warm-up solve, with
+    its distance to the manufactured pair (which solves the eps = 1e-15
+    system)."""
+    import numpy as np
+    from paper_2411_00546_gb300 import inputs
+    n, nu, mu, kappa = 450, 1e-6, 1.0, 0.1
+    o = ras.make_opts(tol=1e-10, inner_tol=1e-8, sigma=1.1, eps0=0.1, gamma=0.1, eps_min=1e-6,
+                      precision=ras.RAS_MIXED, kappa=kappa)
+    pbar = torch.tensor(inputs.yd_manufactured_paper(n, mu, 5), dtype=torch.float64, device=dev)
+    ybar = torch.zeros_like(pbar)
+    yd = torch.zeros_like(pbar)
+    rows = []
+    t_make = None
+    for sx, sy in ((6, 6), (9, 9), (10, 10), (15, 15), (6, 2), (9, 2), (15, 2)):
+        h = ras.ras_create(n, sx, sy, 2, ras.RAS_PHI_KAPPA, nu, mu, yd, None, o, stream=stream.cuda_stream)
+        if t_make is None:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ras.ras_manufacture(h, pbar, 1e-15, ybar, yd)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            t_make = a.elapsed_time(b)
+        y = torch.zeros_like(pbar)
+        p = torch.zeros_like(pbar)
+        for rep in range(2):
+            with torch.cuda.stream(stream):
+                y.zero_()
+                p.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rc, st = ras.ras_raspen_solve(h, y, p, check=False)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+        ras.ras_destroy(h)
+        yn, pn, ybn, pbn = (t.cpu().numpy() for t in (y, p, ybar, pbar))
+        rows.append({"layout": "%dx%d" % (sx, sy), "status": rc, "outer": st.outer_its,
+                     "gmres_per_outer": round(st.gmres_its / max(st.outer_its, 1), 1),
+                     "inner_its_sum": st.inner_its_sum, "ms": round(a.elapsed_time(b), 2),
+                     "dist_y": float(np.abs(yn - ybn).max() / np.abs(ybn).max()),
+                     "dist_p": float(np.abs(pn - pbn).max() / np.abs(pbn).max())})
+    return {"workload": "Sec. 4 model problem, n=450, kappa (y^3 + exp(kappa y)), nu=1e-6, mu=1, f=0, "
+                        "manufactured pbar (k=5), eps 0.1->1e-6, overlap 2, mixed precision",
+            "manufacture_ms": t_make, "ybar_max": float(ybar.abs().max()), "yd_max": float(yd.abs().max()),
+            "rows": rows}
+
+
 def measure_sweeps(ras, torch, dev, stream):
     """Sensitivity studies in mixed precision. Weak scaling: s x s subdomains
     of 50^2 nodes (n = 50 s, overlap 2, s = 2..11), RASPEN and Newton_RAS with
@@ -387,6 +439,7 @@ def parse_args():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cfg2", action="store_true")
     ap.add_argument("--no-sweeps", action="store_true")
+    ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",
                     help="GMRES cycles step by step (every kernel visible to a profiler's launch list)")
     ap.add_argument("--serve-requests", type=int, default=32)
@@ -763,6 +816,9 @@ def main():
     sweeps = None
     if rank == 0 and not args.no_sweeps:
         sweeps = measure_sweeps(ras, torch, dev, stream)
+    paper = None
+    if rank == 0 and not args.no_paper:
+        paper = measure_paper_workload(ras, torch, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -802,7 +858,7 @@ def main():
                                            "cycles as CUDA graphs" % (args.steps, prof_ms / args.steps),
                           "kernels": kernels, "kernel_rooflines": kernel_rooflines,
                           "uneven_batch": batch, "serving": serving, "methods": methods, "n255_family": cfg2,
-                          "sweeps": sweeps,
+                          "sweeps": sweeps, "paper_workload": paper,
                           "autotune": autotune,
                           "y_max": float(np.abs(y_mixed).max()),
                           "p_max": float(np.abs(p_mixed).max())},

@@ -75,7 +75,8 @@ typedef struct {
     double eps_min;        /* target smoothing parameter                     */
     int    kmax_outer_raspen;   /* 50  */
     int    kmax_outer_newton;   /* 200 */
-    int    kmax_inner;          /* 100 */
+    int    kmax_inner;          /* 100; a local solve stopped there keeps its
+                                   iterate (Alg. 1) and counts as a local failure */
     int    max_halvings;        /* 20: backtracking halvings per step         */
     int    gmres_restart;       /* 30  */
     int    gmres_maxit;         /* 1000 total Krylov steps per linear solve    */
@@ -102,7 +103,10 @@ typedef struct {
     long long inner_its_sum;  /* sum over subdomains and evaluations         */
     int    halvings;       /* backtracking halvings, all levels               */
     int    exhausted;      /* steps taken after max_halvings failed halvings  */
-    int    local_failures; /* local solves that ended with a negative status  */
+    int    local_failures; /* local solves that ended with a negative status:
+                              kmax_inner reached (the evaluation goes on with
+                              the iterate), or non-finite / singular (the call
+                              fails with that status)                          */
     double res0;           /* ||F(x0)|| (Newton_RAS) or ||RASPEN F(x0)||       */
     double res;            /* final norm of the same quantity                 */
     double eps_final;      /* smoothing parameter of the final iterate        */
@@ -357,6 +361,24 @@ long long ras_launch_count(void);
 #define RAS_K_COUNT      9
 int ras_profile(ras_problem* h, int enable);
 int ras_profile_read(ras_problem* h, int kind, double* ms, long long* launches, double* work);
+
+/* The manufactured solution of the paper's model problem (Sec. 4): for the
+ * adjoint pbar (device, n*n), the state ybar solves the state equation
+ * F_y(ybar, pbar, eps) = A y + phi(y) - f + (1/nu)(pbar + mu P_eps(-pbar/mu))
+ * = 0 (damped Newton from y = 0, each step by conjugate gradients on the
+ * symmetric positive definite A + diag(phi'(y)); phi must be increasing), and
+ * y_d = -A pbar - phi'(ybar) pbar + ybar, so that (ybar, pbar) solves the
+ * optimality system at eps. The handle's y_d is replaced by it (its phi, nu,
+ * mu, kappa and f are used); ybar and y_d are also written to y_out and
+ * yd_out (device, n*n, either may be NULL). The paper's run: phi =
+ * RAS_PHI_KAPPA, kappa 0.1, nu 1e-6, mu 1, f = 0, pbar = 1.3 mu sin(10 pi
+ * x1) sin(10 pi x2), eps = 1e-15. Newton stops at ||F_y|| <= 1e-14 of its
+ * value at y = 0, or when no step lowers it any more below 1e-9 of it
+ * (rounding level); conjugate gradients run to 1e-10 relative residual.
+ * Single-problem handles only; RAS_EINVAL for eps <= 0, RAS_ENOCONV if
+ * Newton stalls above that level or takes more than 100 steps,
+ * RAS_ENONFINITE on a non-finite residual. */
+int ras_manufacture(ras_problem* h, const double* pbar, double eps, double* y_out, double* yd_out);
 
 /* CUDA-graph execution (not part of the paper's method; default on).
  * Every Arnoldi step (the operator, the CGS2 products, the Givens update of

@@ -773,7 +773,10 @@ int evaluation_results(ras_problem* h, const std::vector<double>& pstart, ras_st
         exh[p] += ls[i].exhausted;
         if (ls[i].status < 0) {
             ++fails[p];
-            worst = std::min(worst, ls[i].status);
+            // Alg. 1 stopped at kmax_inner returns its iterate: the
+            // evaluation goes on with it (counted in local_failures); a
+            // non-finite residual or a singular block ends it
+            if (ls[i].status != ras::ST_ENOCONV) worst = std::min(worst, ls[i].status);
         }
     }
     h->jvp_ready = (worst >= 0);
@@ -1568,6 +1571,106 @@ int need_single(ras_problem* h) {
     return RAS_OK;
 }
 
+// ------------------------------------------------- the paper's model problem
+// Dot product of two vectors of problem 0 (whole segment), read to the host.
+int seg_dot_host(ras_problem* h, const double* a, const double* b, double& out) {
+    const ras::SegGrid g = seg_grid(h, 2);
+    CK(ras::launch_seg_dot(h->st, g, h->d_segs, a, h->L, 1, b, h->partials));
+    CK(ras::launch_seg_reduce(h->st, 1, g.nbps, 1, h->partials, h->scal));
+    CK(cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    TRY(sync(h));
+    out = h->h_scal[0];
+    return RAS_OK;
+}
+
+// F_y at (y + alpha d_y, p) into F (p-plane of F set to zero) and ||F_y||.
+int state_residual(ras_problem* h, const double* x, const double* d, double alpha, double eps, double* F,
+                   double& nrm) {
+    const long long N = plane(h, 0);
+    CK(ras::launch_residual_global(h->st, h->probs[0], x, x + N, d, d ? d + N : nullptr, alpha, eps, F, F + N,
+                                   h->partials, 0));
+    CK(cudaMemsetAsync(F + N, 0, N * sizeof(double), h->st));
+    double s2 = 0.0;
+    TRY(seg_dot_host(h, F, F, s2));
+    nrm = std::sqrt(s2);
+    return RAS_OK;
+}
+
+// Sec. 4: ybar solves the state equation F_y(ybar, pbar, eps) = 0 (damped
+// Newton; each step by conjugate gradients on A + diag(phi'(y)), symmetric
+// positive definite for increasing phi), then y_d = -A pbar - phi'(ybar) pbar
+// + ybar, so that F(ybar, pbar, eps) = 0 with that y_d.
+int manufacture_internal(ras_problem* h, const double* pbar, double eps, double* y_out, double* yd_out) {
+    Range range("ras: manufactured solution");
+    const long long N = plane(h, 0);
+    const ras::SegGrid g = seg_grid(h, 2);
+    double *X = h->X, *F = h->F, *D = h->Dv, *R = h->T1, *Pc = h->T2, *Q = h->T3;
+    CK(cudaMemsetAsync(X, 0, N * sizeof(double), h->st));
+    CK(cudaMemcpyAsync(X + N, pbar, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    double nrm = 0.0;
+    TRY(state_residual(h, X, nullptr, 0.0, eps, F, nrm));
+    const double nrm0 = nrm;
+    constexpr double RTOL = 1e-14, CG_RTOL = 1e-10;
+    for (int k = 0;; ++k) {
+        if (!std::isfinite(nrm)) return fail(h, RAS_ENONFINITE, "state residual not finite");
+        if (nrm <= RTOL * nrm0) break;
+        if (k >= 100) return fail(h, RAS_ENOCONV, "state solve did not converge in 100 Newton steps");
+        CK(ras::launch_coef_global(h->st, h->probs[0], X, X + N, eps, h->coefG));
+        // conjugate gradients for (A + diag phi'(y)) d_y = -F_y; every vector's p-plane stays zero
+        CK(cudaMemsetAsync(D, 0, 2 * N * sizeof(double), h->st));
+        CK(ras::launch_seg_scale(h->st, g, h->d_segs, F, nullptr, -1.0, R));
+        CK(cudaMemcpyAsync(Pc, R, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        double rr = 0.0;
+        TRY(seg_dot_host(h, R, R, rr));
+        const double rr0 = rr;
+        for (int it = 0; it < 100000 && rr > CG_RTOL * CG_RTOL * rr0; ++it) {
+            CK(ras::launch_jacvec_global(h->st, h->probs[0], h->coefG, Pc, Pc + N, Q, Q + N));
+            CK(cudaMemsetAsync(Q + N, 0, N * sizeof(double), h->st));
+            double pq = 0.0;
+            TRY(seg_dot_host(h, Pc, Q, pq));
+            if (!(pq > 0.0)) return fail(h, RAS_ENONFINITE, "state Jacobian not positive definite");
+            const double a = rr / pq;
+            CK(ras::launch_seg_add_scaled(h->st, g, h->d_segs, D, Pc, a, D));
+            CK(ras::launch_seg_add_scaled(h->st, g, h->d_segs, R, Q, -a, R));
+            double rn = 0.0;
+            TRY(seg_dot_host(h, R, R, rn));
+            const double b = rn / rr;
+            rr = rn;
+            CK(ras::launch_seg_add_scaled(h->st, g, h->d_segs, R, Pc, b, Pc));
+        }
+        // backtracking on ||F_y||
+        double alpha = 1.0;
+        bool moved = false;
+        for (int hh = 0; hh < 40; ++hh) {
+            double nt = 0.0;
+            TRY(state_residual(h, X, D, alpha, eps, h->Ov, nt));
+            if (nt <= (1.0 - 1e-4 * alpha) * nrm) {
+                CK(ras::launch_seg_add_scaled(h->st, g, h->d_segs, X, D, alpha, X));
+                CK(cudaMemcpyAsync(F, h->Ov, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+                nrm = nt;
+                moved = true;
+                break;
+            }
+            alpha *= 0.5;
+        }
+        if (!moved) {
+            if (nrm <= 1e-9 * nrm0) break;   // rounding level
+            return fail(h, RAS_ENOCONV, "state solve stalled");
+        }
+    }
+    // y_d = -(A pbar + phi'(ybar) pbar - ybar): minus F_p at y_d = 0
+    CK(cudaMemsetAsync(h->yd, 0, N * sizeof(double), h->st));
+    CK(ras::launch_residual_global(h->st, h->probs[0], X, X + N, nullptr, nullptr, 0.0, eps, F, F + N, h->partials,
+                                   0));
+    CK(ras::launch_seg_scale(h->st, g, h->d_segs, F, nullptr, -1.0, R));
+    CK(cudaMemcpyAsync(h->yd, R + N, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    if (y_out) CK(cudaMemcpyAsync(y_out, X, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    if (yd_out) CK(cudaMemcpyAsync(yd_out, h->yd, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    h->jvp_ready = false;
+    return sync(h);
+}
+
+
 }  // namespace
 
 // ===================================================================== C ABI
@@ -1992,6 +2095,12 @@ int ras_set_state(ras_problem* h, const ras_state* st) {
 int ras_autotune(ras_problem* h, ras_tuning* chosen, ras_tune_report* report) {
     if (!h) return RAS_EINVAL;
     return autotune_internal(h, chosen, report);
+}
+
+int ras_manufacture(ras_problem* h, const double* pbar, double eps, double* y_out, double* yd_out) {
+    if (!h || !pbar || !(eps > 0) || !std::isfinite(eps)) return RAS_EINVAL;
+    TRY(need_single(h));
+    return manufacture_internal(h, pbar, eps, y_out, yd_out);
 }
 
 int ras_use_graphs(ras_problem* h, int enable) {

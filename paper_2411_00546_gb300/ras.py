@@ -135,6 +135,7 @@ _SIGS = {
     "ras_get_state": (_I, [_P, ctypes.POINTER(ras_state)]),
     "ras_set_state": (_I, [_P, ctypes.POINTER(ras_state)]),
     "ras_use_graphs": (_I, [_P, _I]),
+    "ras_manufacture": (_I, [_P, _P, _D, _P, _P]),
     "ras_autotune": (_I, [_P, ctypes.POINTER(ras_tuning), ctypes.POINTER(ras_tune_report)]),
     "ras_get_tuning": (_I, [_P, ctypes.POINTER(ras_tuning)]),
     "ras_set_tuning": (_I, [_P, ctypes.POINTER(ras_tuning)]),
@@ -361,6 +362,13 @@ def ras_get_state(h):
 
 def ras_set_state(h, st):
     return h._check(lib().ras_set_state(h.ptr, ctypes.byref(st)))
+
+
+def ras_manufacture(h, pbar, eps=1e-15, y_out=None, yd_out=None):
+    """Sec. 4's manufactured solution for the adjoint pbar: sets the handle's
+    y_d and writes ybar / y_d into y_out / yd_out (device tensors, optional)."""
+    nn = h.n * h.n
+    return h._check(lib().ras_manufacture(h.ptr, _ptr(pbar, nn), float(eps), _ptr(y_out, nn), _ptr(yd_out, nn)))
 
 
 def ras_use_graphs(h, enable):

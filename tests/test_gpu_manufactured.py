@@ -1,0 +1,73 @@
+"""The paper's model problem (Sec. 4) on the GPU: ras_manufacture's ybar and
+y_d against the oracle's construction, and RASPEN solves of that workload
+(phi = kappa (y^3 + exp(kappa y)), nu = 1e-6, mu = 1, eps_min = 1e-6) against
+the oracle in FP64 and mixed precision with equal counts."""
+import numpy as np
+import pytest
+
+from oracle import discretization as fd
+from oracle import pointwise as pw
+from oracle import ras as oras
+from oracle import solvers
+from oracle import workloads as wl
+from paper_2411_00546_gb300 import inputs
+from gpu_util import FP64_TOL, MIXED_TOL, rel_inf, to_dev, zeros
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+from paper_2411_00546_gb300 import ras  # noqa: E402
+
+PAPER = dict(phi=ras.RAS_PHI_KAPPA, nu=1e-6, mu=1.0, kappa=0.1)
+
+
+def _handle(n, s, prec, yd=None):
+    o = ras.make_opts(tol=1e-10, inner_tol=1e-8, sigma=1.1, eps0=0.1, gamma=0.1, eps_min=1e-6, precision=prec,
+                      kappa=PAPER["kappa"])
+    yd = zeros(n) if yd is None else yd
+    return ras.ras_create(n, s, s, 2, PAPER["phi"], PAPER["nu"], PAPER["mu"], yd, None, o)
+
+
+@pytest.mark.parametrize("n", [63, 90])
+def test_manufactured_solution_matches_oracle(n):
+    pbar = inputs.yd_manufactured_paper(n, PAPER["mu"], 5)
+    Y, yd = wl.manufactured(pbar, n)
+    h = _handle(n, 3, ras.RAS_FP64)
+    try:
+        yb, ydg = zeros(n), zeros(n)
+        ras.ras_manufacture(h, to_dev(pbar), 1e-15, yb, ydg)
+        assert rel_inf(yb.cpu().numpy(), Y) <= FP64_TOL
+        assert rel_inf(ydg.cpu().numpy(), yd) <= FP64_TOL
+        # the handle now carries that y_d: F(ybar, pbar) is at rounding level
+        Fy, Fp = zeros(n), zeros(n)
+        nrm = ras.ras_residual(h, yb, to_dev(pbar), 1e-15, Fy, Fp)
+        prob = fd.Problem(n, pw.PHI_KAPPA, PAPER["nu"], PAPER["mu"], yd, kappa=PAPER["kappa"])
+        assert nrm <= 1e-12 * fd.residual_floor_norm(prob, Y, pbar, 1e-15)
+    finally:
+        ras.ras_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def n63_paper():
+    n = 63
+    pbar = inputs.yd_manufactured_paper(n, PAPER["mu"], 5)
+    Y, yd = wl.manufactured(pbar, n)
+    prob = fd.Problem(n, pw.PHI_KAPPA, PAPER["nu"], PAPER["mu"], yd, kappa=PAPER["kappa"])
+    o = oras.Options(tol=1e-10, inner_tol=1e-8, sigma=1.1, eps0=0.1, gamma=0.1, eps_min=1e-6)
+    return n, yd, solvers.raspen(prob, 3, 3, 2, o)
+
+
+@pytest.mark.parametrize("prec,tol", [(ras.RAS_FP64, FP64_TOL), (ras.RAS_MIXED, MIXED_TOL)])
+def test_paper_workload_raspen_solve(n63_paper, prec, tol):
+    n, yd, ref = n63_paper
+    h = _handle(n, 3, prec, to_dev(yd))
+    try:
+        y, p = zeros(n), zeros(n)
+        rc, st = ras.ras_raspen_solve(h, y, p)
+        assert rel_inf(y.cpu().numpy(), ref.Y, ref.P) <= tol
+        assert rel_inf(p.cpu().numpy(), ref.P, ref.Y) <= tol
+        assert st.outer_its == ref.outer
+        assert st.inner_its_sum == sum(sum(i) for i in ref.inner_its)
+    finally:
+        ras.ras_destroy(h)
