@@ -48,7 +48,7 @@ extern "C" {
 #define RAS_ENONFINITE  -6   /* NaN or Inf in a residual                       */
 #define RAS_ETIMEOUT    -7   /* a bounded device-side wait ran out; the kernel
                                 gave up cleanly and the context stays usable   */
-#define RAS_ENOTIMPL    -8   /* not available in this build                    */
+#define RAS_ENOTIMPL    -8   /* not available in this library version          */
 #define RAS_ECUDA       -9   /* CUDA runtime error                             */
 #define RAS_ESTATE     -10   /* call needs state that is not there (e.g. a JVP
                                  before any ras_apply)                          */
@@ -134,8 +134,8 @@ int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu
                const double* y_d, const double* f, const ras_opts* o,
                void* stream, ras_problem** out);
 
-/* A batch of independent problems in one handle (spec: many problems of
- * uneven grid size in one launch per sweep). Each entry describes one problem
+/* A batch of independent problems in one handle (many problems of uneven
+ * grid size, one launch per sweep step for all of them). Each entry describes one problem
  * exactly like the arguments of ras_create; y_d and f are device pointers,
  * copied. All problems share the options. The subdomains of all problems form
  * one table: every step of a RASPEN-function evaluation (Alg. 3) is one launch
@@ -206,8 +206,8 @@ int ras_batch_raspen_solve(ras_problem* h, double* const* y, double* const* p, r
  *   finished), freeing its storage; RAS_EINVAL for an unknown id. Between
  *   steps only (the server is not thread-safe).
  * ras_server_device_bytes: device bytes held now (workspace + slots).
- * The paper has no serving loop: this is the benchmark spec's continuous-batching
- * use of Alg. 2 and Alg. 3 over independent problems. */
+ * The paper has no serving loop: this is a continuous-batching use of Alg. 2
+ * and Alg. 3 over independent problems. */
 typedef struct ras_server ras_server;
 int ras_server_create(size_t hbm_budget, int max_active, const ras_opts* o, void* stream, ras_server** out);
 int ras_server_request_bytes(const ras_problem_desc* d, const ras_opts* o, size_t* slot_bytes,

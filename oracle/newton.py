@@ -1,7 +1,7 @@
 """Damped Newton with eps-continuation and relaxed backtracking (Alg. 1, Sec. 4.1).
 Test infrastructure.
 
-Readings taken where the paper leaves a choice (each is listed in the design doc):
+Readings taken where the paper leaves a choice:
 
 * Norm: the Euclidean norm of the residual vector, both fields together.
 * Stop test: ||F_{eps_k}(x^k)|| <= max(tol, tol ||F_{eps_0}(x^0)||) ends the
