@@ -79,3 +79,18 @@ def test_eps_solutions_approach_the_manufactured_pair():
         r = solvers.raspen(prob, 2, 2, 2, o)
         errs.append(np.abs(r.P - pbar).max() / np.abs(pbar).max())
     assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-3, errs
+
+
+def test_raspen_reaches_the_manufactured_pair_at_the_paper_eps():
+    """At eps_min = 1e-15 the manufactured (ybar, pbar) is the exact discrete
+    solution: a full RASPEN solve from x0 = 0 (the paper's continuation
+    eps0 = 1, gamma = 1/5) must reproduce it."""
+    n = 31
+    pbar = inputs.yd_manufactured_paper(n, 1.0, 5)
+    Y, yd = wl.manufactured(pbar, n)
+    prob = fd.Problem(n, pw.PHI_KAPPA, 1e-6, 1.0, yd, kappa=0.1)
+    o = oras.Options(tol=1e-10, inner_tol=1e-8, sigma=1.1, eps0=1.0, gamma=0.2, eps_min=1e-15)
+    r = solvers.raspen(prob, 2, 2, 2, o)
+    assert r.status == 0
+    assert np.abs(r.Y - Y).max() <= 1e-10 * np.abs(Y).max()
+    assert np.abs(r.P - pbar).max() <= 1e-10 * np.abs(pbar).max()
