@@ -71,3 +71,32 @@ def test_paper_workload_raspen_solve(n63_paper, prec, tol):
         assert st.inner_its_sum == sum(sum(i) for i in ref.inner_its)
     finally:
         ras.ras_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def n63_paper_tiny_eps():
+    n = 63
+    pbar = inputs.yd_manufactured_paper(n, PAPER["mu"], 5)
+    Y, yd = wl.manufactured(pbar, n)
+    prob = fd.Problem(n, pw.PHI_KAPPA, PAPER["nu"], PAPER["mu"], yd, kappa=PAPER["kappa"])
+    o = oras.Options(tol=1e-10, inner_tol=1e-8, sigma=1.1, eps0=1.0, gamma=0.2, eps_min=1e-15)
+    return n, yd, Y, pbar, solvers.raspen(prob, 3, 3, 2, o)
+
+
+@pytest.mark.parametrize("prec,tol", [(ras.RAS_FP64, FP64_TOL), (ras.RAS_MIXED, MIXED_TOL)])
+def test_paper_workload_at_the_paper_eps(n63_paper_tiny_eps, prec, tol):
+    """eps_min = 1e-15 with the paper's continuation (eps0 = 1, gamma = 1/5):
+    the oracle's solve, which is the manufactured pair to rounding level."""
+    n, yd, Y, pbar, ref = n63_paper_tiny_eps
+    o = ras.make_opts(tol=1e-10, inner_tol=1e-8, sigma=1.1, eps0=1.0, gamma=0.2, eps_min=1e-15, precision=prec,
+                      kappa=PAPER["kappa"])
+    h = ras.ras_create(n, 3, 3, 2, PAPER["phi"], PAPER["nu"], PAPER["mu"], to_dev(yd), None, o)
+    try:
+        y, p = zeros(n), zeros(n)
+        rc, st = ras.ras_raspen_solve(h, y, p)
+        assert rel_inf(y.cpu().numpy(), ref.Y, ref.P) <= tol
+        assert rel_inf(p.cpu().numpy(), ref.P, ref.Y) <= tol
+        assert st.outer_its == ref.outer
+        assert st.inner_its_sum == sum(sum(i) for i in ref.inner_its)
+    finally:
+        ras.ras_destroy(h)
