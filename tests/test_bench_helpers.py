@@ -63,3 +63,15 @@ def test_reference_arm_prints_one_json_line():
     assert line["value"] > 0 and line["unit"] == "solves/s" and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_parallel_cpu_sample_scales_the_throughput():
+    s = bench.run_cpu_sample_parallel("n63", 2)
+    assert s["cores"] == 2 and s["subdomains"] == 2
+    assert s["inner_its"] == 2 * s["single"]["inner_its"]
+    assert s["solve_s"] == pytest.approx(s["single"]["solve_s"] / 2, rel=1.0)
+    counts = {"inner_its_sum": 100, "evaluations": 2, "gmres_its": 10}
+    t_par = bench.cpu_solve_estimate(s, counts, 16)
+    t_one = bench.cpu_solve_estimate(s["single"], counts, 16)
+    assert 0 < t_par < t_one
+    assert bench.host_cores() >= 1
