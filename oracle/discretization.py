@@ -9,7 +9,7 @@ Grid functions are (n, n) float64 arrays indexed [j, i]: i is the x1 index
 
 The residual is the map F(x, eps) of Sec. 3.3 with x = (y, p):
 
-    F_y = A y + phi(y) - f + (1/nu) (p + mu P_eps(-p/mu))
+    F_y = A y + phi(y) - f + (1/nu) (p + mu P_eps(-p/mu))   (= A y + phi(y) - f - u_eps(p))
     F_p = A p + phi'(y) p - y + y_d
 
 and its Jacobian (Sec. 3.3)
@@ -77,7 +77,7 @@ def residual(prob, Y, P, eps, box=None):
     p = P[y0:y1, x0:x1]
     ph, dph, _ = prob.phi(y)
     Fy = (apply_A(prob, Y, box) + ph - prob.f[y0:y1, x0:x1]
-          + (1.0 / prob.nu) * (p + prob.mu * pw.P_eps(-p / prob.mu, eps)))
+          - pw.u_eps(p, eps, prob.nu, prob.mu))
     Fp = apply_A(prob, P, box) + dph * p - y + prob.y_d[y0:y1, x0:x1]
     return Fy, Fp
 
@@ -106,7 +106,7 @@ def jacobian_coefficients(prob, y, p, eps):
     """Nodewise entries of the Jacobian (Sec. 3.3): diagonal addend phi'(y),
     (1,2) block (1/nu)(1 - P_eps'(-p/mu)), (2,1) block phi''(y) p - 1."""
     _, dph, d2ph = prob.phi(y)
-    b = (1.0 / prob.nu) * (1.0 - pw.dP_eps(-p / prob.mu, eps))
+    b = (1.0 / prob.nu) * pw.one_minus_dP_eps(-p / prob.mu, eps)
     c = d2ph * p - 1.0
     return dph, b, c
 

@@ -81,7 +81,7 @@ def residual(prob, Y, P, eps, box=None):
     p = _cut(P, box)
     ph, dph, _ = prob.phi(y)
     Fy = (apply_A(prob, Y, box) + ph - _cut(prob.f, box)
-          + (1.0 / prob.nu) * (p + prob.mu * pw.P_eps(-p / prob.mu, eps)))
+          - pw.u_eps(p, eps, prob.nu, prob.mu))
     Fp = apply_A(prob, P, box) + dph * p - y + _cut(prob.y_d, box)
     return Fy, Fp
 
@@ -106,7 +106,7 @@ def jacvec(prob, Y, P, eps, dY, dP, box=None):
     y = _cut(Y, box)
     p = _cut(P, box)
     _, dph, d2ph = prob.phi(y)
-    b = (1.0 / prob.nu) * (1.0 - pw.dP_eps(-p / prob.mu, eps))
+    b = (1.0 / prob.nu) * pw.one_minus_dP_eps(-p / prob.mu, eps)
     c = d2ph * p - 1.0
     dy = _cut(dY, box)
     dp = _cut(dP, box)
@@ -131,7 +131,7 @@ def jacobian_matrix(prob, Y, P, eps, box=None):
     y = _cut(Y, box).ravel()
     p = _cut(P, box).ravel()
     _, dph, d2ph = prob.phi(y)
-    b = (1.0 / prob.nu) * (1.0 - pw.dP_eps(-p / prob.mu, eps))
+    b = (1.0 / prob.nu) * pw.one_minus_dP_eps(-p / prob.mu, eps)
     c = d2ph * p - 1.0
     L = laplacian_matrix(prob.beta, wx, wy, wz)
     planar = sp.bmat([[L + sp.diags(dph), sp.diags(b)], [sp.diags(c), L + sp.diags(dph)]]).tocsr()

@@ -38,6 +38,48 @@ def test_dP_eps_is_derivative_of_P_eps(eps):
         assert abs(g - ref) <= 4e-16, (x, eps, g, ref)
 
 
+def _rel_ok(got, ref, ulps):
+    return abs(got - ref) <= ulps * 2.0 ** -53 * abs(ref) + 1e-300
+
+
+@pytest.mark.parametrize("eps", EPSS)
+def test_P_eps_minus_id_full_relative_accuracy(eps):
+    """P_eps(x) - x against the 50-digit definition, to a few ulp of itself
+    (the printed difference p + mu P_eps(-p/mu) misses this by 2^-53/eps)."""
+    got = pw.P_eps_minus_id(XS, eps)
+    for x, g in zip(XS, got):
+        ref = float(_P_mp(x, eps) - mpmath.mpf(x))
+        assert _rel_ok(g, ref, 16), (x, eps, g, ref)
+
+
+@pytest.mark.parametrize("eps", EPSS)
+def test_one_minus_dP_eps_full_relative_accuracy(eps):
+    """1 - P_eps'(x) against 1 minus the 50-digit derivative of the definition."""
+    got = pw.one_minus_dP_eps(XS, eps)
+    for x, g in zip(XS, got):
+        ref = float(1 - mpmath.diff(lambda t: _P_mp(t, eps), mpmath.mpf(x)))
+        assert _rel_ok(g, ref, 16), (x, eps, g, ref)
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-6, 1e-15])
+@pytest.mark.parametrize("nu,mu", [(1e-4, 1e-3), (1e-6, 1e-2), (1e-6, 1.0)])
+def test_u_eps_full_relative_accuracy(eps, nu, mu):
+    """u = -(1/nu)(p + mu P_eps(-p/mu)) (Sec. 3.2) in 50 digits: the oracle's
+    control keeps a few ulp of relative accuracy also where |p| < mu, where it
+    is O(eps) and drives the state alone. The reference is taken at
+    p' = -mu fl(-p/mu), within one rounding of p: near |p| = mu, u is
+    ill-conditioned in p (condition ~ 1/|1 - |p|/mu|), which no evaluation
+    from FP64 data escapes."""
+    ps = mu * np.concatenate([np.linspace(-3, 3, 61), [-1e-7, 1e-7, 0.35, -0.999, 1.0000001]])
+    got = pw.u_eps(ps, eps, nu, mu)
+    for p, g in zip(ps, got):
+        X = mpmath.mpf(float(-p / mu))
+        M, N, E = (mpmath.mpf(float(v)) for v in (mu, nu, eps))
+        P = -M * X
+        ref = float(-(P + M * _P_mp(-P / M, E)) / N)
+        assert _rel_ok(g, ref, 24), (p, eps, g, ref)
+
+
 @pytest.mark.parametrize("eps", EPSS)
 def test_lemma5_properties(eps):
     x = np.linspace(-10, 10, 20001)

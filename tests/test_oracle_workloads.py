@@ -4,6 +4,7 @@ own dense Laplacian, the closed form of the eps -> 0 control (soft threshold),
 the construction's residual at rounding level, and convergence of the
 eps-solutions towards the manufactured pair as eps shrinks."""
 import numpy as np
+import pytest
 
 from oracle import discretization as fd
 from oracle import pointwise as pw
@@ -33,10 +34,16 @@ def test_state_solve_matches_dense_brute_force():
     Y, yd = wl.manufactured(pbar, n, nu=nu, mu=mu, kappa=kappa, eps=eps)
     A = _dense_laplacian(n)
     p = pbar.ravel()
-    # control at the adjoint, soft threshold plus smoothing: u = -(1/nu)(p + mu P_eps(-p/mu))
-    x = -p / mu
-    Peps = 2 * x / (np.sqrt((x + 1) ** 2 + eps) + np.sqrt((x - 1) ** 2 + eps))
-    rhs = -(1.0 / nu) * (p + mu * Peps)
+    # control at the adjoint, soft threshold plus smoothing: u = -(1/nu)(p + mu P_eps(-p/mu)),
+    # evaluated in 50 digits (in FP64 the printed difference loses 2^-53/eps where |p| < mu)
+    mpmath = pytest.importorskip("mpmath")
+    with mpmath.workdps(50):
+        def u_mp(pv):
+            P, M, E = mpmath.mpf(float(pv)), mpmath.mpf(mu), mpmath.mpf(eps)
+            x = -P / M
+            Pe = (mpmath.sqrt((x + 1) ** 2 + E) - mpmath.sqrt((x - 1) ** 2 + E)) / 2
+            return float(-(P + M * Pe) / mpmath.mpf(nu))
+        rhs = np.array([u_mp(v) for v in p])
     y = np.zeros(n * n)
     for _ in range(200):
         g = A @ y + kappa * (y ** 3 + np.exp(kappa * y)) - rhs
