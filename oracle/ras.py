@@ -158,19 +158,39 @@ def ras_apply(prob, Y, P, subs, opts, continuation, factor_at_solution=True, onl
     return RasState(Fy, Fp, locs, opts.eps_min)
 
 
+def local_jvp(prob, loc, eps_min, dY, dP):
+    """C_i'(x) d = -(R_i F'(x^(i)) P_i)^-1 R_i F'(x^(i)) d on the box of
+    subdomain i (one term of Alg. 4), written literally: the full product
+    R_i F'(x^(i)) d, then the local solve. Returns the two box fields."""
+    sub = loc.sub
+    vy, vp = fd.jacvec(prob, loc.Yi, loc.Pi, eps_min, dY, dP, sub.box)
+    z = loc.factor.solve(fd.interleave(vy, vp))
+    return fd.deinterleave(-z, sub.wx, sub.wy)
+
+
 def jvp(prob, state, dY, dP):
-    """Alg. 4 with the derivative of the local corrections, written literally."""
+    """Alg. 4: F_eps'(x) d = sum_i tilde P_i C_i'(x) d."""
     n = prob.n
     out_y = np.zeros((n, n))
     out_p = np.zeros((n, n))
     for loc in state.locals:
-        sub = loc.sub
-        vy, vp = fd.jacvec(prob, loc.Yi, loc.Pi, state.eps_min, dY, dP, sub.box)
-        z = loc.factor.solve(fd.interleave(vy, vp))
-        zy, zp = fd.deinterleave(-z, sub.wx, sub.wy)
-        out_y += dd.prolong_restricted(zy, sub, n)
-        out_p += dd.prolong_restricted(zp, sub, n)
+        zy, zp = local_jvp(prob, loc, state.eps_min, dY, dP)
+        out_y += dd.prolong_restricted(zy, loc.sub, n)
+        out_p += dd.prolong_restricted(zp, loc.sub, n)
     return out_y, out_p
+
+
+class SerialEngine:
+    """Alg. 3 and Alg. 4 over the subdomains one after another."""
+
+    def __init__(self, prob, subs, opts):
+        self.prob, self.subs, self.opts = prob, subs, opts
+
+    def apply(self, Y, P, continuation):
+        return ras_apply(self.prob, Y, P, self.subs, self.opts, continuation)
+
+    def jvp(self, state, dY, dP):
+        return jvp(self.prob, state, dY, dP)
 
 
 class LinearRas:

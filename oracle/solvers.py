@@ -47,13 +47,18 @@ class SolveResult:
         self.status = OK
 
 
-def raspen(prob, sx, sy, overlap, opts, Y0=None, P0=None):
+def raspen(prob, sx, sy, overlap, opts, Y0=None, P0=None, engine=None):
+    """Alg. 2. `engine` evaluates Alg. 3 (apply) and Alg. 4 (jvp); the default
+    runs the subdomains one after another, oracle.parallel.ParallelEngine
+    spreads them over processes with identical results."""
     n = prob.n
     subs = dd.subdomains(n, sx, sy, overlap)
+    if engine is None:
+        engine = ras.SerialEngine(prob, subs, opts)
     Y = np.zeros((n, n)) if Y0 is None else Y0.copy()
     P = np.zeros((n, n)) if P0 is None else P0.copy()
     out = SolveResult()
-    state = ras.ras_apply(prob, Y, P, subs, opts, continuation=True)
+    state = engine.apply(Y, P, True)
     out.inner_its.append(state.iterations)
     Fn = float(np.linalg.norm(_join(state.Fy, state.Fp)))
     out.norms.append(Fn)
@@ -62,7 +67,7 @@ def raspen(prob, sx, sy, overlap, opts, Y0=None, P0=None):
     while Fn > stop and k < opts.kmax_outer_raspen:
         def A(v):
             dY, dP = _split(v, n)
-            jy, jp = ras.jvp(prob, state, dY, dP)
+            jy, jp = engine.jvp(state, dY, dP)
             return _join(jy, jp)
         g = gmres(A, -_join(state.Fy, state.Fp), opts.gmres_restart, opts.gmres_rtol, opts.gmres_maxit)
         out.gmres_its.append(g.iterations)
@@ -70,7 +75,7 @@ def raspen(prob, sx, sy, overlap, opts, Y0=None, P0=None):
         Y = Y + dY
         P = P + dP
         k += 1
-        state = ras.ras_apply(prob, Y, P, subs, opts, continuation=False)
+        state = engine.apply(Y, P, False)
         out.inner_its.append(state.iterations)
         Fn = float(np.linalg.norm(_join(state.Fy, state.Fp)))
         out.norms.append(Fn)
