@@ -88,8 +88,19 @@ typedef struct {
     double kappa;               /* parameter of RAS_PHI_KAPPA, 0.1             */
     int    jvp_ir;              /* mixed: FP64 refinement corrections of every
                                    local solve inside the Jacobian action of
-                                   Alg. 4, 1 (0 = plain FP32 solves)            */
-    int    reserved;            /* must be 0                                   */
+                                   Alg. 4, 2 (0 = plain FP32 solves). One
+                                   correction leaves the action's relative
+                                   error near (cond(J_i) 2^-24)^2 ~ 1e-8, which
+                                   moves the final iterate's smaller field (y
+                                   beside p when the L1 control is inactive) by
+                                   about that much relative to its own size;
+                                   two bring it to FP64 rounding level      */
+    int    wait_test;           /* 0. 1 = test of the failure path: the first
+                                   streamed slab wait of every local solve
+                                   gives up at once, the copies already issued
+                                   are drained, and the call returns
+                                   RAS_ETIMEOUT; set it back to 0 with
+                                   ras_set_opts to go on with the handle    */
 } ras_opts;
 
 /* Counters of the last solve or RASPEN-function evaluation. */
@@ -475,23 +486,27 @@ int ras_set_tuning(ras_problem* h, const ras_tuning* t);
  * memory, or a latency-bound loop where an allocation's implicit device
  * synchronisation is not acceptable; ras_create allocates, so those callers
  * cannot use ras_residual.
- * Computes F(x, eps) of Sec. 3.3 at x = (y, p) exactly like ras_residual:
- * writes Fy, Fp (device n*n, either may be NULL) and, if norm_dev != NULL,
- * ||(Fy, Fp)||_2 to norm_dev[0] (device). y, p, y_d: device n*n; f device
- * n*n or NULL (= 0); phi, nu, mu, kappa as in ras_create / ras_opts; eps > 0.
+ * Computes F(x, eps) of Sec. 3.3 at x = (y, p) with the same expression as
+ * ras_residual (results agree to rounding; the norm's summation order
+ * differs): writes Fy, Fp (device n*n, either may be NULL) and, if
+ * norm_dev != NULL, ||(Fy, Fp)||_2 to norm_dev[0] (device). y, p, y_d: device
+ * n*n; f device n*n or NULL (= 0); phi, nu, mu, kappa as in ras_create /
+ * ras_opts; eps > 0.
  * The work is only enqueued on `stream` (cudaStream_t, NULL = legacy default
  * stream); results are ready when the stream reaches it.
  * Scratch: the norm's partial sums live in one fixed array inside the library
- * (2 doubles per grid row, RAS_STATIC_MAX_N rows, 128 KiB), which every GPU
- * that loads the library holds until the process exits. The first call on a
- * device looks up that array's device address with the device current; make
- * that first call before any stream capture. Every call writes all the
- * partials it later reads, so nothing has to start at zero; the array keeps
- * the last call's values. All calls share the array: calls whose GPU work
- * overlaps (other streams, other threads) race and give wrong norms.
+ * (1 double per grid row, RAS_STATIC_MAX_N rows, 64 KiB), which every GPU
+ * that loads the library holds until the process exits. Each call looks up
+ * that array's device address (cudaGetSymbolAddress, no allocation) in the
+ * current context, so it stays valid after cudaDeviceReset; the first call on
+ * a device may load the library's device code, so make it before any stream
+ * capture. Every call writes all the partials it later reads, so nothing has
+ * to start at zero; the array keeps the last call's values. All calls share
+ * the array: calls whose GPU work overlaps (other streams, other threads)
+ * race and give wrong norms.
  * Returns RAS_EINVAL for n < 2, n > RAS_STATIC_MAX_N, a bad phi, nu, mu or
- * eps, or a NULL y, p or y_d; RAS_ECUDA if a launch fails. No allocation of
- * any kind is made. */
+ * eps, or a NULL y, p or y_d; RAS_ECUDA if the lookup or a launch fails. No
+ * allocation of any kind is made. */
 #define RAS_STATIC_MAX_N 8192
 int ras_residual_static(int n, int phi, double nu, double mu, double kappa, double eps,
                         const double* y, const double* p, const double* y_d, const double* f,

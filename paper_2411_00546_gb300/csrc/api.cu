@@ -71,7 +71,8 @@ struct ras_problem {
     int gprec = -1;
     LocalState* ls = nullptr;
     int* d_active = nullptr;
-    int* d_err = nullptr;        // set by kernels whose bounded waits ran out
+    int* d_err = nullptr;        // [0]: set by kernels whose bounded waits ran out; [1]: opts.wait_test
+    int h_wait_test = 0;         // host copy of opts.wait_test (source of the copy into d_err[1])
     int* h_active = nullptr;     // pinned
     int* d_mask = nullptr;       // per-problem masks: row 0 [0, nprob) GMRES/JVP, row 1 outer loop
     double* d_pstart = nullptr;  // per-problem eps start of a RASPEN-function evaluation
@@ -284,7 +285,7 @@ int validate_opts(ras_problem* h, const ras_opts& o) {
         o.kmax_outer_newton < 0 || o.kmax_inner < 0 || o.max_halvings < 0 || o.gmres_restart < 1 ||
         o.gmres_restart > 30 || o.gmres_maxit < 1 || !(o.gmres_rtol > 0) || !(o.floor_factor >= 0) ||
         (o.precision != RAS_FP64 && o.precision != RAS_MIXED) || o.ir_max < 0 || !(o.ir_rtol >= 0) ||
-        !std::isfinite(o.kappa) || o.jvp_ir < 0 || o.jvp_ir > 8)
+        !std::isfinite(o.kappa) || o.jvp_ir < 0 || o.jvp_ir > 8 || o.wait_test < 0 || o.wait_test > 1)
         return fail(h, RAS_EINVAL,
                     "invalid options (need tol, inner_tol, eps0, gamma, eps_min > 0, eps0 >= eps_min, "
                     "gamma <= 1, sigma >= 1, 1 <= gmres_restart <= 30, precision RAS_FP64|RAS_MIXED)");
@@ -323,6 +324,14 @@ int alloc_factor_pools(ras_problem* h) {
 int sync(ras_problem* h) {
     CK(cudaStreamSynchronize(h->st));
     if (h->prof_on && h->prof_recs.size() > 2048) prof_flush(h);
+    return RAS_OK;
+}
+
+// Copy opts.wait_test into d_err[1], where the streamed solves read it.
+int push_wait_test(ras_problem* h) {
+    if (!h->d_err) return RAS_OK;
+    h->h_wait_test = h->o.wait_test;
+    CK(cudaMemcpyAsync(h->d_err + 1, &h->h_wait_test, sizeof(int), cudaMemcpyHostToDevice, h->st));
     return RAS_OK;
 }
 
@@ -1697,8 +1706,8 @@ int ras_default_opts(ras_opts* o) {
     o->ir_max = 6;
     o->ir_rtol = 1e-12;
     o->kappa = 0.1;
-    o->jvp_ir = 1;
-    o->reserved = 0;
+    o->jvp_ir = 2;
+    o->wait_test = 0;
     return RAS_OK;
 }
 
@@ -1807,9 +1816,10 @@ int ensure_pools(ras_problem* h, bool own_data) {
     TRY(ensure(h, &h->ls, h->nsub));
     TRY(ensure(h, &h->d_active, 1));
     if (!h->d_err) {
-        TRY(dalloc(h, &h->d_err, 1));
-        CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st));
+        TRY(dalloc(h, &h->d_err, 2));
+        CK(cudaMemsetAsync(h->d_err, 0, 2 * sizeof(int), h->st));
     }
+    TRY(push_wait_test(h));
     TRY(ensure(h, &h->d_mask, 2 * count));
     TRY(ensure(h, &h->d_tab, (size_t)4 * (ras::VEC_BLOCKS + count)));
     TRY(ensure(h, &h->d_nbps, (size_t)4 * count));
@@ -1936,10 +1946,22 @@ int ras_set_eps(ras_problem* h, double eps_min) {
 int ras_set_opts(ras_problem* h, const ras_opts* o) {
     if (!h || !o) return RAS_EINVAL;
     TRY(validate_opts(h, *o));
+    {
+        // only the failure-path test switch changed: the factors stay valid
+        ras_opts t = *o;
+        t.wait_test = h->o.wait_test;
+        if (std::memcmp(&t, &h->o, sizeof(ras_opts)) == 0) {
+            h->o.wait_test = o->wait_test;
+            TRY(push_wait_test(h));
+            TRY(sync(h));
+            return RAS_OK;
+        }
+    }
     const bool kappa_changed = (o->kappa != h->o.kappa);
     h->o = *o;
     h->jvp_ready = false;
     ++h->gen;
+    TRY(push_wait_test(h));
     TRY(alloc_factor_pools(h));
     if (h->own_factors) {
         fill_pointers(h);

@@ -64,7 +64,7 @@ __device__ __forceinline__ LocalView make_view(const SubDev& s, const ProbDev& P
 __device__ void local_residual(const LocalView& V, const ProbDev& P, double eps, double* out,
                                double& nrm2, double& flr2, double* red) {
     const int wx = V.wx, nn = wx * V.wy;
-    const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu, imu = 1.0 / P.mu;
+    const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu, imu = 1.0 / P.mu, munu = P.mu / P.nu;
     double a = 0.0, b = 0.0;
     for (int q = threadIdx.x; q < nn; q += NT) {
         const int lx = q % wx, ly = q / wx;
@@ -76,11 +76,13 @@ __device__ void local_residual(const LocalView& V, const ProbDev& P, double eps,
         double ph, d1, d2;
         phi_eval(P.phi, P.kappa, yc, ph, d1, d2);
         const double fv = P.f ? P.f[g] : 0.0;
-        const double pe_ = P_eps(-pc * imu, eps);
-        const double Fy = beta * (4.0 * yc - yw - ye - ys - yn) + ph - fv + inu * (pc + mu * pe_);
+        // -u = (mu/nu)(P_eps(x) - x), x = -p/mu (control of Sec. 3.2)
+        const double xq = -pc * imu;
+        const double dq = P_eps_minus_id(xq, eps);
+        const double Fy = beta * (4.0 * yc - yw - ye - ys - yn) + ph - fv + munu * dq;
         const double Fp = beta * (4.0 * pc - pw - pe - ps - pn) + d1 * pc - yc + P.yd[g];
         const double My = beta * (4.0 * fabs(yc) + fabs(yw) + fabs(ye) + fabs(ys) + fabs(yn)) + fabs(ph) +
-                          fabs(fv) + inu * (fabs(pc) + mu * fabs(pe_));
+                          fabs(fv) + inu * (fabs(pc) + mu * fabs(xq + dq));
         const double Mp = beta * (4.0 * fabs(pc) + fabs(pw) + fabs(pe) + fabs(ps) + fabs(pn)) +
                           fabs(d1 * pc) + fabs(yc) + fabs(P.yd[g]);
         if (out) {
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_local_factor(int nsub, int max
             double ph, d1, d2;
             phi_eval(P.phi, P.kappa, y, ph, d1, d2);
             ca[q] = d1;
-            cb[q] = inu * (1.0 - dP_eps(-p / mu, eps));
+            cb[q] = inu * one_minus_dP_eps(-p / mu, eps);
             cc[q] = d2 * p - 1.0;
         }
     }
@@ -566,7 +568,7 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub
             double ph, d1, d2;
             phi_eval(P.phi, P.kappa, y, ph, d1, d2);
             ca[q] = d1;
-            cb[q] = inu * (1.0 - dP_eps(-p / mu, eps));
+            cb[q] = inu * one_minus_dP_eps(-p / mu, eps);
             cc[q] = d2 * p - 1.0;
         }
     }
@@ -860,7 +862,7 @@ __global__ void __launch_bounds__(1024, 1) k_local_factor_wide(int nsub, const S
             double ph, d1, d2;
             phi_eval(P.phi, P.kappa, y, ph, d1, d2);
             ca[q] = d1;
-            cb[q] = inu * (1.0 - dP_eps(-p / mu, eps));
+            cb[q] = inu * one_minus_dP_eps(-p / mu, eps);
             cc[q] = d2 * p - 1.0;
         }
     }

@@ -92,17 +92,36 @@ constexpr int ST_ETIMEOUT = -7;
 constexpr int ST_SKIP = 2;        // subdomain of a problem not taking part in this evaluation
 
 // ------------------------------------------------------------- pointwise math
-// Smoothed projection of Sec. 3.1 in the cancellation-free quotient form of
-// Lemma 5's proof: P_eps(x) = 2x / (sqrt((x+1)^2+eps) + sqrt((x-1)^2+eps)).
-__device__ __forceinline__ double P_eps(double x, double eps) {
-    double a = x + 1.0, b = x - 1.0;
-    return 2.0 * x / (sqrt(a * a + eps) + sqrt(b * b + eps));
+// The reduced system (Sec. 3.3) uses the smoothed projection P_eps of Sec. 3.1
+// only in two combinations: the control u = -(1/nu)(p + mu P_eps(-p/mu)) =
+// -(mu/nu)(P_eps(x) - x) with x = -p/mu, and the Jacobian entry
+// (1/nu)(1 - P_eps'(x)). Where |x| < 1 both are O(eps) differences of O(1)
+// numbers; evaluated as printed they would lose a relative 2^-53/eps. Both are
+// written here with every difference |s| - sqrt(s^2 + eps) replaced by
+// -eps/(|s| + sqrt(s^2 + eps)) (the device of Lemma 5's quotient form), so
+// they keep full relative accuracy. One division each; valid for |x| < 1e30.
+
+// P_eps(x) - x = x (2 - a - b)/(a + b), a = sqrt((x+1)^2+eps), b = sqrt((x-1)^2+eps),
+// 2 - a - b = 2(1 - max(1,|x|)) - eps/t1 - eps/t2, t1 = |x+1| + a, t2 = |x-1| + b.
+__device__ __forceinline__ double P_eps_minus_id(double x, double eps) {
+    const double s1 = x + 1.0, s2 = x - 1.0;
+    const double a = sqrt(fma(s1, s1, eps)), b = sqrt(fma(s2, s2, eps));
+    const double t1 = fabs(s1) + a, t2 = fabs(s2) + b;
+    const double gap = 2.0 * (1.0 - fmax(1.0, fabs(x)));
+    const double t12 = t1 * t2;
+    return x * fma(gap, t12, -eps * (t1 + t2)) / ((a + b) * t12);
 }
 
-// P_eps'(x) = ((x+1)/sqrt((x+1)^2+eps) - (x-1)/sqrt((x-1)^2+eps)) / 2 (Sec. 3.1).
-__device__ __forceinline__ double dP_eps(double x, double eps) {
-    double a = x + 1.0, b = x - 1.0;
-    return 0.5 * (a / sqrt(a * a + eps) - b / sqrt(b * b + eps));
+// 1 - P_eps'(x) = ((1 - g(x+1)) + (1 + g(x-1)))/2, g(s) = s/sqrt(s^2+eps):
+// 1 - g(s1) = r1/a with r1 = eps/(a + s1) (s1 > 0) or a - s1 (s1 <= 0);
+// 1 + g(s2) = r2/b with r2 = eps/(b - s2) (s2 < 0) or b + s2 (s2 >= 0).
+__device__ __forceinline__ double one_minus_dP_eps(double x, double eps) {
+    const double s1 = x + 1.0, s2 = x - 1.0;
+    const double a = sqrt(fma(s1, s1, eps)), b = sqrt(fma(s2, s2, eps));
+    double n1, d1, n2, d2;
+    if (s1 > 0.0) { n1 = eps; d1 = a + s1; } else { n1 = a - s1; d1 = 1.0; }
+    if (s2 < 0.0) { n2 = eps; d2 = b - s2; } else { n2 = b + s2; d2 = 1.0; }
+    return 0.5 * fma(n1 * d2, b, n2 * d1 * a) / (d1 * d2 * a * b);
 }
 
 // phi, phi', phi'' of the three nonlinearities.

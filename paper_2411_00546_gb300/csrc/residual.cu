@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(NT) k_residual_global(ProbDev P, const double*
                                                         double* partials) {
     __shared__ double red[2 * NT];
     const int n = P.n;
-    const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu, imu = 1.0 / P.mu;
+    const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu, imu = 1.0 / P.mu, munu = P.mu / P.nu;
     auto vy = [=](int i, int j) -> double {
         if (i < 0 || i >= n || j < 0 || j >= n) return 0.0;
         const long long g = (long long)j * n + i;
@@ -50,15 +50,17 @@ __global__ void __launch_bounds__(NT) k_residual_global(ProbDev P, const double*
             double ph, d1, d2;
             phi_eval(P.phi, P.kappa, yc, ph, d1, d2);
             const double fv = P.f ? P.f[g] : 0.0;
-            const double pe_ = P_eps(-pc * imu, eps);
-            const double Fyv = beta * (4.0 * yc - yw - ye - ys - yn) + ph - fv + inu * (pc + mu * pe_);
+            // -u = (mu/nu)(P_eps(x) - x), x = -p/mu (control of Sec. 3.2)
+            const double xq = -pc * imu;
+            const double dq = P_eps_minus_id(xq, eps);
+            const double Fyv = beta * (4.0 * yc - yw - ye - ys - yn) + ph - fv + munu * dq;
             const double Fpv = beta * (4.0 * pc - pw - pe - ps - pn) + d1 * pc - yc + P.yd[g];
             if (Fy) Fy[g] = Fyv;
             if (Fp) Fp[g] = Fpv;
             a += Fyv * Fyv + Fpv * Fpv;
             if (FLOOR) {
                 const double My = beta * (4.0 * fabs(yc) + fabs(yw) + fabs(ye) + fabs(ys) + fabs(yn)) + fabs(ph) +
-                                  fabs(fv) + inu * (fabs(pc) + mu * fabs(pe_));
+                                  fabs(fv) + inu * (fabs(pc) + mu * fabs(xq + dq));
                 const double Mp = beta * (4.0 * fabs(pc) + fabs(pw) + fabs(pe) + fabs(ps) + fabs(pn)) +
                                   fabs(d1 * pc) + fabs(yc) + fabs(P.yd[g]);
                 b += My * My + Mp * Mp;
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(NT) k_coef_global(ProbDev P, const double* __r
         const double yv = y[g], pv = p[g];
         phi_eval(P.phi, P.kappa, yv, ph, d1, d2);
         coef[g] = d1;
-        coef[nn + g] = inu * (1.0 - dP_eps(-pv / mu, eps));
+        coef[nn + g] = inu * one_minus_dP_eps(-pv / mu, eps);
         coef[2 * nn + g] = d2 * pv - 1.0;
     }
 }

@@ -70,10 +70,10 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
         : "memory");
 }
 
-// Bounded wait for phase `parity` of `bar`; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for phase `parity` of `bar` (at most `limit` polls); false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = WAIT_LIMIT) {
     const uint32_t a = smem_u32(bar);
-    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -138,7 +138,10 @@ __device__ void stream_abort(Stream<T>& S, uint32_t first, uint32_t last, uint32
 // loads overlap the streamed products instead of stalling every row.
 // vec, tmp: shared arrays of mp T. w: global scratch, m*W T. m <= NT: thread
 // t handles entry t of every block row. Returns false if a wait timed out
-// (the CTA must then return).
+// (the CTA must then return). err[0] is the timeout flag; err[1] != 0 is the
+// timeout test of ras_opts.wait_test: the first slab wait of the solve then
+// polls zero times, so it runs out with its copy still in flight, and the
+// copies issued so far are drained with the normal limit before the return.
 template <typename T, class Rhs, class Pre, class Out>
 __device__ bool stream_solve(Stream<T>& S, const T* __restrict__ G, int m, int mp, int W, T beta, T* w, T* vec,
                              T* tmp, Rhs rhs, Pre pre, Out out, int* err) {
@@ -150,6 +153,7 @@ __device__ bool stream_solve(Stream<T>& S, const T* __restrict__ G, int m, int m
     const uint32_t D = min((uint32_t)Ring<T>::MAXD, (uint32_t)Ring<T>::RING_BYTES / slab_bytes);
     const long long blk = (long long)mp * mp;
     const uint32_t total = (uint32_t)((2 * W - 1) * nslab);
+    const bool first_zero = err && err[1] != 0;
     // slab q of this solve: forward blocks 0..W-2, then backward W-1..0
     auto src = [&](uint32_t q) -> const T* {
         const int f = (W - 1) * nslab;
@@ -173,7 +177,7 @@ __device__ bool stream_solve(Stream<T>& S, const T* __restrict__ G, int m, int m
     // one mp x mp product from the stream: tmp = G_(next block) vec
     auto matvec = [&]() -> bool {
         for (int sl = 0; sl < nslab; ++sl, ++q, k = (k + 1 == D) ? 0u : k + 1) {
-            const bool ok = mbar_wait(&S.full[k], (S.phase >> k) & 1u);
+            const bool ok = mbar_wait(&S.full[k], (S.phase >> k) & 1u, (q == 0 && first_zero) ? 0 : WAIT_LIMIT);
             const T* slot = reinterpret_cast<const T*>(S.ring + k * slab_bytes);
             T acc = (T)0;
             if (ok) {

@@ -44,7 +44,7 @@ class ras_opts(ctypes.Structure):
                 ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
                 ("gmres_rtol", ctypes.c_double), ("floor_factor", ctypes.c_double),
                 ("precision", ctypes.c_int), ("ir_max", ctypes.c_int), ("ir_rtol", ctypes.c_double),
-                ("kappa", ctypes.c_double), ("jvp_ir", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("kappa", ctypes.c_double), ("jvp_ir", ctypes.c_int), ("wait_test", ctypes.c_int)]
 
 
 class ras_stats(ctypes.Structure):

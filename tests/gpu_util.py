@@ -10,18 +10,12 @@ FP64_TOL = 1e-10     # relative inf-norm per field, pure FP64 path
 MIXED_TOL = 1e-8     # relative inf-norm per field, FP32-factor / FP64-refinement path
 
 
-def rel_inf(a, b, other=None):
-    """max|a - b| / max|b| (relative infinity norm of one field). With the
-    other field of the solution given, the scale is never taken below 1e-2 of
-    the joint scale max(|b|, |other|): a field below 1% of the other (y ~ 1e-6
-    beside p ~ 1e-3 when the L1 control is inactive and y only reflects the
-    eps-smoothing) is determined only to the solve's accuracy on the joint
-    scale."""
+def rel_inf(a, b):
+    """max|a - b| / max|b|: the relative infinity norm of one field, each field
+    (y or p) on its own scale."""
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     scale = np.max(np.abs(b))
-    if other is not None:
-        scale = max(scale, 1e-2 * max(scale, float(np.max(np.abs(other)))))
     diff = np.max(np.abs(a - b))
     if scale == 0.0:
         return diff

@@ -52,8 +52,8 @@ def _solve(h, cfgs):
 
 def _check(cfgs, ref, Y, P, stats, tol):
     for k, (c, r, st) in enumerate(zip(cfgs, ref, stats)):
-        assert rel_inf(Y[k], r.Y, r.P) <= tol, k
-        assert rel_inf(P[k], r.P, r.Y) <= tol, k
+        assert rel_inf(Y[k], r.Y) <= tol, k
+        assert rel_inf(P[k], r.P) <= tol, k
         assert st.outer_its == r.outer, k
         assert st.inner_its_sum == sum(sum(i) for i in r.inner_its), k
 
@@ -167,8 +167,8 @@ def test_autotune_leaves_solve_state():
         assert rc == ras.RAS_ESTATE
         y2, p2 = zeros(n), zeros(n)
         ras.ras_raspen_solve(h, y2, p2)
-        assert rel_inf(y2.cpu().numpy(), y.cpu().numpy(), p.cpu().numpy()) <= MIXED_TOL
-        assert rel_inf(p2.cpu().numpy(), p.cpu().numpy(), y.cpu().numpy()) <= MIXED_TOL
+        assert rel_inf(y2.cpu().numpy(), y.cpu().numpy()) <= MIXED_TOL
+        assert rel_inf(p2.cpu().numpy(), p.cpu().numpy()) <= MIXED_TOL
     finally:
         ras.ras_destroy(h)
 

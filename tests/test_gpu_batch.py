@@ -53,8 +53,8 @@ def test_batch_matches_individual_solves(oracle_solves, prec, tol):
         ps = [zeros(c["n"]) for c in cfgs]
         rc, stats = ras.ras_batch_raspen_solve(h, ys, ps)
         for k, (c, ref, st) in enumerate(zip(cfgs, oracle_solves, stats)):
-            assert rel_inf(ys[k].cpu().numpy(), ref.Y, ref.P) <= tol, k
-            assert rel_inf(ps[k].cpu().numpy(), ref.P, ref.Y) <= tol, k
+            assert rel_inf(ys[k].cpu().numpy(), ref.Y) <= tol, k
+            assert rel_inf(ps[k].cpu().numpy(), ref.P) <= tol, k
             assert st.outer_its == ref.outer, k
             assert st.inner_its_sum == sum(sum(i) for i in ref.inner_its), k
             # the same problem alone on the GPU
@@ -62,8 +62,8 @@ def test_batch_matches_individual_solves(oracle_solves, prec, tol):
             try:
                 y1, p1 = zeros(c["n"]), zeros(c["n"])
                 rc1, st1 = ras.ras_raspen_solve(h1, y1, p1)
-                assert rel_inf(ys[k].cpu().numpy(), y1.cpu().numpy(), p1.cpu().numpy()) <= tol
-                assert rel_inf(ps[k].cpu().numpy(), p1.cpu().numpy(), y1.cpu().numpy()) <= tol
+                assert rel_inf(ys[k].cpu().numpy(), y1.cpu().numpy()) <= tol
+                assert rel_inf(ps[k].cpu().numpy(), p1.cpu().numpy()) <= tol
                 assert st1.outer_its == st.outer_its and st1.inner_its_sum == st.inner_its_sum
             finally:
                 ras.ras_destroy(h1)

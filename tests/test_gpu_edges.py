@@ -38,8 +38,8 @@ def test_smallest_grids_reach_the_dense_newton_root(n, s, ov, prec, tol):
         y, p = zeros(n), zeros(n)
         rc, st = ras.ras_raspen_solve(h, y, p)
         assert rc in (ras.RAS_OK, ras.RAS_OK_FLOOR)
-        assert rel_inf(y.cpu().numpy(), ref.Y, ref.P) <= tol
-        assert rel_inf(p.cpu().numpy(), ref.P, ref.Y) <= tol
+        assert rel_inf(y.cpu().numpy(), ref.Y) <= tol
+        assert rel_inf(p.cpu().numpy(), ref.P) <= tol
     finally:
         ras.ras_destroy(h)
 
@@ -86,8 +86,8 @@ def test_widest_block_matches_oracle(prec, tol):
         Fy, Fp = zeros(n), zeros(n)
         ras.ras_apply(h, zeros(n), zeros(n), 1, Fy, Fp)
         assert ras.ras_local_iterations(h)[0] == ref.iterations[0]
-        assert rel_inf(Fy.cpu().numpy(), ref.Fy, ref.Fp) <= tol
-        assert rel_inf(Fp.cpu().numpy(), ref.Fp, ref.Fy) <= tol
+        assert rel_inf(Fy.cpu().numpy(), ref.Fy) <= tol
+        assert rel_inf(Fp.cpu().numpy(), ref.Fp) <= tol
     finally:
         ras.ras_destroy(h)
 
@@ -104,8 +104,8 @@ def test_inactive_control(prec, tol):
     try:
         y, p = zeros(n), zeros(n)
         rc, st = ras.ras_raspen_solve(h, y, p)
-        assert rel_inf(y.cpu().numpy(), ref.Y, ref.P) <= tol
-        assert rel_inf(p.cpu().numpy(), ref.P, ref.Y) <= tol
+        assert rel_inf(y.cpu().numpy(), ref.Y) <= tol
+        assert rel_inf(p.cpu().numpy(), ref.P) <= tol
         assert st.outer_its == ref.outer
     finally:
         ras.ras_destroy(h)

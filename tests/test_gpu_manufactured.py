@@ -65,8 +65,8 @@ def test_paper_workload_raspen_solve(n63_paper, prec, tol):
     try:
         y, p = zeros(n), zeros(n)
         rc, st = ras.ras_raspen_solve(h, y, p)
-        assert rel_inf(y.cpu().numpy(), ref.Y, ref.P) <= tol
-        assert rel_inf(p.cpu().numpy(), ref.P, ref.Y) <= tol
+        assert rel_inf(y.cpu().numpy(), ref.Y) <= tol
+        assert rel_inf(p.cpu().numpy(), ref.P) <= tol
         assert st.outer_its == ref.outer
         assert st.inner_its_sum == sum(sum(i) for i in ref.inner_its)
     finally:
@@ -94,8 +94,8 @@ def test_paper_workload_at_the_paper_eps(n63_paper_tiny_eps, prec, tol):
     try:
         y, p = zeros(n), zeros(n)
         rc, st = ras.ras_raspen_solve(h, y, p)
-        assert rel_inf(y.cpu().numpy(), ref.Y, ref.P) <= tol
-        assert rel_inf(p.cpu().numpy(), ref.P, ref.Y) <= tol
+        assert rel_inf(y.cpu().numpy(), ref.Y) <= tol
+        assert rel_inf(p.cpu().numpy(), ref.P) <= tol
         assert st.outer_its == ref.outer
         assert st.inner_its_sum == sum(sum(i) for i in ref.inner_its)
     finally:

@@ -45,8 +45,8 @@ def test_newton_solve_parity(oracle_runs, n, eps0, phi, prec, tol):
         y, p = zeros(n), zeros(n)
         rc, st = ras.ras_newton_solve(h, y, p)
         assert rc in (ras.RAS_OK, ras.RAS_OK_FLOOR)
-        assert rel_inf(y.cpu().numpy(), ref.Y, ref.P) <= tol
-        assert rel_inf(p.cpu().numpy(), ref.P, ref.Y) <= tol
+        assert rel_inf(y.cpu().numpy(), ref.Y) <= tol
+        assert rel_inf(p.cpu().numpy(), ref.P) <= tol
         assert st.outer_its == ref.outer
         assert st.gmres_its == sum(ref.gmres_its)
         assert st.halvings == ref.newton.halvings

@@ -36,9 +36,59 @@ def test_sweep_case_raspen_solve(case, prec, tol):
     try:
         y, p = zeros(n), zeros(n)
         rc, st = ras.ras_raspen_solve(h, y, p)
-        assert rel_inf(y.cpu().numpy(), ref.Y, ref.P) <= tol
-        assert rel_inf(p.cpu().numpy(), ref.P, ref.Y) <= tol
+        assert rel_inf(y.cpu().numpy(), ref.Y) <= tol
+        assert rel_inf(p.cpu().numpy(), ref.P) <= tol
         assert st.outer_its == ref.outer
         assert st.inner_its_sum == sum(sum(i) for i in ref.inner_its)
+    finally:
+        ras.ras_destroy(h)
+
+
+# The (nu, mu) regimes of the paper's parameter study (Sec. 5.4) on its model
+# problem (Sec. 4; y_d from the oracle's manufactured construction at eps =
+# 1e-15), RASPEN_eps and Newton_RAS_eps with one of the study's schedules, at
+# n = 63 on 3 x 3 subdomains with overlap 2. The study's third block, nu = 1e-8
+# with mu = 1, is left out: on grids this coarse the manufactured state
+# overflows exp(kappa y) (the oracle's state solve at n = 127 already meets
+# non-finite values), so there is no problem to compare on.
+SENSITIVITY = [(1e-8, 1e-4), (1e-4, 1.0)]
+
+
+@pytest.fixture(scope="module", params=SENSITIVITY, ids=lambda v: "nu%g-mu%g" % v)
+def sensitivity_case(request):
+    from oracle import discretization as fd
+    from oracle import pointwise as pw
+    from oracle import ras as oras
+    from oracle import workloads as wl
+    nu, mu = request.param
+    n = 63
+    pbar = inputs.yd_manufactured_paper(n, mu, 5)
+    _, yd = wl.manufactured(pbar, n, nu=nu, mu=mu)
+    prob = fd.Problem(n, pw.PHI_KAPPA, nu, mu, yd, kappa=0.1)
+    kw = dict(tol=1e-10, inner_tol=1e-8, sigma=1.1, eps0=1e-3, gamma=0.2, eps_min=1e-6)
+    refs = {"raspen": solvers.raspen(prob, 3, 3, 2, oras.Options(**kw)),
+            "newton_ras": solvers.newton_ras(prob, 3, 3, 2, oras.Options(**kw))}
+    return n, nu, mu, yd, kw, refs
+
+
+@pytest.mark.parametrize("method", ["raspen", "newton_ras"])
+@pytest.mark.parametrize("prec,tol", PRECS)
+def test_sensitivity_regime_matches_oracle(sensitivity_case, method, prec, tol):
+    from gpu_util import to_dev
+    n, nu, mu, yd, kw, refs = sensitivity_case
+    ref = refs[method]
+    h = ras.ras_create(n, 3, 3, 2, ras.RAS_PHI_KAPPA, nu, mu, to_dev(yd), None,
+                       ras.make_opts(precision=prec, kappa=0.1, **kw))
+    try:
+        y, p = zeros(n), zeros(n)
+        fn = ras.ras_raspen_solve if method == "raspen" else ras.ras_newton_ras_solve
+        rc, st = fn(h, y, p, check=False)
+        assert rc in (ras.RAS_OK, ras.RAS_OK_FLOOR) and ref.status in (0, 1), (rc, ref.status)
+        assert rel_inf(y.cpu().numpy(), ref.Y) <= tol
+        assert rel_inf(p.cpu().numpy(), ref.P) <= tol
+        assert st.outer_its == ref.outer
+        if method == "raspen":
+            assert st.inner_its_sum == sum(sum(i) for i in ref.inner_its)
+            assert st.gmres_its == sum(ref.gmres_its)
     finally:
         ras.ras_destroy(h)
