@@ -348,6 +348,15 @@ int check_err(ras_problem* h) {
     return RAS_OK;
 }
 
+// A device-side failure found after the solve (a bounded wait that ran out):
+// the call's stats carry the same status as its return value.
+int check_err_stats(ras_problem* h, ras_stats* stats, int count) {
+    const int e = check_err(h);
+    if (e != RAS_OK && stats)
+        for (int k = 0; k < count; ++k) stats[k].status = e;
+    return e;
+}
+
 size_t prec_bytes(const ras_problem* h) { return h->o.precision == RAS_MIXED ? sizeof(float) : sizeof(double); }
 
 // Algorithmic work of a factorisation: 16 wx^3 wy flops per subdomain (block-
@@ -2017,7 +2026,7 @@ int ras_apply(ras_problem* h, const double* y, const double* p, int continuation
     const std::vector<double> pstart(1, continuation ? h->o.eps0 : h->o.eps_min);
     const int rc = ras_apply_internal(h, pstart, h->F, stats);
     if (rc == RAS_ECUDA) return rc;
-    TRY(check_err(h));
+    TRY(check_err_stats(h, stats, 1));
     TRY(copy_out(h, h->F, 0, Fy, Fp));
     TRY(sync(h));
     if (stats) stats->status = rc;
@@ -2056,7 +2065,7 @@ int ras_batch_raspen_solve(ras_problem* h, double* const* y, double* const* p, r
     for (int k = 0; k < h->nprob; ++k) TRY(copy_in(h, h->X, k, y[k], p[k]));
     const int rc = raspen_internal(h, stats);
     if (rc == RAS_ECUDA) return rc;
-    TRY(check_err(h));
+    TRY(check_err_stats(h, stats, h->nprob));
     for (int k = 0; k < h->nprob; ++k) TRY(copy_out(h, h->X, k, y[k], p[k]));
     TRY(sync(h));
     return rc;
@@ -2075,7 +2084,7 @@ int ras_newton_ras_solve(ras_problem* h, double* y, double* p, ras_stats* stats)
     TRY(copy_in(h, h->X, 0, y, p));
     const int rc = newton_ras_internal(h, stats);
     if (rc == RAS_ECUDA) return rc;
-    TRY(check_err(h));
+    TRY(check_err_stats(h, stats, 1));
     TRY(copy_out(h, h->X, 0, y, p));
     TRY(sync(h));
     return rc;
@@ -2088,7 +2097,7 @@ int ras_newton_solve(ras_problem* h, double* y, double* p, ras_stats* stats) {
     TRY(copy_in(h, h->X, 0, y, p));
     const int rc = newton_internal(h, stats, false);
     if (rc == RAS_ECUDA) return rc;
-    TRY(check_err(h));
+    TRY(check_err_stats(h, stats, 1));
     TRY(copy_out(h, h->X, 0, y, p));
     TRY(sync(h));
     return rc;

@@ -59,10 +59,11 @@ __device__ __forceinline__ LocalView make_view(const SubDev& s, const ProbDev& P
 
 // K_i at the view's state and eps (residual F of Sec. 3.3 at the nodes of
 // Omega_i). Writes the interleaved residual to `out` when non-null and
-// returns (block-wide) its squared 2-norm and the squared norm of the
-// nodewise |term| sums (rounding-floor estimate).
+// returns (block-wide) its squared 2-norm and, with `with_floor`, the squared
+// norm of the nodewise |term| sums (rounding-floor estimate; the stop test
+// reads it only at eps_min, so callers ask for it only there; else 0).
 __device__ void local_residual(const LocalView& V, const ProbDev& P, double eps, double* out,
-                               double& nrm2, double& flr2, double* red) {
+                               double& nrm2, double& flr2, double* red, bool with_floor) {
     const int wx = V.wx, nn = wx * V.wy;
     const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu, imu = 1.0 / P.mu, munu = P.mu / P.nu;
     double a = 0.0, b = 0.0;
@@ -81,16 +82,18 @@ __device__ void local_residual(const LocalView& V, const ProbDev& P, double eps,
         const double dq = P_eps_minus_id(xq, eps);
         const double Fy = beta * (4.0 * yc - yw - ye - ys - yn) + ph - fv + munu * dq;
         const double Fp = beta * (4.0 * pc - pw - pe - ps - pn) + d1 * pc - yc + P.yd[g];
-        const double My = beta * (4.0 * fabs(yc) + fabs(yw) + fabs(ye) + fabs(ys) + fabs(yn)) + fabs(ph) +
-                          fabs(fv) + inu * (fabs(pc) + mu * fabs(xq + dq));
-        const double Mp = beta * (4.0 * fabs(pc) + fabs(pw) + fabs(pe) + fabs(ps) + fabs(pn)) +
-                          fabs(d1 * pc) + fabs(yc) + fabs(P.yd[g]);
+        if (with_floor) {
+            const double My = beta * (4.0 * fabs(yc) + fabs(yw) + fabs(ye) + fabs(ys) + fabs(yn)) + fabs(ph) +
+                              fabs(fv) + inu * (fabs(pc) + mu * fabs(xq + dq));
+            const double Mp = beta * (4.0 * fabs(pc) + fabs(pw) + fabs(pe) + fabs(ps) + fabs(pn)) +
+                              fabs(d1 * pc) + fabs(yc) + fabs(P.yd[g]);
+            b += My * My + Mp * Mp;
+        }
         if (out) {
             out[2 * q] = Fy;
             out[2 * q + 1] = Fp;
         }
         a += Fy * Fy + Fp * Fp;
-        b += My * My + Mp * Mp;
     }
     block_sum2<NT>(a, b, red);
     nrm2 = a;
@@ -153,7 +156,7 @@ __global__ void __launch_bounds__(NT) k_local_init(int nsub, const SubDev* __res
     __syncthreads();
     const LocalView V = make_view(s, P, X, c, nullptr, 0.0);
     double n2, f2;
-    local_residual(V, P, eps_start, Kpool + s.voff, n2, f2, red);
+    local_residual(V, P, eps_start, Kpool + s.voff, n2, f2, red, eps_start == np.eps_min);
     if (threadIdx.x == 0) {
         LocalState st;
         st.eps = eps_start;
@@ -337,7 +340,7 @@ __global__ void __launch_bounds__(NT) k_local_linesearch(int nsub, const SubDev*
     for (;;) {
         const LocalView V = make_view(s, P, X, c, d, alpha);
         double n2, f2;
-        local_residual(V, P, L.eps, Kt, n2, f2, red);
+        local_residual(V, P, L.eps, Kt, n2, f2, red, L.eps == np.eps_min);
         nt = sqrt(n2);
         ft = sqrt(f2);
         if (nt <= np.sigma * L.nrm || h == np.max_halvings) break;
@@ -356,7 +359,7 @@ __global__ void __launch_bounds__(NT) k_local_linesearch(int nsub, const SubDev*
     } else {
         const LocalView V = make_view(s, P, X, c, nullptr, 0.0);
         double n2, f2;
-        local_residual(V, P, en, K, n2, f2, red);
+        local_residual(V, P, en, K, n2, f2, red, en == np.eps_min);
         L.nrm = sqrt(n2);
         L.flr = sqrt(f2);
     }
