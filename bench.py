@@ -36,19 +36,31 @@ SM_MAX_MHZ = 2070.0
 FP32_LANES = 128     # FP32 FMA lanes per SM
 FP64_LANES = 2       # FP64 FMA per clock per SM on GB300 (1.2 TFLOP/s class)
 
+NEWTON_CAP = 25      # outer iterations of the unpreconditioned Newton baselines in the bench
+
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one ncu capture of the n1023 workload (profiles/dram_jvp_n1023.md), valid
-# while what the kernel is built from is unchanged since that capture: its
-# source file, and the data layouts it reads (the header from ProbDev to the
-# status values).
-TRAFFIC = {"jvp": {"bytes_per_launch": 8546142720.0, "workload": "n1023",
+# one ncu capture of the n1023 workload, valid while what the kernel is built
+# from is unchanged since that capture: its source file, and the data layouts
+# it reads (the header from ProbDev to the status values).
+TRAFFIC = {"jvp": {"bytes_per_launch": 12841677056.0, "workload": "n1023",
                    "sources": [("paper_2411_00546_gb300/csrc/solve.cu", None, None),
                                ("paper_2411_00546_gb300/csrc/ras_internal.cuh", "struct ProbDev {",
                                 "// Status values")],
-                   "sha256": ["f0efb1a3e01960cc4d101288c0db55eba4c15b8da07803980d579ed27e86b951",
+                   "sha256": ["0850b808025f4864f42d3be3904337159fef448ad41d8100022d4c6e10bee0f4",
                               "28382610a57d0127f35485ec44db715ade6772f607ad44839b39d271bd0f8d38"]}}
 
-NEWTON_CAP = 25      # outer iterations of the unpreconditioned Newton baselines in the bench
+# FP64-pipe thread instructions per grid node of the global residual kernel
+# (sm__thread_inst_executed_pipe_fp64_pred_on.sum / n^2) from one ncu capture,
+# valid while residual.cu and the pointwise functions of ras_internal.cuh are
+# unchanged since; the residual's roofline counts these instructions.
+FP64_INST = {"residual": {"per_node": 64.229, "workload": "n1023",
+                          "sources": [("paper_2411_00546_gb300/csrc/residual.cu", None, None),
+                                      ("paper_2411_00546_gb300/csrc/ras_internal.cuh",
+                                       "// ------------------------------------------------------------- pointwise math",
+                                       "// eps_{k+1} = max(gamma eps_k, eps_min)")],
+                          "sha256": ["3cf6991c991cff72343d99ec1b305ef03f2a8a070d2be704207453d9768dbf77",
+                                     "b9612a2d2daf4b94bfb91eb7abf9b47b370ef4de1eb40b684ac192d4abee9b77"]}}
+
 
 def field_err(a, b):
     """Relative infinity-norm error of one field: max|a - b| / max|b|."""
@@ -93,11 +105,11 @@ def jvp_alg_bytes(n, sx, sy, overlap, factor_bytes):
     return total + 3 * 2 * n * n * 8
 
 
-def traffic_for(kind, workload):
-    """Captured DRAM bytes per launch of `kind`, or None when there is no
-    capture for this workload or the kernel's sources changed since."""
+def _captured(table, key, kind, workload):
+    """table[kind][key] from an ncu capture, or None when there is no capture
+    for this workload or the kernel's sources changed since."""
     import hashlib
-    t = TRAFFIC.get(kind)
+    t = table.get(kind)
     if t is None or t["workload"] != workload:
         return None
     for (path, start, end), sha in zip(t["sources"], t["sha256"]):
@@ -113,7 +125,17 @@ def traffic_for(kind, workload):
             data = text[text.index(start):text.index(end)].encode()
         if hashlib.sha256(data).hexdigest() != sha:
             return None
-    return t["bytes_per_launch"]
+    return t[key]
+
+
+def traffic_for(kind, workload):
+    """Captured DRAM bytes per launch of `kind` (see TRAFFIC), or None."""
+    return _captured(TRAFFIC, "bytes_per_launch", kind, workload)
+
+
+def fp64_inst_for(kind, workload):
+    """Captured FP64-pipe instructions per node of `kind` (see FP64_INST), or None."""
+    return _captured(FP64_INST, "per_node", kind, workload)
 
 
 def measure_batch(ras, torch, dev, stream, autotune=True):
@@ -176,50 +198,71 @@ def measure_batch(ras, torch, dev, stream, autotune=True):
             "max_err_batched_vs_alone": err, "autotune": tuned}
 
 
-def measure_serving(ras, torch, dev, stream, count):
+def measure_serving(ras, torch, dev, stream, count, rate=None, seq_mixed=True):
     """Serving: the first `count` requests of the Poisson stream (lambda = 200/s,
     seed 5, n ~ U{127,255,511,1023}) through the continuous-batching server
     (HBM budget 150 GB, up to 64 admitted), mixed precision; p50/p99 latency
-    and solves/s. Baseline: the same requests solved one at a time in FP64 in
-    arrival order (a single FIFO queue), from their measured solve times."""
+    and solves/s. With `rate`, the same requests arrive at `rate` per second
+    instead (every gap scaled by 200/rate: a stretched replay of the stream,
+    so that arrivals overlap completions in a steady state), and the latencies
+    of the requests arriving in the middle 80% of the stream are reported
+    beside all of them. Baselines: the same requests solved one at a time in
+    arrival order (a single FIFO queue) from their measured stand-alone solve
+    times, in FP64 and in mixed precision (batching and precision apart)."""
     from paper_2411_00546_gb300 import inputs, serve
-    stream_reqs = inputs.arrival_stream()[:count]
+    scale = 1.0 if rate is None else 200.0 / rate
+    stream_reqs = [(t * scale, c) for t, c in inputs.arrival_stream()[:count]]
     reqs = [(t, dict(n=c["n"], sx=c["sx"], sy=c["sy"], overlap=c["overlap"], phi=c["phi"], nu=c["nu"],
                      mu=c["mu"], y_d=inputs.make_yd(c))) for t, c in stream_reqs]
     base = dict(eps0=0.1, gamma=0.1, eps_min=1e-6, tol=1e-10, inner_tol=1e-8, sigma=1.1)
     o = ras.make_opts(precision=ras.RAS_MIXED, **base)
-    serve.run_stream(reqs[:2], 150e9, 64, o, stream.cuda_stream)   # warm-up
+    serve.run_stream([(0.0, reqs[0][1]), (0.0, reqs[1][1])], 150e9, 64, o, stream.cuda_stream)   # warm-up
     out = serve.run_stream(reqs, 150e9, 64, o, stream.cuda_stream)
     lat = list(out["latency_s"].values())
     span = out["wall_s"] - out["first_arrival_s"]
+    arr = sorted(t for t, _ in reqs)
+    lo, hi = arr[int(0.1 * len(arr))], arr[min(len(arr) - 1, int(0.9 * len(arr)))]
+    mid = [out["latency_s"][i] for i, (t, _) in enumerate(reqs) if lo <= t <= hi and i in out["latency_s"]]
     res = {"workload": "first %d requests of the Poisson stream (lambda 200/s, seed 5), n ~ U{127,255,511,1023}, "
-                       "mu, nu, phi, y_d as the uneven batch" % count,
-           "budget_bytes": 150e9, "max_active": 64, "p50_ms": 1e3 * serve.percentile(lat, 50),
-           "p99_ms": 1e3 * serve.percentile(lat, 99), "solves_per_s": len(lat) / span, "steps": out["steps"],
+                       "mu, nu, phi, y_d as the uneven batch%s" % (
+                           count, "" if rate is None else "; replayed at %g requests/s (gaps x %g)" % (rate, scale)),
+           "budget_bytes": 150e9, "max_active": 64, "requests": len(lat),
+           "arrival_span_s": arr[-1] - arr[0],
+           "p50_ms": 1e3 * serve.percentile(lat, 50), "p99_ms": 1e3 * serve.percentile(lat, 99),
+           "solves_per_s": len(lat) / span, "steps": out["steps"],
            "peak_active": out["peak_active"], "peak_device_bytes": out["peak_device_bytes"],
            "all_ok": all(v == ras.RAS_OK for v in out["status"].values())}
-    # sequential FP64 baseline: one solve at a time, first come first served
-    o64 = ras.make_opts(precision=ras.RAS_FP64, **base)
-    t_free, seq_lat = 0.0, []
-    for (t, d), (_, c) in zip(reqs, stream_reqs):
-        yd = torch.tensor(d["y_d"], dtype=torch.float64, device=dev)
-        h = ras.ras_create(c["n"], c["sx"], c["sy"], c["overlap"], c["phi"], c["nu"], c["mu"], yd, None, o64,
-                           stream=stream.cuda_stream)
-        y = torch.zeros_like(yd)
-        p = torch.zeros_like(yd)
-        torch.cuda.synchronize(dev)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ras.ras_raspen_solve(h, y, p, check=False)
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        ras.ras_destroy(h)
-        start = max(t, t_free)
-        t_free = start + a.elapsed_time(b) / 1e3
-        seq_lat.append(t_free - t)
-    res["sequential_fp64"] = {"p50_ms": 1e3 * serve.percentile(seq_lat, 50),
-                              "p99_ms": 1e3 * serve.percentile(seq_lat, 99),
-                              "solves_per_s": len(seq_lat) / (t_free - reqs[0][0])}
+    if rate is not None and mid:
+        res["steady_window"] = {"arrivals_s": [lo, hi], "requests": len(mid),
+                                "p50_ms": 1e3 * serve.percentile(mid, 50), "p99_ms": 1e3 * serve.percentile(mid, 99)}
+
+    def sequential(prec):
+        o_ = ras.make_opts(precision=prec, **base)
+        t_free, seq_lat, solve_s = 0.0, [], []
+        for (t, d), (_, c) in zip(reqs, stream_reqs):
+            yd = torch.tensor(d["y_d"], dtype=torch.float64, device=dev)
+            h = ras.ras_create(c["n"], c["sx"], c["sy"], c["overlap"], c["phi"], c["nu"], c["mu"], yd, None, o_,
+                               stream=stream.cuda_stream)
+            y = torch.zeros_like(yd)
+            p = torch.zeros_like(yd)
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ras.ras_raspen_solve(h, y, p, check=False)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ras.ras_destroy(h)
+            dt = a.elapsed_time(b) / 1e3
+            solve_s.append(dt)
+            start = max(t, t_free)
+            t_free = start + dt
+            seq_lat.append(t_free - t)
+        return {"p50_ms": 1e3 * serve.percentile(seq_lat, 50), "p99_ms": 1e3 * serve.percentile(seq_lat, 99),
+                "solves_per_s": len(seq_lat) / (t_free - reqs[0][0]), "solve_s_sum": sum(solve_s)}
+
+    res["sequential_fp64"] = sequential(ras.RAS_FP64)
+    if seq_mixed:
+        res["sequential_mixed"] = sequential(ras.RAS_MIXED)
     return res
 
 
@@ -323,10 +366,36 @@ def measure_paper_workload(ras, torch, dev, stream):
                      "inner_its_sum": st.inner_its_sum, "ms": round(a.elapsed_time(b), 2),
                      "dist_y": float(np.abs(yn - ybn).max() / np.abs(ybn).max()),
                      "dist_p": float(np.abs(pn - pbn).max() / np.abs(pbn).max())})
+    # the paper's own continuation (eps0 = 1, gamma = 1/5) down to its eps_min = 1e-15
+    rows15 = []
+    o15 = ras.make_opts(tol=1e-10, inner_tol=1e-8, sigma=1.1, eps0=1.0, gamma=0.2, eps_min=1e-15,
+                        precision=ras.RAS_MIXED, kappa=kappa)
+    for sx, sy in ((10, 10), (6, 2), (15, 15)):
+        h = ras.ras_create(n, sx, sy, 2, ras.RAS_PHI_KAPPA, nu, mu, yd, None, o15, stream=stream.cuda_stream)
+        y = torch.zeros_like(pbar)
+        p = torch.zeros_like(pbar)
+        for rep in range(2):
+            with torch.cuda.stream(stream):
+                y.zero_()
+                p.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rc, st = ras.ras_raspen_solve(h, y, p, check=False)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+        ras.ras_destroy(h)
+        yn, pn, ybn, pbn = (t.cpu().numpy() for t in (y, p, ybar, pbar))
+        rows15.append({"layout": "%dx%d" % (sx, sy), "status": rc, "outer": st.outer_its,
+                       "gmres_per_outer": round(st.gmres_its / max(st.outer_its, 1), 1),
+                       "inner_its_sum": st.inner_its_sum, "ms": round(a.elapsed_time(b), 2),
+                       "dist_y": float(np.abs(yn - ybn).max() / np.abs(ybn).max()),
+                       "dist_p": float(np.abs(pn - pbn).max() / np.abs(pbn).max())})
     return {"workload": "Sec. 4 model problem, n=450, kappa (y^3 + exp(kappa y)), nu=1e-6, mu=1, f=0, "
                         "manufactured pbar (k=5), eps 0.1->1e-6, overlap 2, mixed precision",
             "manufacture_ms": t_make, "ybar_max": float(ybar.abs().max()), "yd_max": float(yd.abs().max()),
-            "rows": rows}
+            "rows": rows,
+            "eps_min_1e-15": {"schedule": "the paper's: eps0 = 1, gamma = 1/5, eps_min = 1e-15 (Sec. 5)",
+                              "rows": rows15}}
 
 
 def measure_sweeps(ras, torch, dev, stream):
@@ -586,6 +655,10 @@ def parse_args():
     ap.add_argument("--no-graphs", action="store_true",
                     help="GMRES cycles step by step (every kernel visible to a profiler's launch list)")
     ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-rate", type=float, default=None,
+                    help="replay the serving stream at this many requests/s (default: the stream's 200/s)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving measurement and print it as one JSON line")
     return ap.parse_args()
 
 
@@ -844,6 +917,11 @@ def main():
     from paper_2411_00546_gb300 import ras
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    if args.serve_only:
+        if rank == 0:
+            st_ = torch.cuda.Stream(device=dev)
+            print(json.dumps({"serving": measure_serving(ras, torch, dev, st_, args.serve_requests, args.serve_rate)}))
+        return
     cfg = inputs.problem(args.workload)
     n = cfg["n"]
     yd_np = inputs.make_yd(cfg)
@@ -1040,13 +1118,27 @@ def main():
             e["bytes_read_gbs"] = round(moved / (ms / 1e3) / 1e9, 1)
             e["bytes_read_frac"] = round(e["bytes_read_gbs"] / hbm_peak, 4)
         if kind == "residual":
-            # FP64-pipe bound on GB300: about 42 FP64 operations per node (two
-            # square roots and a division among them) against 40 bytes
-            a64 = 42.0 * (work / 40.0) / (ms / 1e3) / 1e12
-            e.update({"bound": "fp64", "fp64_achieved_tflops": round(a64, 3),
-                      "fp64_peak_tflops": round(fp64_peak, 3), "fp64_frac": round(a64 / fp64_peak, 4),
-                      "hbm_frac": e["frac"]})
-            e["frac"] = e["fp64_frac"]
+            # FP64-pipe bound on GB300: about 42 FP64 operations per node in
+            # the formula (two square roots and a division among them), which
+            # the square roots and the division expand into ~64 FP64-pipe
+            # instructions (ncu count) against 40 bytes. The roofline counts
+            # the instructions the pipe executes, against its instruction rate.
+            nodes = work / 40.0       # over the n launches
+            a64 = 42.0 * nodes / (ms / 1e3) / 1e12
+            e.update({"bound": "fp64", "formula_ops_tflops": round(a64, 3),
+                      "formula_ops_frac": round(a64 / fp64_peak, 4), "hbm_frac": e["frac"]})
+            ipn = fp64_inst_for("residual", args.workload)
+            if ipn is not None:
+                inst_rate = ipn * nodes / (ms / 1e3) / 1e9
+                inst_peak = SM_COUNT * FP64_LANES * clk / 1e9
+                e.update({"unit": "G FP64 inst/s", "achieved": round(inst_rate, 1), "peak": round(inst_peak, 1),
+                          "frac": round(inst_rate / inst_peak, 4), "fp64_inst_per_node": ipn,
+                          "peak_source": "derived: %d SMs x %d FP64 lanes x %.0f MHz" % (SM_COUNT, FP64_LANES,
+                                                                                        clk / 1e6),
+                          "count": "FP64-pipe thread instructions per node from an ncu capture of this "
+                                   "kernel x nodes / live time per launch"})
+            else:
+                e["frac"] = e["formula_ops_frac"]
         if kind == "krylov":
             # one FP64 FMA per 8-byte basis element read: the FP64 pipe binds
             a64 = 2.0 * (work / 8.0) / (ms / 1e3) / 1e12
@@ -1076,7 +1168,7 @@ def main():
         batch = measure_batch(ras, torch, dev, stream, autotune=not args.no_autotune)
     serving = None
     if rank == 0 and not args.no_serve:
-        serving = measure_serving(ras, torch, dev, stream, args.serve_requests)
+        serving = measure_serving(ras, torch, dev, stream, args.serve_requests, args.serve_rate)
     methods = None
     if rank == 0 and not args.no_methods:
         methods = measure_methods(ras, torch, dev, stream)

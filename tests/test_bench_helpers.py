@@ -92,3 +92,25 @@ def test_timed_oracle_solve_equals_the_serial_oracle():
     assert o["outer"] == ref.outer and o["gmres_its"] == ref.gmres_its
     assert o["inner_its_per_eval"] == [sum(i) for i in ref.inner_its]
     assert o["workers"] == 2 and o["wall_s"] > 0 and o["cpu_s"] > 0
+
+
+def test_bench_names_are_all_defined():
+    """Every global name bench.py reads is defined in it or imported (its GPU
+    legs run only on a GPU, so a missing constant would surface only there)."""
+    import ast
+    import builtins
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    defined = set(dir(builtins)) | {"__file__"}
+    for node in ast.walk(tree):
+        if isinstance(node, (ast.FunctionDef, ast.ClassDef)):
+            defined.add(node.name)
+        elif isinstance(node, (ast.Import, ast.ImportFrom)):
+            defined.update((a.asname or a.name).split(".")[0] for a in node.names)
+        elif isinstance(node, ast.arg):
+            defined.add(node.arg)
+        elif isinstance(node, ast.ExceptHandler) and node.name:
+            defined.add(node.name)
+        elif isinstance(node, ast.Name) and isinstance(node.ctx, ast.Store):
+            defined.add(node.id)
+    used = {n.id for n in ast.walk(tree) if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load)}
+    assert sorted(used - defined) == []
