@@ -577,6 +577,69 @@ def measure_active(ras, torch, dev, stream):
     return out
 
 
+def measure_cube(ras, torch, dev, stream):
+    """The unit cube (7-point stencil) through ras_create3: RASPEN_eps solves
+    of the 63^3 workload (11 x 11 x 8 boxes, overlap 1) in mixed precision and
+    FP64 (one warm-up solve each, then one timed with CUDA events), the
+    mixed-vs-FP64 per-field error, and the 23^3 workload against the oracle's
+    own solve of it (per-field errors and equal outer / Krylov / local counts)."""
+    import numpy as np
+    from oracle import ras as oras
+    from oracle import three_d as t3
+    from paper_2411_00546_gb300 import inputs
+
+    def solve(cfg, prec):
+        n = cfg["n"]
+        yd = torch.tensor(inputs.make_yd3(cfg), dtype=torch.float64, device=dev)
+        o = ras.make_opts(tol=cfg["tol"], inner_tol=cfg["inner_tol"], sigma=cfg["sigma"], eps0=cfg["eps0"],
+                          gamma=cfg["gamma"], eps_min=cfg["eps_min"], precision=prec, kappa=cfg["kappa"])
+        h = ras.ras_create3(n, cfg["sx"], cfg["sy"], cfg["sz"], cfg["overlap"], cfg["phi"], cfg["nu"], cfg["mu"],
+                            yd, None, o, stream=stream.cuda_stream)
+        y = torch.zeros((n, n, n), dtype=torch.float64, device=dev)
+        p = torch.zeros_like(y)
+        for rep_ in range(2):
+            with torch.cuda.stream(stream):
+                y.zero_()
+                p.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rc, st = ras.ras_raspen_solve(h, y, p, check=False)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+        nsub = ras.ras_subdomain_count(h)
+        ras.ras_destroy(h)
+        ms = a.elapsed_time(b)
+        return y.cpu().numpy(), p.cpu().numpy(), {
+            "status": rc, "ms": round(ms, 2), "solves_per_s": 1e3 / ms, "boxes": nsub,
+            "unknowns_per_s": 2.0 * n ** 3 * 1e3 / ms, "outer_its": st.outer_its, "gmres_its": st.gmres_its,
+            "evaluations": st.evaluations, "inner_its_sum": st.inner_its_sum}
+
+    out = {}
+    cfg = inputs.problem3("c63")
+    ym, pm, rm = solve(cfg, ras.RAS_MIXED)
+    y6, p6, r6 = solve(cfg, ras.RAS_FP64)
+    rm.update({"err_vs_fp64_y": field_err(ym, y6), "err_vs_fp64_p": field_err(pm, p6),
+               "active_fraction": float(np.mean(np.abs(p6) > cfg["mu"]))})
+    out["c63"] = {"workload": "63^3 cube, 11 x 11 x 8 boxes, overlap 1, y^3, nu 1e-5, mu 1e-3",
+                  "mixed": rm, "fp64": r6}
+    cfg = inputs.problem3("c23")
+    prob = t3.Problem(cfg["n"], cfg["phi"], cfg["nu"], cfg["mu"], inputs.make_yd3(cfg), kappa=cfg["kappa"])
+    t0 = time.time()
+    ref = t3.raspen(prob, cfg["sx"], cfg["sy"], cfg["sz"], cfg["overlap"],
+                    oras.Options(tol=cfg["tol"], inner_tol=cfg["inner_tol"], sigma=cfg["sigma"], eps0=cfg["eps0"],
+                                 gamma=cfg["gamma"], eps_min=cfg["eps_min"]))
+    oracle_s = time.time() - t0
+    c23 = {"workload": "23^3 cube, 4 x 4 x 4 boxes, overlap 1", "oracle_solve_s": round(oracle_s, 2)}
+    for prec, name in ((ras.RAS_MIXED, "mixed"), (ras.RAS_FP64, "fp64")):
+        Y, P, r = solve(cfg, prec)
+        r.update({"err_vs_oracle_y": field_err(Y, ref.Y), "err_vs_oracle_p": field_err(P, ref.P),
+                  "counts_equal": bool(r["outer_its"] == ref.outer and r["gmres_its"] == sum(ref.gmres_its)
+                                       and r["inner_its_sum"] == sum(sum(i) for i in ref.inner_its))})
+        c23[name] = r
+    out["c23"] = c23
+    return out
+
+
 def measure_methods(ras, torch, dev, stream):
     """The paper's method comparison (Sec. 5, its tables of outer / GMRES /
     inner counts and times) on the n255 workload in mixed precision: RASPEN,
@@ -652,6 +715,7 @@ def parse_args():
     ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--no-active", action="store_true")
     ap.add_argument("--no-sensitivity", action="store_true")
+    ap.add_argument("--no-cube", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",
                     help="GMRES cycles step by step (every kernel visible to a profiler's launch list)")
     ap.add_argument("--serve-requests", type=int, default=32)
@@ -1187,6 +1251,9 @@ def main():
     sensitivity = None
     if rank == 0 and not args.no_sensitivity:
         sensitivity = measure_sensitivity(ras, torch, dev, stream)
+    cube = None
+    if rank == 0 and not args.no_cube:
+        cube = measure_cube(ras, torch, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -1240,7 +1307,7 @@ def main():
                           "kernels": kernels, "kernel_rooflines": kernel_rooflines,
                           "uneven_batch": batch, "serving": serving, "methods": methods, "n255_family": cfg2,
                           "sweeps": sweeps, "paper_workload": paper, "n1023_active": active,
-                          "sensitivity": sensitivity,
+                          "sensitivity": sensitivity, "cube": cube,
                           "autotune": autotune,
                           "y_max": float(np.abs(y_mixed).max()),
                           "p_max": float(np.abs(p_mixed).max())},

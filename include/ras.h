@@ -145,6 +145,27 @@ int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu
                const double* y_d, const double* f, const ras_opts* o,
                void* stream, ras_problem** out);
 
+/* Create a problem on the unit cube (Assumption 1 allows Omega in R^2 or R^3;
+ * Sec. 2): an n x n x n grid of interior nodes, the 7-point stencil
+ * A = -Laplace (beta (6 z - the six neighbours), beta = (n+1)^2), split into
+ * sx x sy x sz non-overlapping boxes (balanced sizes, larger first; box index
+ * (bz*sy + by)*sx + bx), each grown by `overlap` node layers and clipped.
+ * Grid functions are n^3 FP64 with x1 fastest, then x2, then x3 (node
+ * (i, j, k) at (k*n + j)*n + i); y_d and f as in ras_create with n^3 entries.
+ * The local Jacobian of a box is block tridiagonal over its x3 planes, so
+ * every box plane must have 2*wx*wy <= 160 unknowns (wx, wy = box extents
+ * along x1 and x2, overlap included) -> RAS_EINVAL otherwise; 1 <= sz <= n.
+ * Every call that takes a handle works on the result (vectors of 2*n^3, or
+ * n^3 per field) except ras_residual_static, the batch and the server, which
+ * describe square problems only. */
+int ras_create3(int n, int sx, int sy, int sz, int overlap, int phi, double nu, double mu,
+                const double* y_d, const double* f, const ras_opts* o,
+                void* stream, ras_problem** out);
+
+/* 2 for a handle made by ras_create / ras_batch_create (the square), 3 for
+ * one made by ras_create3 (the cube); RAS_EINVAL on NULL. */
+int ras_problem_dim(const ras_problem* h);
+
 /* A batch of independent problems in one handle (many problems of uneven
  * grid size, one launch per sweep step for all of them). Each entry describes one problem
  * exactly like the arguments of ras_create; y_d and f are device pointers,

@@ -46,13 +46,14 @@ using ras::SubDev;
 struct ras_problem {
     int nprob = 0;
     std::vector<ras_problem_desc> desc;
+    std::vector<int> sz;      // per problem: subdomains along x3 on the cube, 0 on the square
     ras_opts o{};
     cudaStream_t st = nullptr;
     int nsub = 0, maxm = 0;
-    long long L = 0;          // length of a global vector (sum of 2 n_k^2)
-    long long Lsum = 0;       // sum of 2*wx*wy
-    long long Nsum = 0;       // sum of wx*wy
-    long long Gsum = 0;       // sum of wy*mp^2
+    long long L = 0;          // length of a global vector (sum of 2 nn_k)
+    long long Lsum = 0;       // sum of 2*wx*wy*wz
+    long long Nsum = 0;       // sum of wx*wy*wz
+    long long Gsum = 0;       // sum of bw*mp^2
     std::vector<SubDev> subs;
     std::vector<ProbDev> probs;
     std::vector<Seg> segs;
@@ -359,16 +360,17 @@ int check_err_stats(ras_problem* h, ras_stats* stats, int count) {
 
 size_t prec_bytes(const ras_problem* h) { return h->o.precision == RAS_MIXED ? sizeof(float) : sizeof(double); }
 
-// Algorithmic work of a factorisation: 16 wx^3 wy flops per subdomain (block-
-// tridiagonal Gauss-Jordan = no-fill band LU count). With `ls`: only active
+// Algorithmic work of a factorisation: 16 bl^3 bw flops per subdomain (block-
+// tridiagonal Gauss-Jordan = no-fill band LU count; bl nodes per block row,
+// bw block rows). With `ls`: only active
 // subdomains, or (skip_skipped) all but those of non-participating problems.
 double factor_flops(const ras_problem* h, const std::vector<LocalState>* ls, bool skip_skipped) {
     double w = 0.0;
     for (int i = 0; i < h->nsub; ++i) {
         if (ls && !skip_skipped && !(*ls)[i].active) continue;
         if (ls && skip_skipped && (*ls)[i].status == ras::ST_SKIP) continue;
-        const double wx = h->subs[i].wx, wy = h->subs[i].wy;
-        w += 16.0 * wx * wx * wx * wy;
+        const double bl = h->subs[i].bl, bw = h->subs[i].bw;
+        w += 16.0 * bl * bl * bl * bw;
     }
     return w;
 }
@@ -379,12 +381,12 @@ double solve_bytes(const ras_problem* h, const std::vector<int>* mask) {
     for (int i = 0; i < h->nsub; ++i) {
         const SubDev& s = h->subs[i];
         if (mask && !(*mask)[s.prob]) continue;
-        b += 2.0 * (double)s.wy * s.mp * s.mp * (double)prec_bytes(h);
+        b += 2.0 * (double)s.bw * s.mp * s.mp * (double)prec_bytes(h);
     }
     return b;
 }
 
-long long plane(const ras_problem* h, int p) { return (long long)h->probs[p].n * h->probs[p].n; }
+long long plane(const ras_problem* h, int p) { return h->probs[p].nn; }
 
 double resid_bytes(const ras_problem* h) { return (h->f ? 48.0 : 40.0) * (double)plane(h, 0); }
 
@@ -753,7 +755,7 @@ int ras_apply_T(ras_problem* h, const std::vector<double>& pstart, double* Fout,
             double bytes = 0.0;
             for (int i = 0; i < h->nsub; ++i) {
                 const double mp = h->subs[i].mp;
-                bytes += (after[i].solves - before[i].solves) * 2.0 * mp * mp * h->subs[i].wy * sizeof(T);
+                bytes += (after[i].solves - before[i].solves) * 2.0 * mp * mp * h->subs[i].bw * sizeof(T);
             }
             h->prof_recs[dir_rec - 1].work = bytes;
         }
@@ -1730,9 +1732,11 @@ bool desc_valid(const ras_problem_desc& d) {
 // Host-side layout of a set of problems: problem and subdomain descriptors,
 // segment offsets of the global vectors, offsets into the local pools and
 // the register-tile classes. The y_d / f pointers are set by the caller.
-int build_layout(ras_problem* h, int count, const ras_problem_desc* pd) {
+int build_layout(ras_problem* h, int count, const ras_problem_desc* pd, const int* sz = nullptr) {
     h->nprob = count;
     h->desc.assign(pd, pd + count);
+    h->sz.assign(count, 0);
+    if (sz) h->sz.assign(sz, sz + count);
     h->probs.clear();
     h->segs.clear();
     h->subs.clear();
@@ -1743,42 +1747,63 @@ int build_layout(ras_problem* h, int count, const ras_problem_desc* pd) {
     for (int p = 0; p < count; ++p) {
         const ras_problem_desc& d = pd[p];
         const int n = d.n;
+        const bool cube = h->sz[p] > 0;
         ProbDev P{};
         P.n = n;
+        P.nz = cube ? n : 1;
+        P.nn = (long long)n * n * P.nz;
         P.phi = d.phi;
         P.h = 1.0 / (n + 1);
         P.beta = 1.0 / (P.h * P.h);
+        P.diag = (cube ? 6.0 : 4.0) * P.beta;
         P.nu = d.nu;
         P.mu = d.mu;
         P.kappa = h->o.kappa;
         P.ofs = vec;
         h->probs.push_back(P);
-        h->segs.push_back(Seg{vec, 2LL * n * n});
+        h->segs.push_back(Seg{vec, 2 * P.nn});
         h->sub_first.push_back((int)h->subs.size());
         const auto bx = split_blocks(n, d.sx), by = split_blocks(n, d.sy);
-        for (int j = 0; j < d.sy; ++j) {
-            for (int i = 0; i < d.sx; ++i) {
-                SubDev s{};
-                s.prob = p;
-                s.ox0 = bx[i].first; s.owx = bx[i].second - bx[i].first;
-                s.oy0 = by[j].first; s.owy = by[j].second - by[j].first;
-                s.x0 = std::max(0, s.ox0 - d.overlap);
-                s.y0 = std::max(0, s.oy0 - d.overlap);
-                s.wx = std::min(n, bx[i].second + d.overlap) - s.x0;
-                s.wy = std::min(n, by[j].second + d.overlap) - s.y0;
-                s.mp = ((2 * s.wx + 31) / 32) * 32;
-                s.voff = voff; s.noff = noff; s.goff = goff;
-                voff += 2LL * s.wx * s.wy;
-                noff += (long long)s.wx * s.wy;
-                goff += (long long)s.wy * s.mp * s.mp;
-                h->maxm = std::max(h->maxm, 2 * s.wx);
-                h->subs.push_back(s);
+        const auto bz = cube ? split_blocks(n, h->sz[p]) : std::vector<std::pair<int, int>>{{0, 1}};
+        for (int k = 0; k < (int)bz.size(); ++k) {
+            for (int j = 0; j < d.sy; ++j) {
+                for (int i = 0; i < d.sx; ++i) {
+                    SubDev s{};
+                    s.prob = p;
+                    s.ox0 = bx[i].first; s.owx = bx[i].second - bx[i].first;
+                    s.oy0 = by[j].first; s.owy = by[j].second - by[j].first;
+                    s.oz0 = bz[k].first; s.owz = bz[k].second - bz[k].first;
+                    s.x0 = std::max(0, s.ox0 - d.overlap);
+                    s.y0 = std::max(0, s.oy0 - d.overlap);
+                    s.wx = std::min(n, bx[i].second + d.overlap) - s.x0;
+                    s.wy = std::min(n, by[j].second + d.overlap) - s.y0;
+                    if (cube) {
+                        s.z0 = std::max(0, s.oz0 - d.overlap);
+                        s.wz = std::min(n, bz[k].second + d.overlap) - s.z0;
+                        s.bl = s.wx * s.wy;
+                        s.bw = s.wz;
+                    } else {
+                        s.z0 = 0;
+                        s.wz = 1;
+                        s.bl = s.wx;
+                        s.bw = s.wy;
+                    }
+                    s.mp = ((2 * s.bl + 31) / 32) * 32;
+                    s.voff = voff; s.noff = noff; s.goff = goff;
+                    voff += 2LL * s.wx * s.wy * s.wz;
+                    noff += (long long)s.wx * s.wy * s.wz;
+                    goff += (long long)s.bw * s.mp * s.mp;
+                    h->maxm = std::max(h->maxm, 2 * s.bl);
+                    h->subs.push_back(s);
+                }
             }
         }
         h->sub_count.push_back((int)h->subs.size() - h->sub_first.back());
-        vec += 2LL * n * n;
+        vec += 2 * P.nn;
     }
-    if (h->maxm > ras::MAX_M) return fail(h, RAS_EINVAL, "a subdomain is wider than 80 nodes (2 wx > 160)");
+    if (h->maxm > ras::MAX_M)
+        return fail(h, RAS_EINVAL,
+                    "a local block row has more than 160 unknowns (2 wx > 160; on the cube 2 wx wy > 160)");
     h->nsub = (int)h->subs.size();
     h->Lsum = voff; h->Nsum = noff; h->Gsum = goff; h->L = vec;
     // register-tile classes of the FP32 factorisation: tile = mp / 16
@@ -1873,12 +1898,12 @@ int upload_layout(ras_problem* h) {
     ++h->gen;
     if (h->own_factors) fill_pointers(h);
     TRY(build_grid(h, 2, std::vector<int>(h->nprob, 1)));
-    // solve order: largest factor (wy * mp^2) first, ties by index
+    // solve order: largest factor (bw * mp^2) first, ties by index
     std::vector<int> order(h->nsub);
     for (int k = 0; k < h->nsub; ++k) order[k] = k;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return (long long)h->subs[a].wy * h->subs[a].mp * h->subs[a].mp >
-               (long long)h->subs[b].wy * h->subs[b].mp * h->subs[b].mp;
+        return (long long)h->subs[a].bw * h->subs[a].mp * h->subs[a].mp >
+               (long long)h->subs[b].bw * h->subs[b].mp * h->subs[b].mp;
     });
     CK(cudaMemcpyAsync(h->d_order, order.data(), h->nsub * sizeof(int), cudaMemcpyHostToDevice, h->st));
     TRY(sync(h));
@@ -1891,9 +1916,10 @@ int upload_layout(ras_problem* h) {
     return RAS_OK;
 }
 
-}  // namespace
-
-int ras_batch_create(int count, const ras_problem_desc* pd, const ras_opts* o, void* stream, ras_problem** out) {
+// A handle for `count` problems; sz (null: all on the square) gives per
+// problem the subdomains along x3 of a cube problem, 0 for the square.
+int create_internal(int count, const ras_problem_desc* pd, const int* sz, const ras_opts* o, void* stream,
+                    ras_problem** out) {
     if (!out) return RAS_EINVAL;
     *out = nullptr;
     if (count < 1 || count > 4096 || !pd) return RAS_EINVAL;
@@ -1904,13 +1930,13 @@ int ras_batch_create(int count, const ras_problem_desc* pd, const ras_opts* o, v
     else ras_default_opts(&h->o);
     h->st = (cudaStream_t)stream;
     int rc = validate_opts(h, h->o);
-    if (rc == RAS_OK) rc = build_layout(h, count, pd);
+    if (rc == RAS_OK) rc = build_layout(h, count, pd, sz);
     if (rc == RAS_OK) rc = ensure_pools(h, true);
     if (rc != RAS_OK) {
         ras_destroy(h);
         return rc;
     }
-    // y_d and f of problem p at the plane offset sum_{q<p} n_q^2
+    // y_d and f of problem p at the plane offset sum_{q<p} nn_q
     long long poff = 0;
     cudaError_t e = cudaSuccess;
     for (int p = 0; p < count && e == cudaSuccess; ++p) {
@@ -1931,6 +1957,27 @@ int ras_batch_create(int count, const ras_problem_desc* pd, const ras_opts* o, v
     }
     *out = h;
     return RAS_OK;
+}
+
+}  // namespace
+
+int ras_batch_create(int count, const ras_problem_desc* pd, const ras_opts* o, void* stream, ras_problem** out) {
+    return create_internal(count, pd, nullptr, o, stream, out);
+}
+
+int ras_create3(int n, int sx, int sy, int sz, int overlap, int phi, double nu, double mu, const double* y_d,
+                const double* f, const ras_opts* o, void* stream, ras_problem** out) {
+    if (out) *out = nullptr;
+    if (sz < 1 || sz > n) return RAS_EINVAL;
+    ras_problem_desc d{};
+    d.n = n; d.sx = sx; d.sy = sy; d.overlap = overlap; d.phi = phi; d.nu = nu; d.mu = mu;
+    d.y_d = y_d; d.f = f;
+    return create_internal(1, &d, &sz, o, stream, out);
+}
+
+int ras_problem_dim(const ras_problem* h) {
+    if (!h) return RAS_EINVAL;
+    return h->probs[0].nz > 1 ? 3 : 2;
 }
 
 int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu, const double* y_d,

@@ -4,10 +4,11 @@
 // One CTA owns one subdomain i for the whole launch. The local problem is
 //   K_i(c) = R_i F_eps(x + P_i c) = 0                          (Sec. 4.2)
 // solved by Alg. 1 from c = 0. Its Jacobian J_i = R_i F'(x + P_i c) P_i in the
-// interleaved (y, p) ordering, grouped by grid rows of Omega_i, is block
-// tridiagonal: diagonal blocks D_j (one grid row, m = 2 wx unknowns) and
-// off-diagonal blocks -beta I (the 5-point coupling between neighbouring rows,
-// beta = 1/h^2, the same for both fields). Its block LU therefore only needs
+// interleaved (y, p) ordering, grouped by grid rows of Omega_i (planes on the
+// cube), is block tridiagonal: diagonal blocks D_j (one grid row or plane,
+// m = 2 bl unknowns) and off-diagonal blocks -beta I (the stencil's coupling
+// between neighbouring rows or planes, beta = 1/h^2, the same for both
+// fields). Its block LU therefore only needs
 //   S_0 = D_0,  S_j = D_j - beta^2 S_{j-1}^-1,
 // and the factor stores G_j = S_j^-1 (in the packed order of packed_index),
 // computed by Gauss-Jordan elimination with partial pivoting inside each
@@ -22,12 +23,13 @@ constexpr int NT = LOC_THREADS;
 constexpr int NW = NT / 32;
 constexpr double U_ROUND = 1.1102230246251565e-16;  // 2^-53
 
-// Value of the local state at local node (lx, ly), field f:
-// x + c + alpha d on Omega_i, x on the ring outside it, 0 outside the grid.
+// Value of the local state at local node (lx, ly), field f (square), or
+// (lx, ly, lz) (cube): x + c + alpha d on Omega_i, x on the ring outside it,
+// 0 outside the grid.
 struct LocalView {
     const double* X;   // y-plane of this problem; p-plane at X + nn
     long long nn;
-    int n, x0, y0, wx, wy;
+    int n, nz, x0, y0, z0, wx, wy, wz;
     const double* c;
     const double* d;   // may be null
     double alpha;
@@ -44,15 +46,37 @@ struct LocalView {
         }
         return v;
     }
+
+    __device__ __forceinline__ double val3(int lx, int ly, int lz, int f) const {
+        const int gi = x0 + lx, gj = y0 + ly, gk = z0 + lz;
+        if (gi < 0 || gi >= n || gj < 0 || gj >= n || gk < 0 || gk >= nz) return 0.0;
+        double v = X[f * nn + ((long long)gk * n + gj) * n + gi];
+        if (lx >= 0 && lx < wx && ly >= 0 && ly < wy && lz >= 0 && lz < wz) {
+            const int lq = 2 * ((lz * wy + ly) * wx + lx) + f;
+            double cc = c[lq];
+            if (d) cc = fma(alpha, d[lq], cc);
+            v += cc;
+        }
+        return v;
+    }
+
+    // the state at local node q of Omega_i itself (either geometry)
+    __device__ __forceinline__ double at(int q, int f) const {
+        const int lx = q % wx, r = q / wx, ly = r % wy, lz = r / wy;
+        double cc = c[2 * q + f];
+        if (d) cc = fma(alpha, d[2 * q + f], cc);
+        return X[f * nn + ((long long)(z0 + lz) * n + (y0 + ly)) * n + (x0 + lx)] + cc;
+    }
 };
 
 __device__ __forceinline__ LocalView make_view(const SubDev& s, const ProbDev& P, const double* X,
                                                const double* c, const double* d, double alpha) {
     LocalView V;
     V.X = X + P.ofs;
-    V.nn = (long long)P.n * P.n;
+    V.nn = P.nn;
     V.n = P.n;
-    V.x0 = s.x0; V.y0 = s.y0; V.wx = s.wx; V.wy = s.wy;
+    V.nz = P.nz;
+    V.x0 = s.x0; V.y0 = s.y0; V.z0 = s.z0; V.wx = s.wx; V.wy = s.wy; V.wz = s.wz;
     V.c = c; V.d = d; V.alpha = alpha;
     return V;
 }
@@ -64,9 +88,48 @@ __device__ __forceinline__ LocalView make_view(const SubDev& s, const ProbDev& P
 // reads it only at eps_min, so callers ask for it only there; else 0).
 __device__ void local_residual(const LocalView& V, const ProbDev& P, double eps, double* out,
                                double& nrm2, double& flr2, double* red, bool with_floor) {
-    const int wx = V.wx, nn = wx * V.wy;
+    const int wx = V.wx, nn = wx * V.wy * V.wz;
     const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu, imu = 1.0 / P.mu, munu = P.mu / P.nu;
     double a = 0.0, b = 0.0;
+    if (V.nz > 1) {
+        // the cube: 7-point stencil, beta (6 z - sum of the six neighbours)
+        for (int q = threadIdx.x; q < nn; q += NT) {
+            const int lx = q % wx, r = q / wx, ly = r % V.wy, lz = r / V.wy;
+            const long long g = ((long long)(V.z0 + lz) * V.n + (V.y0 + ly)) * V.n + (V.x0 + lx);
+            const double yc = V.val3(lx, ly, lz, 0), pc = V.val3(lx, ly, lz, 1);
+            const double yw = V.val3(lx - 1, ly, lz, 0), ye = V.val3(lx + 1, ly, lz, 0);
+            const double ys = V.val3(lx, ly - 1, lz, 0), yn = V.val3(lx, ly + 1, lz, 0);
+            const double yb = V.val3(lx, ly, lz - 1, 0), yt = V.val3(lx, ly, lz + 1, 0);
+            const double pw = V.val3(lx - 1, ly, lz, 1), pe = V.val3(lx + 1, ly, lz, 1);
+            const double ps = V.val3(lx, ly - 1, lz, 1), pn = V.val3(lx, ly + 1, lz, 1);
+            const double pb = V.val3(lx, ly, lz - 1, 1), pt = V.val3(lx, ly, lz + 1, 1);
+            double ph, d1, d2;
+            phi_eval(P.phi, P.kappa, yc, ph, d1, d2);
+            const double fv = P.f ? P.f[g] : 0.0;
+            const double xq = -pc * imu;
+            const double dq = P_eps_minus_id(xq, eps);
+            const double Fy = beta * (6.0 * yc - yw - ye - ys - yn - yb - yt) + ph - fv + munu * dq;
+            const double Fp = beta * (6.0 * pc - pw - pe - ps - pn - pb - pt) + d1 * pc - yc + P.yd[g];
+            if (with_floor) {
+                const double My = beta * (6.0 * fabs(yc) + fabs(yw) + fabs(ye) + fabs(ys) + fabs(yn) + fabs(yb) +
+                                          fabs(yt)) +
+                                  fabs(ph) + fabs(fv) + inu * (fabs(pc) + mu * fabs(xq + dq));
+                const double Mp = beta * (6.0 * fabs(pc) + fabs(pw) + fabs(pe) + fabs(ps) + fabs(pn) + fabs(pb) +
+                                          fabs(pt)) +
+                                  fabs(d1 * pc) + fabs(yc) + fabs(P.yd[g]);
+                b += My * My + Mp * Mp;
+            }
+            if (out) {
+                out[2 * q] = Fy;
+                out[2 * q + 1] = Fp;
+            }
+            a += Fy * Fy + Fp * Fp;
+        }
+        block_sum2<NT>(a, b, red);
+        nrm2 = a;
+        flr2 = b;
+        return;
+    }
     for (int q = threadIdx.x; q < nn; q += NT) {
         const int lx = q % wx, ly = q / wx;
         const long long g = (long long)(V.y0 + ly) * V.n + (V.x0 + lx);
@@ -150,7 +213,7 @@ __global__ void __launch_bounds__(NT) k_local_init(int nsub, const SubDev* __res
         }
         return;
     }
-    const int L = 2 * s.wx * s.wy;
+    const int L = 2 * s.wx * s.wy * s.wz;
     double* c = cpool + s.voff;
     for (int q = threadIdx.x; q < L; q += NT) c[q] = 0.0;
     __syncthreads();
@@ -192,7 +255,8 @@ __global__ void __launch_bounds__(FACT_THREADS) k_local_factor(int nsub, int max
     if (ls[i].status == ST_SKIP) return;
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
-    const int m = 2 * s.wx, W = s.wy, nn = s.wx * s.wy, LD = maxm + 1;
+    const int m = 2 * s.bl, W = s.bw, nn = s.wx * s.wy * s.wz, LD = maxm + 1;
+    const bool cube = P.nz > 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     T* M = reinterpret_cast<T*>(smem_raw);
     T* colk = M + (size_t)maxm * LD;
@@ -211,8 +275,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_local_factor(int nsub, int max
         const double* c = cpool + s.voff;
         const LocalView V = make_view(s, P, X, c, nullptr, 0.0);
         for (int q = tid; q < nn; q += FACT_THREADS) {
-            const int lx = q % s.wx, ly = q / s.wx;
-            const double y = V.val(lx, ly, 0), p = V.val(lx, ly, 1);
+            const double y = V.at(q, 0), p = V.at(q, 1);
             double ph, d1, d2;
             phi_eval(P.phi, P.kappa, y, ph, d1, d2);
             ca[q] = d1;
@@ -223,7 +286,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_local_factor(int nsub, int max
     if (tid == 0) sh_fail = 0;
     __syncthreads();
 
-    const T tbeta = (T)beta, tbeta2 = (T)(beta * beta), tdiag = (T)(4.0 * beta);
+    const T tbeta = (T)beta, tbeta2 = (T)(beta * beta), tdiag = (T)P.diag;
     T* G = static_cast<T*>(s.gptr);
     for (int j = 0; j < W; ++j) {
         // S_j = D_j - beta^2 G_{j-1}
@@ -231,7 +294,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_local_factor(int nsub, int max
         const T* Gp = G + (long long)(j > 0 ? j - 1 : 0) * blk;
         for (int r = warp; r < m; r += FW) {
             const int ix = r >> 1, f = r & 1;
-            const int q = j * s.wx + ix;
+            const int q = j * s.bl + ix;
             for (int cidx = lane; cidx < m; cidx += 32) {
                 const int cx = cidx >> 1, cf = cidx & 1;
                 T v = (j > 0) ? -tbeta2 * Gp[packed_index<T>(r, cidx, s.mp)] : (T)0;
@@ -239,7 +302,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_local_factor(int nsub, int max
                     if (cf == f) v += tdiag + (T)ca[q];
                     else if (f == 0) v += (T)cb[q];
                     else v += (T)cc[q];
-                } else if (cf == f && (cx == ix - 1 || cx == ix + 1)) {
+                } else if (cf == f && row_neighbour(ix, cx, s.wx, cube)) {
                     v -= tbeta;
                 }
                 M[r * LD + cidx] = v;
@@ -330,7 +393,7 @@ __global__ void __launch_bounds__(NT) k_local_linesearch(int nsub, const SubDev*
     if (!L.active) return;
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
-    const int len = 2 * s.wx * s.wy;
+    const int len = 2 * s.wx * s.wy * s.wz;
     double* c = cpool + s.voff;
     const double* d = dpool + s.voff;
     double* K = Kpool + s.voff;
@@ -382,14 +445,15 @@ __global__ void __launch_bounds__(NT) k_local_prolong(int nsub, const SubDev* __
     if (ls[i].status == ST_SKIP) return;
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
-    const long long nn = (long long)P.n * P.n;
+    const long long nn = P.nn;
     double* Fy = F + P.ofs;
     const double* c = cpool + s.voff;
-    const int no = s.owx * s.owy;
+    const int no = s.owx * s.owy * s.owz;
     for (int q = threadIdx.x; q < no; q += NT) {
-        const int gx = s.ox0 + q % s.owx, gy = s.oy0 + q / s.owx;
-        const int lq = (gy - s.y0) * s.wx + (gx - s.x0);
-        const long long g = (long long)gy * P.n + gx;
+        const int r = q / s.owx;
+        const int gx = s.ox0 + q % s.owx, gy = s.oy0 + r % s.owy, gz = s.oz0 + r / s.owy;
+        const int lq = ((gz - s.z0) * s.wy + (gy - s.y0)) * s.wx + (gx - s.x0);
+        const long long g = grid_index(P, gx, gy, gz);
         Fy[g] = c[2 * lq];
         Fy[nn + g] = c[2 * lq + 1];
     }
@@ -442,6 +506,37 @@ __device__ __forceinline__ void add_band(float (&Mr)[R][R], int ty, int m, int w
             else if (off == 1 && (a & 1) == 0) Mr[a][b] += (float)cb[q];
             else if (off == -1 && (a & 1) == 1) Mr[a][b] += (float)cc[q];
             else if (off == 2 || off == -2) Mr[a][b] -= tbeta;
+        }
+    }
+}
+
+// Entries of D_j on the cube (one plane of bl = wx*wy nodes) inside the tile
+// of thread (ty, tx), rows ty*R + a and columns tx*R + b: the 2 x 2 node
+// blocks on the diagonal as in add_band (6 beta + phi' on the diagonal) and
+// -beta at the in-plane neighbours of the same field, node offsets +-1 within
+// a grid line and +-wx, which reach tiles away from the diagonal.
+template <int R>
+__device__ __forceinline__ void add_plane(float (&Mr)[R][R], int ty, int tx, int m, int bl, int wx, int j,
+                                          float tdiag, float tbeta, const double* ca, const double* cb,
+                                          const double* cc) {
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        const int r = ty * R + a;
+        if (r >= m) continue;
+        const int ix = r >> 1, f = r & 1;
+        const int q = j * bl + ix;
+#pragma unroll
+        for (int b = 0; b < R; ++b) {
+            const int c = tx * R + b;
+            if (c >= m) continue;
+            const int cx = c >> 1, cf = c & 1;
+            if (cx == ix) {
+                if (cf == f) Mr[a][b] += tdiag + (float)ca[q];
+                else if (f == 0) Mr[a][b] += (float)cb[q];
+                else Mr[a][b] += (float)cc[q];
+            } else if (cf == f && row_neighbour(ix, cx, wx, true)) {
+                Mr[a][b] -= tbeta;
+            }
         }
     }
 }
@@ -554,7 +649,8 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub
     if (ls[i].status == ST_SKIP) return;
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
-    const int m = 2 * s.wx, W = s.wy, nn = s.wx * s.wy, mp = s.mp;
+    const int m = 2 * s.bl, W = s.bw, nn = s.wx * s.wy * s.wz, mp = s.mp;
+    const bool cube = P.nz > 1;
     const int tid = threadIdx.x, ty = tid & 15, tx = tid >> 4, warp = tid >> 5, lane = tid & 31;
 
     const double eps = ls[i].eps;
@@ -566,8 +662,7 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub
         const double* c = cpool + s.voff;
         const LocalView V = make_view(s, P, X, c, nullptr, 0.0);
         for (int q = tid; q < nn; q += FACT_THREADS) {
-            const int lx = q % s.wx, ly = q / s.wx;
-            const double y = V.val(lx, ly, 0), p = V.val(lx, ly, 1);
+            const double y = V.at(q, 0), p = V.at(q, 1);
             double ph, d1, d2;
             phi_eval(P.phi, P.kappa, y, ph, d1, d2);
             ca[q] = d1;
@@ -578,7 +673,7 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub
     if (tid == 0) sh_fail = 0;
     __syncthreads();   // coefficients visible to the whole CTA
 
-    const float tbeta = (float)beta, tbeta2 = (float)(beta * beta), tdiag = (float)(4.0 * beta);
+    const float tbeta = (float)beta, tbeta2 = (float)(beta * beta), tdiag = (float)P.diag;
     const long long blk = (long long)mp * mp;
     float* G = static_cast<float*>(s.gptr);
     float Mr[R][R];
@@ -589,12 +684,12 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub
     bool failed = false;
     auto dval = [=](int j, int r, int c) -> float {
         const int ix = r >> 1, f = r & 1, cx = c >> 1, cf = c & 1;
-        const int q = j * s.wx + ix;
+        const int q = j * s.bl + ix;
         if (cx == ix) {
             if (cf == f) return tdiag + (float)ca[q];
             return (f == 0) ? (float)cb[q] : (float)cc[q];
         }
-        return (cf == f && (cx == ix - 1 || cx == ix + 1)) ? -tbeta : 0.f;
+        return (cf == f && row_neighbour(ix, cx, s.wx, cube)) ? -tbeta : 0.f;
     };
     for (int j = 0; j < W && !failed; ++j) {
         // S_j = D_j - beta^2 G_{j-1}: the tile holds G_{j-1} (zero for j = 0)
@@ -602,9 +697,10 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub
         for (int a = 0; a < R; ++a)
 #pragma unroll
             for (int b = 0; b < R; ++b) Mr[a][b] = -tbeta2 * Mr[a][b];
-        if (tx == ty) add_band<R, 0>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
-        else if (tx == ty + 1) add_band<R, 1>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
-        else if (tx == ty - 1) add_band<R, -1>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
+        if (cube) add_plane<R>(Mr, ty, tx, m, s.bl, s.wx, j, tdiag, tbeta, ca, cb, cc);
+        else if (tx == ty) add_band<R, 0>(Mr, ty, m, s.bl, j, tdiag, tbeta, ca, cb, cc);
+        else if (tx == ty + 1) add_band<R, 1>(Mr, ty, m, s.bl, j, tdiag, tbeta, ca, cb, cc);
+        else if (tx == ty - 1) add_band<R, -1>(Mr, ty, m, s.bl, j, tdiag, tbeta, ca, cb, cc);
         if (tid == 0) sh_viol = 0;
 
         for (int kt = 0; kt < 16 && kt * R < m; ++kt) {
@@ -848,7 +944,8 @@ __global__ void __launch_bounds__(1024, 1) k_local_factor_wide(int nsub, const S
     if (ls[i].status == ST_SKIP) return;
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
-    const int m = 2 * s.wx, W = s.wy, nn = s.wx * s.wy, mp = s.mp;
+    const int m = 2 * s.bl, W = s.bw, nn = s.wx * s.wy * s.wz, mp = s.mp;
+    const bool cube = P.nz > 1;
     const int tid = threadIdx.x, ty = tid & 31, tx = tid >> 5, warp = tid >> 5, lane = tid & 31;
 
     const double eps = ls[i].eps;
@@ -860,8 +957,7 @@ __global__ void __launch_bounds__(1024, 1) k_local_factor_wide(int nsub, const S
         const double* c = cpool + s.voff;
         const LocalView V = make_view(s, P, X, c, nullptr, 0.0);
         for (int q = tid; q < nn; q += NTH) {
-            const int lx = q % s.wx, ly = q / s.wx;
-            const double y = V.val(lx, ly, 0), p = V.val(lx, ly, 1);
+            const double y = V.at(q, 0), p = V.at(q, 1);
             double ph, d1, d2;
             phi_eval(P.phi, P.kappa, y, ph, d1, d2);
             ca[q] = d1;
@@ -872,7 +968,7 @@ __global__ void __launch_bounds__(1024, 1) k_local_factor_wide(int nsub, const S
     if (tid == 0) sh_fail = 0;
     __syncthreads();   // coefficients visible to the whole CTA
 
-    const float tbeta = (float)beta, tbeta2 = (float)(beta * beta), tdiag = (float)(4.0 * beta);
+    const float tbeta = (float)beta, tbeta2 = (float)(beta * beta), tdiag = (float)P.diag;
     const long long blk = (long long)mp * mp;
     float* G = static_cast<float*>(s.gptr);
     float Mr[R][R];
@@ -883,12 +979,12 @@ __global__ void __launch_bounds__(1024, 1) k_local_factor_wide(int nsub, const S
     bool failed = false;
     auto dval = [=](int j, int r, int c) -> float {
         const int ix = r >> 1, f = r & 1, cx = c >> 1, cf = c & 1;
-        const int q = j * s.wx + ix;
+        const int q = j * s.bl + ix;
         if (cx == ix) {
             if (cf == f) return tdiag + (float)ca[q];
             return (f == 0) ? (float)cb[q] : (float)cc[q];
         }
-        return (cf == f && (cx == ix - 1 || cx == ix + 1)) ? -tbeta : 0.f;
+        return (cf == f && row_neighbour(ix, cx, s.wx, cube)) ? -tbeta : 0.f;
     };
     for (int j = 0; j < W && !failed; ++j) {
         // S_j = D_j - beta^2 G_{j-1}: the tile holds G_{j-1} (zero for j = 0)
@@ -897,11 +993,12 @@ __global__ void __launch_bounds__(1024, 1) k_local_factor_wide(int nsub, const S
 #pragma unroll
             for (int b = 0; b < R; ++b) Mr[a][b] = -tbeta2 * Mr[a][b];
         const int dt = tx - ty;
-        if (dt == 0) add_band_any<R, 0>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
-        else if (dt == 1) add_band_any<R, 1>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
-        else if (dt == -1) add_band_any<R, -1>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
-        else if (R == 1 && dt == 2) add_band_any<R, 2>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
-        else if (R == 1 && dt == -2) add_band_any<R, -2>(Mr, ty, m, s.wx, j, tdiag, tbeta, ca, cb, cc);
+        if (cube) add_plane<R>(Mr, ty, tx, m, s.bl, s.wx, j, tdiag, tbeta, ca, cb, cc);
+        else if (dt == 0) add_band_any<R, 0>(Mr, ty, m, s.bl, j, tdiag, tbeta, ca, cb, cc);
+        else if (dt == 1) add_band_any<R, 1>(Mr, ty, m, s.bl, j, tdiag, tbeta, ca, cb, cc);
+        else if (dt == -1) add_band_any<R, -1>(Mr, ty, m, s.bl, j, tdiag, tbeta, ca, cb, cc);
+        else if (R == 1 && dt == 2) add_band_any<R, 2>(Mr, ty, m, s.bl, j, tdiag, tbeta, ca, cb, cc);
+        else if (R == 1 && dt == -2) add_band_any<R, -2>(Mr, ty, m, s.bl, j, tdiag, tbeta, ca, cb, cc);
         if (tid == 0) sh_viol = 0;
 
         for (int kt = 0; kt < 32 && kt * R < m; ++kt) {

@@ -1,15 +1,21 @@
 // Internal declarations of the RAS / RASPEN CUDA library (sm_103a).
 //
 // Layout in HBM
-//  * grid functions: n*n FP64, row-major, x1 index fastest (node (i, j) at
-//    [j*n + i]); global Krylov vectors are planar [y-plane | p-plane], 2*n*n.
-//  * per subdomain i (box Omega_i of wx*wy nodes at (x0, y0)):
-//      local vectors: 2*wx*wy FP64, interleaved (y, p) per node, nodes
+//  * grid functions: nn = n*n (square) or n*n*n (cube) FP64, x1 index fastest,
+//    then x2, then x3 (node (i, j, k) at [(k*n + j)*n + i], k = 0 on the
+//    square); global Krylov vectors are planar [y-plane | p-plane], 2*nn.
+//  * per subdomain i (box Omega_i of wx*wy*wz nodes at (x0, y0, z0), wz = 1
+//    on the square):
+//      local vectors: 2*wx*wy*wz FP64, interleaved (y, p) per node, nodes
 //                     lexicographic with the x1 index fastest, at voff;
-//      node arrays:   wx*wy FP64 (Jacobian coefficients), at noff;
-//      factors:       wy blocks G_j of mp^2 T (mp = 2wx rounded up to 32, zero
-//                     padded) at goff, where G_j is the inverse of the j-th
-//                     Schur complement of the block-tridiagonal local Jacobian.
+//      node arrays:   wx*wy*wz FP64 (Jacobian coefficients), at noff;
+//      factors:       bw blocks G_j of mp^2 T (mp = 2*bl rounded up to 32,
+//                     zero padded) at goff, where G_j is the inverse of the
+//                     j-th Schur complement of the block-tridiagonal local
+//                     Jacobian. A block row is one grid line of the box on the
+//                     square (bl = wx nodes, bw = wy rows) and one plane of it
+//                     on the cube (bl = wx*wy nodes, bw = wz planes): in both
+//                     the rows couple to their neighbours by -beta I only.
 //                     Each block is stored in the "packed" order of
 //                     packed_index(): the streaming solve reads it as mp/32
 //                     contiguous slabs, one per group of 32 rows, and thread t
@@ -21,34 +27,64 @@
 
 namespace ras {
 
-constexpr int MAX_M = 160;          // max unknowns of one local block row (2*wx)
+constexpr int MAX_M = 160;          // max unknowns of one local block row (2*bl)
 constexpr int FACT_THREADS = 256;   // threads of the factorisation kernel
 constexpr int LOC_THREADS = 256;    // threads of the per-subdomain kernels
 constexpr int VEC_THREADS = 256;    // threads of the grid-stride vector kernels
 constexpr int VEC_BLOCKS = 608;     // 4 x 152 SMs: fixed grid => fixed reduction order
 
 struct ProbDev {
-    int n;
+    int n;                // nodes per grid direction
+    int nz;               // grid planes: 1 on the square, n on the cube
     int phi;
+    int pad_;
     double h, beta, nu, mu, kappa;
+    double diag;          // 2 d beta: diagonal of the (2d+1)-point stencil, d = 2 or 3
+    long long nn;         // grid nodes, n*n*nz
     const double* yd;
     const double* f;      // nullptr means f = 0
     long long ofs;        // offset of this problem's y-plane in every global
-                          // vector buffer; its p-plane follows at ofs + n*n
+                          // vector buffer; its p-plane follows at ofs + nn
 };
 
 struct SubDev {
     int prob;
-    int x0, y0, wx, wy;       // Omega_i
-    int ox0, oy0, owx, owy;   // tilde Omega_i (owned nodes)
-    int mp;                   // 2*wx rounded up to a multiple of 32 (packed block size)
+    int x0, y0, z0, wx, wy, wz;         // Omega_i (z0 = 0, wz = 1 on the square)
+    int ox0, oy0, oz0, owx, owy, owz;   // tilde Omega_i (owned nodes)
+    int bl, bw;               // nodes per block row and block rows (wx, wy; wx*wy, wz on the cube)
+    int mp;                   // 2*bl rounded up to a multiple of 32 (packed block size)
     int pad_;
-    long long goff;           // factor offset (elements of T); wy blocks of mp*mp
-    long long voff;           // local-vector offset (doubles), length 2*wx*wy
-    long long noff;           // node-array offset (doubles), length wx*wy
-    void* gptr;               // this subdomain's factor blocks (wy blocks of mp*mp T)
-    double* cptr;             // its Jacobian coefficients (3 arrays of wx*wy doubles)
+    long long goff;           // factor offset (elements of T); bw blocks of mp*mp
+    long long voff;           // local-vector offset (doubles), length 2*wx*wy*wz
+    long long noff;           // node-array offset (doubles), length wx*wy*wz
+    void* gptr;               // this subdomain's factor blocks (bw blocks of mp*mp T)
+    double* cptr;             // its Jacobian coefficients (3 arrays of wx*wy*wz doubles)
 };
+
+// Local node q of a box -> (lx, ly, lz), x1 index fastest.
+__host__ __device__ __forceinline__ void local_coords(const SubDev& s, int q, int& lx, int& ly, int& lz) {
+    lx = q % s.wx;
+    const int r = q / s.wx;
+    ly = r % s.wy;
+    lz = r / s.wy;
+}
+
+// Global index of grid node (i, j, k) (k = 0 on the square).
+__host__ __device__ __forceinline__ long long grid_index(const ProbDev& P, int i, int j, int k) {
+    return ((long long)k * P.n + j) * P.n + i;
+}
+
+// Is node cx of a block row an in-row stencil neighbour of node ix (the same
+// field)? A block row is a grid line (wx = its length, cube = false) or a
+// plane of wx-node lines (cube = true).
+__host__ __device__ __forceinline__ bool row_neighbour(int ix, int cx, int wx, bool cube) {
+    const int d = cx - ix;
+    if (!cube) return d == 1 || d == -1;
+    if (d == wx || d == -wx) return true;
+    if (d == 1) return ix % wx != wx - 1;
+    if (d == -1) return ix % wx != 0;
+    return false;
+}
 
 // Segment of one problem inside a global vector buffer: [ofs, ofs + len).
 struct Seg {

@@ -74,6 +74,66 @@ __global__ void __launch_bounds__(NT) k_residual_global(ProbDev P, const double*
     }
 }
 
+// The same on the cube (7-point stencil): block b takes the grid lines
+// (j, k) with j + n k = b, b + NB, ...; its threads take the nodes of a line.
+template <bool FLOOR>
+__global__ void __launch_bounds__(NT) k_residual_global3(ProbDev P, const double* __restrict__ y,
+                                                         const double* __restrict__ p,
+                                                         const double* __restrict__ dy,
+                                                         const double* __restrict__ dp, double alpha,
+                                                         double eps, double* Fy, double* Fp,
+                                                         double* partials) {
+    __shared__ double red[2 * NT];
+    const int n = P.n;
+    const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu, imu = 1.0 / P.mu, munu = P.mu / P.nu;
+    auto vy = [=](int i, int j, int k) -> double {
+        if (i < 0 || i >= n || j < 0 || j >= n || k < 0 || k >= n) return 0.0;
+        const long long g = ((long long)k * n + j) * n + i;
+        return dy ? fma(alpha, dy[g], y[g]) : y[g];
+    };
+    auto vp = [=](int i, int j, int k) -> double {
+        if (i < 0 || i >= n || j < 0 || j >= n || k < 0 || k >= n) return 0.0;
+        const long long g = ((long long)k * n + j) * n + i;
+        return dp ? fma(alpha, dp[g], p[g]) : p[g];
+    };
+    double a = 0.0, b = 0.0;
+    for (int jr = blockIdx.x; jr < n * n; jr += NB) {
+        const int j = jr % n, k = jr / n;
+        for (int i = threadIdx.x; i < n; i += NT) {
+            const long long g = ((long long)k * n + j) * n + i;
+            const double yc = vy(i, j, k), pc = vp(i, j, k);
+            const double yw = vy(i - 1, j, k), ye = vy(i + 1, j, k), ys = vy(i, j - 1, k), yn = vy(i, j + 1, k);
+            const double yb = vy(i, j, k - 1), yt = vy(i, j, k + 1);
+            const double pw = vp(i - 1, j, k), pe = vp(i + 1, j, k), ps = vp(i, j - 1, k), pn = vp(i, j + 1, k);
+            const double pb = vp(i, j, k - 1), pt = vp(i, j, k + 1);
+            double ph, d1, d2;
+            phi_eval(P.phi, P.kappa, yc, ph, d1, d2);
+            const double fv = P.f ? P.f[g] : 0.0;
+            const double xq = -pc * imu;
+            const double dq = P_eps_minus_id(xq, eps);
+            const double Fyv = beta * (6.0 * yc - yw - ye - ys - yn - yb - yt) + ph - fv + munu * dq;
+            const double Fpv = beta * (6.0 * pc - pw - pe - ps - pn - pb - pt) + d1 * pc - yc + P.yd[g];
+            if (Fy) Fy[g] = Fyv;
+            if (Fp) Fp[g] = Fpv;
+            a += Fyv * Fyv + Fpv * Fpv;
+            if (FLOOR) {
+                const double My = beta * (6.0 * fabs(yc) + fabs(yw) + fabs(ye) + fabs(ys) + fabs(yn) + fabs(yb) +
+                                          fabs(yt)) +
+                                  fabs(ph) + fabs(fv) + inu * (fabs(pc) + mu * fabs(xq + dq));
+                const double Mp = beta * (6.0 * fabs(pc) + fabs(pw) + fabs(pe) + fabs(ps) + fabs(pn) + fabs(pb) +
+                                          fabs(pt)) +
+                                  fabs(d1 * pc) + fabs(yc) + fabs(P.yd[g]);
+                b += My * My + Mp * Mp;
+            }
+        }
+    }
+    block_sum2<NT>(a, b, red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = a;
+        partials[NB + blockIdx.x] = b;
+    }
+}
+
 // out[v] = sum over the nparts partials of row v, in index order (one warp per row).
 __global__ void k_reduce_partials(const double* __restrict__ partials, int nparts, int nvals,
                                   double* out) {
@@ -90,7 +150,7 @@ __global__ void k_reduce_partials(const double* __restrict__ partials, int npart
 __global__ void __launch_bounds__(NT) k_coef_global(ProbDev P, const double* __restrict__ y,
                                                     const double* __restrict__ p, double eps,
                                                     double* coef) {
-    const long long nn = (long long)P.n * P.n;
+    const long long nn = P.nn;
     const double inu = 1.0 / P.nu, mu = P.mu;
     for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < nn; g += (long long)NB * NT) {
         double ph, d1, d2;
@@ -108,16 +168,26 @@ __global__ void __launch_bounds__(NT) k_jacvec_global(ProbDev P, const double* _
                                                       const double* __restrict__ vp, double* oy,
                                                       double* op) {
     const int n = P.n;
-    const long long nn = (long long)n * n;
+    const long long nn = P.nn, pl = (long long)n * n;
     const double beta = P.beta;
+    const bool cube = P.nz > 1;
     for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < nn; g += (long long)NB * NT) {
-        const int i = (int)(g % n), j = (int)(g / n);
+        const long long gp = g % pl;
+        const int i = (int)(gp % n), j = (int)(gp / n), k = (int)(g / pl);
         const double yc = vy[g], pc = vp[g];
-        const double sy = gval(vy, n, i - 1, j) + gval(vy, n, i + 1, j) + gval(vy, n, i, j - 1) + gval(vy, n, i, j + 1);
-        const double sp = gval(vp, n, i - 1, j) + gval(vp, n, i + 1, j) + gval(vp, n, i, j - 1) + gval(vp, n, i, j + 1);
+        const double* wy = vy + (long long)k * pl;
+        const double* wp = vp + (long long)k * pl;
+        double sy = gval(wy, n, i - 1, j) + gval(wy, n, i + 1, j) + gval(wy, n, i, j - 1) + gval(wy, n, i, j + 1);
+        double sp = gval(wp, n, i - 1, j) + gval(wp, n, i + 1, j) + gval(wp, n, i, j - 1) + gval(wp, n, i, j + 1);
+        double dg = 4.0;
+        if (cube) {
+            dg = 6.0;
+            if (k > 0) { sy += vy[g - pl]; sp += vp[g - pl]; }
+            if (k < n - 1) { sy += vy[g + pl]; sp += vp[g + pl]; }
+        }
         const double a = coef[g], b = coef[nn + g], c = coef[2 * nn + g];
-        oy[g] = beta * (4.0 * yc - sy) + a * yc + b * pc;
-        op[g] = beta * (4.0 * pc - sp) + c * yc + a * pc;
+        oy[g] = beta * (dg * yc - sy) + a * yc + b * pc;
+        op[g] = beta * (dg * pc - sp) + c * yc + a * pc;
     }
 }
 
@@ -472,10 +542,16 @@ cudaError_t launch_residual_global(cudaStream_t st, const ProbDev& P, const doub
                                    const double* dy, const double* dp, double alpha, double eps,
                                    double* Fy, double* Fp, double* partials, int floor) {
     count_launch();
-    if (floor)
+    if (P.nz > 1) {
+        if (floor)
+            k_residual_global3<true><<<NB, NT, 0, st>>>(P, y, p, dy, dp, alpha, eps, Fy, Fp, partials);
+        else
+            k_residual_global3<false><<<NB, NT, 0, st>>>(P, y, p, dy, dp, alpha, eps, Fy, Fp, partials);
+    } else if (floor) {
         k_residual_global<true><<<NB, NT, 0, st>>>(P, y, p, dy, dp, alpha, eps, Fy, Fp, partials);
-    else
+    } else {
         k_residual_global<false><<<NB, NT, 0, st>>>(P, y, p, dy, dp, alpha, eps, Fy, Fp, partials);
+    }
     return cudaGetLastError();
 }
 

@@ -258,24 +258,28 @@ __device__ __forceinline__ int next_position(int* ticket, int* slot) {
 }
 
 // r = bsign * B - J_i z in FP64 with the Jacobian coefficients stored by the
-// factor kernel (5-point coupling inside Omega_i only); returns ||r||^2.
-__device__ double local_linear_residual(const SubDev& s, double beta, const double* coef, double bsign,
-                                        const double* B, const double* z, double* r, double* red) {
-    const int wx = s.wx, wy = s.wy, nn = wx * wy;
+// factor kernel (the stencil's coupling inside Omega_i only; diag = 4 beta on
+// the square, 6 beta on the cube); returns ||r||^2.
+__device__ double local_linear_residual(const SubDev& s, double beta, double diag, const double* coef,
+                                        double bsign, const double* B, const double* z, double* r,
+                                        double* red) {
+    const int wx = s.wx, wy = s.wy, wz = s.wz, nn = wx * wy * wz, pl = wx * wy;
     const double* ca = s.cptr;
     const double* cb = ca + nn;
     const double* cc = cb + nn;
     double r2 = 0.0, dummy = 0.0;
     for (int q = threadIdx.x; q < nn; q += NT) {
-        const int lx = q % wx, ly = q / wx;
+        const int lx = q % wx, rq = q / wx, ly = rq % wy, lz = rq / wy;
         const double zyc = z[2 * q], zpc = z[2 * q + 1];
         double sy = 0.0, sp = 0.0;
         if (lx > 0) { sy += z[2 * (q - 1)]; sp += z[2 * (q - 1) + 1]; }
         if (lx < wx - 1) { sy += z[2 * (q + 1)]; sp += z[2 * (q + 1) + 1]; }
         if (ly > 0) { sy += z[2 * (q - wx)]; sp += z[2 * (q - wx) + 1]; }
         if (ly < wy - 1) { sy += z[2 * (q + wx)]; sp += z[2 * (q + wx) + 1]; }
-        const double Jy = beta * (4.0 * zyc - sy) + ca[q] * zyc + cb[q] * zpc;
-        const double Jp = beta * (4.0 * zpc - sp) + cc[q] * zyc + ca[q] * zpc;
+        if (lz > 0) { sy += z[2 * (q - pl)]; sp += z[2 * (q - pl) + 1]; }
+        if (lz < wz - 1) { sy += z[2 * (q + pl)]; sp += z[2 * (q + pl) + 1]; }
+        const double Jy = beta * (diag * zyc - sy) + ca[q] * zyc + cb[q] * zpc;
+        const double Jp = beta * (diag * zpc - sp) + cc[q] * zyc + ca[q] * zpc;
         const double ry = bsign * B[2 * q] - Jy, rp = bsign * B[2 * q + 1] - Jp;
         r[2 * q] = ry;
         r[2 * q + 1] = rp;
@@ -308,8 +312,8 @@ __global__ void __launch_bounds__(NT) k_local_direction(int nsub, const SubDev* 
     if (!ls[i].active) continue;
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
-    const int m = 2 * s.wx, W = s.wy, L = m * W;
-    const double beta = P.beta;
+    const int m = 2 * s.bl, W = s.bw, L = m * W;
+    const double beta = P.beta, sdiag = P.nz > 1 ? 6.0 : 4.0;
     const double* K = Kpool + s.voff;
     double* d = dpool + s.voff;
     double* r = rpool + s.voff;
@@ -338,7 +342,7 @@ __global__ void __launch_bounds__(NT) k_local_direction(int nsub, const SubDev* 
             return;
         }
         if (it >= np.ir_max) break;
-        const double r2 = local_linear_residual(s, beta, coef, -1.0, K, d, r, red);
+        const double r2 = local_linear_residual(s, beta, sdiag, coef, -1.0, K, d, r, red);
         if (sqrt(r2) <= np.ir_rtol * bnorm) break;
     }
     if (threadIdx.x == 0) ls[i].solves += nsolves;
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(NT) k_local_direction(int nsub, const SubDev* 
 
 // Jacobian action of the RASPEN function (Alg. 4):
 //   O = -D - sum_i tilde P_i J_i(x^(i))^-1 B_i D,  B_i D = R_i A (I - P_i R_i) D,
-// i.e. b = -beta * (sum of D over the 5-point neighbours outside Omega_i).
+// i.e. b = -beta * (sum of D over the stencil neighbours outside Omega_i).
 // With nir > 0 (mixed precision) the local solve is refined nir times in FP64:
 // z += J^-1 (b - J z), J from the coefficients at x^(i).
 template <typename T>
@@ -369,30 +373,38 @@ __global__ void __launch_bounds__(NT) k_local_jvp(int nsub, const SubDev* __rest
     const SubDev s = subs[i];
     if (pmask && !pmask[s.prob]) continue;
     const ProbDev P = probs[s.prob];
-    const int n = P.n, m = 2 * s.wx, W = s.wy;
-    const long long nn = (long long)n * n;
-    const double beta = P.beta;
+    const int n = P.n, nz = P.nz, m = 2 * s.bl, W = s.bw;
+    const long long nn = P.nn;
+    const double beta = P.beta, sdiag = P.nz > 1 ? 6.0 : 4.0;
     const double* Dy = D + P.ofs;
     double* Oy = O + P.ofs;
     const T* G = static_cast<const T*>(s.gptr);
     T* w = wpool + s.voff;
+    // local entry (j, t) is node q = j*bl + t/2 of the box, field t & 1
     auto bval = [=](int j, int t) -> double {
-        const int lx = t >> 1, f = t & 1;
-        const int gx = s.x0 + lx, gy = s.y0 + j;
+        const int f = t & 1;
+        int lx, ly, lz;
+        local_coords(s, j * s.bl + (t >> 1), lx, ly, lz);
+        const int gx = s.x0 + lx, gy = s.y0 + ly, gz = s.z0 + lz;
         const double* Df = Dy + f * nn;
         double b = 0.0;
-        if (lx == 0 && gx > 0) b += Df[(long long)gy * n + gx - 1];
-        if (lx == s.wx - 1 && gx < n - 1) b += Df[(long long)gy * n + gx + 1];
-        if (j == 0 && gy > 0) b += Df[(long long)(gy - 1) * n + gx];
-        if (j == W - 1 && gy < n - 1) b += Df[(long long)(gy + 1) * n + gx];
+        if (lx == 0 && gx > 0) b += Df[grid_index(P, gx - 1, gy, gz)];
+        if (lx == s.wx - 1 && gx < n - 1) b += Df[grid_index(P, gx + 1, gy, gz)];
+        if (ly == 0 && gy > 0) b += Df[grid_index(P, gx, gy - 1, gz)];
+        if (ly == s.wy - 1 && gy < n - 1) b += Df[grid_index(P, gx, gy + 1, gz)];
+        if (lz == 0 && gz > 0) b += Df[grid_index(P, gx, gy, gz - 1)];
+        if (lz == s.wz - 1 && gz < nz - 1) b += Df[grid_index(P, gx, gy, gz + 1)];
         return -beta * b;
     };
     // owned node of local entry (j, t): its global index, else -1
     auto owned = [=](int j, int t) -> long long {
-        const int lx = t >> 1, f = t & 1;
-        const int gx = s.x0 + lx, gy = s.y0 + j;
-        if (gx >= s.ox0 && gx < s.ox0 + s.owx && gy >= s.oy0 && gy < s.oy0 + s.owy)
-            return f * nn + (long long)gy * n + gx;
+        const int f = t & 1;
+        int lx, ly, lz;
+        local_coords(s, j * s.bl + (t >> 1), lx, ly, lz);
+        const int gx = s.x0 + lx, gy = s.y0 + ly, gz = s.z0 + lz;
+        if (gx >= s.ox0 && gx < s.ox0 + s.owx && gy >= s.oy0 && gy < s.oy0 + s.owy && gz >= s.oz0 &&
+            gz < s.oz0 + s.owz)
+            return f * nn + grid_index(P, gx, gy, gz);
         return -1;
     };
     auto owned_out = [=](int j, int t, double z) {
@@ -428,7 +440,7 @@ __global__ void __launch_bounds__(NT) k_local_jvp(int nsub, const SubDev* __rest
             [=](int, int) { return 0.0; }, [=](int j, int t, T zz, double) { z[j * m + t] = (double)zz; }, err))
         return;
     for (int it = 0; it < nir; ++it) {
-        local_linear_residual(s, beta, coef, 1.0, b, z, r, red);
+        local_linear_residual(s, beta, sdiag, coef, 1.0, b, z, r, red);
         if (!stream_solve<T>(
                 S, G, m, s.mp, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)r[j * m + t]; },
                 [=](int j, int t) { return z[j * m + t]; },
@@ -456,19 +468,24 @@ __global__ void __launch_bounds__(NT) k_local_precond(int nsub, const SubDev* __
     const int i = order[pos];
     const SubDev s = subs[i];
     const ProbDev P = probs[s.prob];
-    const int n = P.n, m = 2 * s.wx, W = s.wy;
-    const long long nn = (long long)n * n;
+    const int m = 2 * s.bl, W = s.bw;
+    const long long nn = P.nn;
     const double* Ry = R + P.ofs;
     double* Zy = Z + P.ofs;
     auto rhs = [=](int j, int t) -> T {
-        const int lx = t >> 1, f = t & 1;
-        return (T)Ry[f * nn + (long long)(s.y0 + j) * n + s.x0 + lx];
+        const int f = t & 1;
+        int lx, ly, lz;
+        local_coords(s, j * s.bl + (t >> 1), lx, ly, lz);
+        return (T)Ry[f * nn + grid_index(P, s.x0 + lx, s.y0 + ly, s.z0 + lz)];
     };
     auto out = [=](int j, int t, T z, double) {
-        const int lx = t >> 1, f = t & 1;
-        const int gx = s.x0 + lx, gy = s.y0 + j;
-        if (gx >= s.ox0 && gx < s.ox0 + s.owx && gy >= s.oy0 && gy < s.oy0 + s.owy)
-            Zy[f * nn + (long long)gy * n + gx] = (double)z;
+        const int f = t & 1;
+        int lx, ly, lz;
+        local_coords(s, j * s.bl + (t >> 1), lx, ly, lz);
+        const int gx = s.x0 + lx, gy = s.y0 + ly, gz = s.z0 + lz;
+        if (gx >= s.ox0 && gx < s.ox0 + s.owx && gy >= s.oy0 && gy < s.oy0 + s.owy && gz >= s.oz0 &&
+            gz < s.oz0 + s.owz)
+            Zy[f * nn + grid_index(P, gx, gy, gz)] = (double)z;
     };
     if (!stream_solve<T>(S, static_cast<const T*>(s.gptr), m, s.mp, W, (T)P.beta, wpool + s.voff, vec, tmp, rhs,
                          [=](int, int) { return 0.0; }, out, err))

@@ -94,9 +94,12 @@ extern "C" int ras_residual_static(int n, int phi, double nu, double mu, double 
     if (partials_address(&partials) != cudaSuccess) return RAS_ECUDA;
     ras::ProbDev P{};
     P.n = n;
+    P.nz = 1;
+    P.nn = (long long)n * n;
     P.phi = phi;
     P.h = 1.0 / (n + 1);
     P.beta = 1.0 / (P.h * P.h);
+    P.diag = 4.0 * P.beta;
     P.nu = nu;
     P.mu = mu;
     P.kappa = kappa;

@@ -112,6 +112,55 @@ def make_yd(cfg):
     raise KeyError(kind)
 
 
+def yd_sine3(n):
+    """The cube: y_d(x1, x2, x3) = sin(2 pi x1) sin(2 pi x2) sin(2 pi x3), an
+    (n, n, n) array indexed [k, j, i] (x1 fastest)."""
+    s = np.sin(2 * np.pi * coords(n))
+    return s[:, None, None] * s[None, :, None] * s[None, None, :]
+
+
+def yd_fourier3(n, seed, modes=8, fmax=4):
+    """The cube: sum of `modes` products sin(2 pi a x1) sin(2 pi b x2)
+    sin(2 pi c x3), amplitude ~ U(-1, 1), frequencies ~ U{1..fmax}, drawn in the
+    order (amplitude, a, b, c) per mode from SplitMix64(seed)."""
+    rng = SplitMix64(seed)
+    x = coords(n)
+    y = np.zeros((n, n, n))
+    for _ in range(modes):
+        amp = 2.0 * rng.uniform() - 1.0
+        a, b, c = rng.randint(1, fmax), rng.randint(1, fmax), rng.randint(1, fmax)
+        sa, sb, sc = np.sin(2 * np.pi * a * x), np.sin(2 * np.pi * b * x), np.sin(2 * np.pi * c * x)
+        y += amp * sc[:, None, None] * sb[None, :, None] * sa[None, None, :]
+    return y
+
+
+def problem3(name, **over):
+    """Named workloads on the unit cube (7-point stencil): n, layout
+    (sx, sy, sz), overlap, phi, nu, mu, y_d and the eps schedule. Every box
+    plane has at most 80 nodes."""
+    base = dict(eps0=0.1, gamma=0.1, eps_min=1e-6, tol=1e-10, inner_tol=1e-8, sigma=1.1, kappa=0.1)
+    if name == "c15":            # 15^3 grid, 3x3x3 boxes, overlap 1
+        cfg = dict(n=15, sx=3, sy=3, sz=3, overlap=1, phi=PHI_CUBIC, nu=1e-4, mu=1e-3, yd=("sine3",))
+    elif name == "c23":          # 23^3 grid, 4x4x4 boxes, overlap 1, Fourier data
+        cfg = dict(n=23, sx=4, sy=4, sz=4, overlap=1, phi=PHI_CUBIC, nu=1e-5, mu=1e-3, yd=("fourier3", 3))
+    elif name == "c63":          # 63^3 grid, 11x11x8 boxes of about 6 x 6 x 8 nodes, overlap 1
+        cfg = dict(n=63, sx=11, sy=11, sz=8, overlap=1, phi=PHI_CUBIC, nu=1e-5, mu=1e-3, yd=("fourier3", 3))
+    else:
+        raise KeyError(name)
+    base.update(cfg)
+    base.update(over)
+    return base
+
+
+def make_yd3(cfg):
+    kind = cfg["yd"]
+    if kind[0] == "sine3":
+        return yd_sine3(cfg["n"])
+    if kind[0] == "fourier3":
+        return yd_fourier3(cfg["n"], kind[1])
+    raise KeyError(kind)
+
+
 def uneven_batch(seed=4, count=64):
     """64 independent problems of uneven size: n ~ U{63,127,255,511},
     mu ~ logU[1e-4,1e-2], nu ~ logU[1e-6,1e-3], phi ~ U{y^3, exp}, block size

@@ -118,6 +118,9 @@ _I = ctypes.c_int
 _SIGS = {
     "ras_default_opts": (_I, [ctypes.POINTER(ras_opts)]),
     "ras_create": (_I, [_I, _I, _I, _I, _I, _D, _D, _P, _P, ctypes.POINTER(ras_opts), _P, ctypes.POINTER(_P)]),
+    "ras_create3": (_I, [_I, _I, _I, _I, _I, _I, _D, _D, _P, _P, ctypes.POINTER(ras_opts), _P,
+                         ctypes.POINTER(_P)]),
+    "ras_problem_dim": (_I, [_P]),
     "ras_batch_create": (_I, [_I, ctypes.POINTER(ras_problem_desc), ctypes.POINTER(ras_opts), _P,
                               ctypes.POINTER(_P)]),
     "ras_problem_count": (_I, [_P]),
@@ -209,11 +212,14 @@ def _ptr(t, n=None, device=True):
 
 
 class Handle:
-    """Opaque ras_problem* plus the grid size, for argument checks."""
+    """Opaque ras_problem* plus the grid size, for argument checks (nn: grid
+    nodes, n^2 on the square, n^3 on the cube)."""
 
-    def __init__(self, ptr, n):
+    def __init__(self, ptr, n, dim=2):
         self.ptr = ptr
         self.n = n
+        self.dim = dim
+        self.nn = None if n is None else n ** dim
 
     def _check(self, rc, ok=(RAS_OK, RAS_OK_FLOOR)):
         if rc not in ok:
@@ -238,6 +244,26 @@ def ras_create(n, sx, sy, overlap, phi, nu, mu, y_d, f=None, opts=None, stream=N
     if rc != RAS_OK:
         raise RasError(rc, "ras_create failed")
     return Handle(out, n)
+
+
+def ras_create3(n, sx, sy, sz, overlap, phi, nu, mu, y_d, f=None, opts=None, stream=None):
+    """A problem on the n x n x n cube (7-point stencil), sx x sy x sz boxes;
+    y_d, f: CUDA float64 tensors of n^3 entries (x1 fastest)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    out = ctypes.c_void_p()
+    nn = n ** 3
+    rc = lib().ras_create3(n, sx, sy, sz, overlap, phi, nu, mu, _ptr(y_d, nn), _ptr(f, nn),
+                           ctypes.byref(opts) if opts is not None else None, ctypes.c_void_p(stream),
+                           ctypes.byref(out))
+    if rc != RAS_OK:
+        raise RasError(rc, "ras_create3 failed")
+    return Handle(out, n, 3)
+
+
+def ras_problem_dim(h):
+    return lib().ras_problem_dim(h.ptr)
 
 
 class BatchHandle(Handle):
@@ -294,12 +320,12 @@ def ras_set_opts(h, opts):
 
 
 def ras_set_data(h, y_d, f=None):
-    nn = h.n * h.n
+    nn = h.nn
     return h._check(lib().ras_set_data(h.ptr, _ptr(y_d, nn), _ptr(f, nn)))
 
 
 def ras_residual(h, y, p, eps, Fy=None, Fp=None):
-    nn = h.n * h.n
+    nn = h.nn
     nrm = ctypes.c_double()
     h._check(lib().ras_residual(h.ptr, _ptr(y, nn), _ptr(p, nn), eps, _ptr(Fy, nn), _ptr(Fp, nn),
                                 ctypes.byref(nrm)))
@@ -307,7 +333,7 @@ def ras_residual(h, y, p, eps, Fy=None, Fp=None):
 
 
 def ras_apply(h, y, p, continuation, Fy, Fp, check=True):
-    nn = h.n * h.n
+    nn = h.nn
     st = ras_stats()
     rc = lib().ras_apply(h.ptr, _ptr(y, nn), _ptr(p, nn), int(continuation), _ptr(Fy, nn), _ptr(Fp, nn),
                          ctypes.byref(st))
@@ -317,18 +343,18 @@ def ras_apply(h, y, p, continuation, Fy, Fp, check=True):
 
 
 def ras_jvp(h, dy, dp, oy, op):
-    nn = h.n * h.n
+    nn = h.nn
     return h._check(lib().ras_jvp(h.ptr, _ptr(dy, nn), _ptr(dp, nn), _ptr(oy, nn), _ptr(op, nn)))
 
 
 def ras_precondition(h, y, p, eps, ry, rp, zy, zp):
-    nn = h.n * h.n
+    nn = h.nn
     return h._check(lib().ras_precondition(h.ptr, _ptr(y, nn), _ptr(p, nn), eps, _ptr(ry, nn), _ptr(rp, nn),
                                            _ptr(zy, nn), _ptr(zp, nn)))
 
 
 def ras_raspen_solve(h, y, p, check=True):
-    nn = h.n * h.n
+    nn = h.nn
     st = ras_stats()
     rc = lib().ras_raspen_solve(h.ptr, _ptr(y, nn), _ptr(p, nn), ctypes.byref(st))
     if check:
@@ -337,7 +363,7 @@ def ras_raspen_solve(h, y, p, check=True):
 
 
 def ras_newton_ras_solve(h, y, p, check=True):
-    nn = h.n * h.n
+    nn = h.nn
     st = ras_stats()
     rc = lib().ras_newton_ras_solve(h.ptr, _ptr(y, nn), _ptr(p, nn), ctypes.byref(st))
     if check:
@@ -346,7 +372,7 @@ def ras_newton_ras_solve(h, y, p, check=True):
 
 
 def ras_newton_solve(h, y, p, check=True):
-    nn = h.n * h.n
+    nn = h.nn
     st = ras_stats()
     rc = lib().ras_newton_solve(h.ptr, _ptr(y, nn), _ptr(p, nn), ctypes.byref(st))
     if check:
@@ -367,7 +393,7 @@ def ras_set_state(h, st):
 def ras_manufacture(h, pbar, eps=1e-15, y_out=None, yd_out=None):
     """Sec. 4's manufactured solution for the adjoint pbar: sets the handle's
     y_d and writes ybar / y_d into y_out / yd_out (device tensors, optional)."""
-    nn = h.n * h.n
+    nn = h.nn
     return h._check(lib().ras_manufacture(h.ptr, _ptr(pbar, nn), float(eps), _ptr(y_out, nn), _ptr(yd_out, nn)))
 
 
@@ -407,7 +433,7 @@ def make_tuning(factor_wide_max=(-1,) * RAS_NTILE, solve_ctas_per_sm=0, vec_bloc
 
 
 def ras_solve_host(h, method, y_d_host, y_host, p_host, check=True):
-    nn = h.n * h.n
+    nn = h.nn
     st = ras_stats()
     rc = lib().ras_solve_host(h.ptr, int(method), _ptr(y_d_host, nn, device=False),
                               _ptr(y_host, nn, device=False), _ptr(p_host, nn, device=False),
