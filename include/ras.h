@@ -139,7 +139,13 @@ int ras_default_opts(ras_opts* o);
  *   o        options (copied); NULL means ras_default_opts.
  *   stream   cudaStream_t to use, NULL for the legacy default stream.
  * Limits: n >= 2, 1 <= sx, sy <= n, overlap >= 0, and every local block row
- * has 2*wx <= 160 unknowns (wx = subdomain width in nodes) -> RAS_EINVAL.
+ * has 2*wx <= 512 unknowns (wx = subdomain width in nodes, overlap included)
+ * -> RAS_EINVAL. Rows of up to 160 unknowns take the register-tile
+ * factorisation and the streamed solves; wider ones (the paper's 2 x s and
+ * small s x s layouts) a factorisation of the block in its HBM slot by one
+ * 1024-thread CTA and solves with plain loads, one CTA per subdomain. Partial
+ * pivoting is checked per block (on S_j for narrow rows, on S_j^T for wide
+ * ones) and a block that needs row interchanges is redone with them.
  * On success *out receives the handle. */
 int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu,
                const double* y_d, const double* f, const ras_opts* o,
@@ -153,8 +159,9 @@ int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu
  * Grid functions are n^3 FP64 with x1 fastest, then x2, then x3 (node
  * (i, j, k) at (k*n + j)*n + i); y_d and f as in ras_create with n^3 entries.
  * The local Jacobian of a box is block tridiagonal over its x3 planes, so
- * every box plane must have 2*wx*wy <= 160 unknowns (wx, wy = box extents
- * along x1 and x2, overlap included) -> RAS_EINVAL otherwise; 1 <= sz <= n.
+ * every box plane must have 2*wx*wy <= 512 unknowns (wx, wy = box extents
+ * along x1 and x2, overlap included; up to 160 on the register-tile path)
+ * -> RAS_EINVAL otherwise; 1 <= sz <= n.
  * Every call that takes a handle works on the result (vectors of 2*n^3, or
  * n^3 per field) except ras_residual_static, the batch and the server, which
  * describe square problems only. */
@@ -172,7 +179,8 @@ int ras_problem_dim(const ras_problem* h);
  * copied. All problems share the options. The subdomains of all problems form
  * one table: every step of a RASPEN-function evaluation (Alg. 3) is one launch
  * for the whole batch, and the FP32 factorisation is launched once per
- * register-tile class (block size mp = 2*wx rounded up to 32, tile mp/16).
+ * register-tile class (block size mp = 2*wx rounded up to 32, tile mp/16),
+ * with one more launch for the wide-block subdomains of all problems.
  * Limits as in ras_create, per problem; 1 <= count <= 4096. */
 typedef struct {
     int n, sx, sy, overlap, phi;

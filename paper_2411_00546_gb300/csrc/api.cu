@@ -49,7 +49,7 @@ struct ras_problem {
     std::vector<int> sz;      // per problem: subdomains along x3 on the cube, 0 on the square
     ras_opts o{};
     cudaStream_t st = nullptr;
-    int nsub = 0, maxm = 0;
+    int nsub = 0, maxm = 0;   // maxm: largest 2*bl of the narrow (register / streaming path) subdomains
     long long L = 0;          // length of a global vector (sum of 2 nn_k)
     long long Lsum = 0;       // sum of 2*wx*wy*wz
     long long Nsum = 0;       // sum of wx*wy*wz
@@ -91,6 +91,8 @@ struct ras_problem {
     bool have_resume = false;
     int* d_order = nullptr;      // subdomain indices, largest factors first (solve kernels)
     int* d_ticket = nullptr;     // work counter of the persistent solve kernels
+    std::vector<int> h_wide;     // wide-block subdomains (MAX_M < 2 bl <= MAX_MW)
+    int* d_wide = nullptr;
     // block tables of the segmented kernels, one per mask row (0: GMRES/JVP,
     // 1: outer loop, 2: every problem), VEC_BLOCKS + nprob entries each
     int2* d_tab = nullptr;       // row 3: the GMRES cycle's table, built on the device from d_mask row 0
@@ -508,7 +510,15 @@ void stats_clear(ras_stats* s, int count) {
     std::memset(s, 0, sizeof(ras_stats) * count);
 }
 
-// Factorisation launches: FP32 one per register-tile class, FP64 one.
+// Factorisation of the wide-block subdomains (none: nothing launched).
+template <typename T>
+cudaError_t launch_factor_wide(ras_problem* h, int only_active) {
+    return ras::launch_local_factor_big<T>(h->st, (int)h->h_wide.size(), h->d_wide, h->d_subs, h->d_probs, h->X,
+                                           h->ls, h->cpool, h->coef, (T*)h->gpool, only_active);
+}
+
+// Factorisation launches: FP32 one per register-tile class, FP64 one, and
+// one for the wide-block subdomains.
 template <typename T>
 // nwork: most subdomains that factorise in this sweep (the active count, or
 // every subdomain); up to tune.factor_wide_max of a class (default: one per
@@ -532,11 +542,17 @@ int launch_factor(ras_problem* h, int only_active, double flops, int nwork) {
             }));
             first = false;
         }
+        if (!h->h_wide.empty())
+            CK(timed(h, RAS_K_FACTOR, first ? flops : 0.0, [&] { return launch_factor_wide<T>(h, only_active); }));
         return RAS_OK;
     }
     CK(timed(h, RAS_K_FACTOR, flops, [&] {
-        return ras::launch_local_factor<T>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs, h->X, h->ls, h->cpool,
-                                           h->coef, (T*)h->gpool, only_active);
+        cudaError_t e = cudaSuccess;
+        if (h->maxm > 0)
+            e = ras::launch_local_factor<T>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs, h->X, h->ls, h->cpool,
+                                            h->coef, (T*)h->gpool, only_active);
+        if (e == cudaSuccess) e = launch_factor_wide<T>(h, only_active);
+        return e;
     }));
     return RAS_OK;
 }
@@ -555,10 +571,13 @@ int launch_factor_sel(ras_problem* h) {
                                                 h->d_subs, h->d_probs, h->X, h->ls, h->cpool, h->coef,
                                                 (float*)h->gpool, 1, wide, ras::FactorSel{h->d_active, thr}));
         }
+        CK(launch_factor_wide<T>(h, 1));
         return RAS_OK;
     }
-    CK(ras::launch_local_factor<T>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs, h->X, h->ls, h->cpool, h->coef,
-                                   (T*)h->gpool, 1));
+    if (h->maxm > 0)
+        CK(ras::launch_local_factor<T>(h->st, h->nsub, h->maxm, h->d_subs, h->d_probs, h->X, h->ls, h->cpool,
+                                       h->coef, (T*)h->gpool, 1));
+    CK(launch_factor_wide<T>(h, 1));
     return RAS_OK;
 }
 
@@ -645,6 +664,9 @@ int build_sweep_graph(ras_problem* h, double* Fout, const NewtonParams& np) {
                 CK(ras::launch_local_direction<T>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs,
                                                   h->ls, np, h->coef, gp, h->Kpool, h->dpool, h->rpool, wp, h->d_err,
                                                   h->d_order, h->d_ticket));
+                CK(ras::launch_local_direction_wide<T>(h->st, (int)h->h_wide.size(), h->d_wide, h->d_subs,
+                                                       h->d_probs, h->ls, np, h->coef, gp, h->Kpool, h->dpool,
+                                                       h->rpool, wp, h->d_err));
                 CK(cudaMemsetAsync(h->d_active, 0, sizeof(int), h->st));
                 CK(ras::launch_local_linesearch(h->st, h->nsub, h->d_subs, h->d_probs, h->X, h->ls, np, h->cpool,
                                                 h->dpool, h->Kpool, h->Ktpool, h->d_active));
@@ -738,9 +760,14 @@ int ras_apply_T(ras_problem* h, const std::vector<double>& pstart, double* Fout,
         }
         TRY(launch_factor<T>(h, 1, fl, *h->h_active));
         CK(timed(h, RAS_K_DIRECTION, 0.0, [&] {
-            return ras::launch_local_direction<T>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs, h->ls, np,
-                                                  h->coef, gp, h->Kpool, h->dpool, h->rpool, wp, h->d_err,
-                                                  h->d_order, h->d_ticket);
+            cudaError_t e = ras::launch_local_direction<T>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs,
+                                                           h->d_probs, h->ls, np, h->coef, gp, h->Kpool, h->dpool,
+                                                           h->rpool, wp, h->d_err, h->d_order, h->d_ticket);
+            if (e == cudaSuccess)
+                e = ras::launch_local_direction_wide<T>(h->st, (int)h->h_wide.size(), h->d_wide, h->d_subs,
+                                                        h->d_probs, h->ls, np, h->coef, gp, h->Kpool, h->dpool,
+                                                        h->rpool, wp, h->d_err);
+            return e;
         }));
         const size_t dir_rec = h->prof_recs.size();
         CK(cudaMemsetAsync(h->d_active, 0, sizeof(int), h->st));
@@ -832,13 +859,26 @@ int jvp_internal(ras_problem* h, const double* D, double* O, const std::vector<i
     const int nir = (h->o.precision == RAS_MIXED) ? h->o.jvp_ir : 0;
     const int* dm = mask ? h->d_mask : nullptr;
     CK(timed(h, RAS_K_JVP, solve_bytes(h, mask) * (1 + nir), [&] {
-        if (h->o.precision == RAS_MIXED)
-            return ras::launch_local_jvp<float>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs,
-                                                (const float*)h->gpool, (float*)h->wpool, h->coef, h->dpool,
-                                                h->rpool, h->Ktpool, nir, D, O, dm, h->d_err, h->d_order, h->d_ticket);
-        return ras::launch_local_jvp<double>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs,
-                                             (const double*)h->gpool, (double*)h->wpool, h->coef, h->dpool,
-                                             h->rpool, h->Ktpool, 0, D, O, dm, h->d_err, h->d_order, h->d_ticket);
+        const int nw = (int)h->h_wide.size();
+        cudaError_t e;
+        if (h->o.precision == RAS_MIXED) {
+            e = ras::launch_local_jvp<float>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs,
+                                             (const float*)h->gpool, (float*)h->wpool, h->coef, h->dpool, h->rpool,
+                                             h->Ktpool, nir, D, O, dm, h->d_err, h->d_order, h->d_ticket);
+            if (e == cudaSuccess)
+                e = ras::launch_local_jvp_wide<float>(h->st, nw, h->d_wide, h->d_subs, h->d_probs,
+                                                      (const float*)h->gpool, (float*)h->wpool, h->coef, h->dpool,
+                                                      h->rpool, h->Ktpool, nir, D, O, dm, h->d_err);
+            return e;
+        }
+        e = ras::launch_local_jvp<double>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs,
+                                          (const double*)h->gpool, (double*)h->wpool, h->coef, h->dpool, h->rpool,
+                                          h->Ktpool, 0, D, O, dm, h->d_err, h->d_order, h->d_ticket);
+        if (e == cudaSuccess)
+            e = ras::launch_local_jvp_wide<double>(h->st, nw, h->d_wide, h->d_subs, h->d_probs,
+                                                   (const double*)h->gpool, (double*)h->wpool, h->coef, h->dpool,
+                                                   h->rpool, h->Ktpool, 0, D, O, dm, h->d_err);
+        return e;
     }));
     return RAS_OK;
 }
@@ -869,13 +909,24 @@ int factor_at(ras_problem* h, double eps) {
 
 int precond_internal(ras_problem* h, const double* R, double* Zo) {
     CK(timed(h, RAS_K_PRECOND, solve_bytes(h, nullptr), [&] {
-        if (h->o.precision == RAS_MIXED)
-            return ras::launch_local_precond<float>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs,
-                                                    (const float*)h->gpool, (float*)h->wpool, R, Zo, h->d_err,
-                                                    h->d_order, h->d_ticket);
-        return ras::launch_local_precond<double>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs,
-                                                 (const double*)h->gpool, (double*)h->wpool, R, Zo, h->d_err,
+        const int nw = (int)h->h_wide.size();
+        cudaError_t e;
+        if (h->o.precision == RAS_MIXED) {
+            e = ras::launch_local_precond<float>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs,
+                                                 (const float*)h->gpool, (float*)h->wpool, R, Zo, h->d_err,
                                                  h->d_order, h->d_ticket);
+            if (e == cudaSuccess)
+                e = ras::launch_local_precond_wide<float>(h->st, nw, h->d_wide, h->d_subs, h->d_probs,
+                                                          (const float*)h->gpool, (float*)h->wpool, R, Zo, h->d_err);
+            return e;
+        }
+        e = ras::launch_local_precond<double>(h->st, h->nsub, h->tune.solve_ctas_per_sm, h->d_subs, h->d_probs,
+                                              (const double*)h->gpool, (double*)h->wpool, R, Zo, h->d_err,
+                                              h->d_order, h->d_ticket);
+        if (e == cudaSuccess)
+            e = ras::launch_local_precond_wide<double>(h->st, nw, h->d_wide, h->d_subs, h->d_probs,
+                                                       (const double*)h->gpool, (double*)h->wpool, R, Zo, h->d_err);
+        return e;
     }));
     return RAS_OK;
 }
@@ -1743,6 +1794,8 @@ int build_layout(ras_problem* h, int count, const ras_problem_desc* pd, const in
     h->sub_first.clear();
     h->sub_count.clear();
     h->maxm = 0;
+    h->h_wide.clear();
+    int maxm_all = 0;
     long long voff = 0, noff = 0, goff = 0, vec = 0;
     for (int p = 0; p < count; ++p) {
         const ras_problem_desc& d = pd[p];
@@ -1793,7 +1846,9 @@ int build_layout(ras_problem* h, int count, const ras_problem_desc* pd, const in
                     voff += 2LL * s.wx * s.wy * s.wz;
                     noff += (long long)s.wx * s.wy * s.wz;
                     goff += (long long)s.bw * s.mp * s.mp;
-                    h->maxm = std::max(h->maxm, 2 * s.bl);
+                    maxm_all = std::max(maxm_all, 2 * s.bl);
+                    if (s.mp > ras::MAX_M) h->h_wide.push_back((int)h->subs.size());
+                    else h->maxm = std::max(h->maxm, 2 * s.bl);
                     h->subs.push_back(s);
                 }
             }
@@ -1801,9 +1856,9 @@ int build_layout(ras_problem* h, int count, const ras_problem_desc* pd, const in
         h->sub_count.push_back((int)h->subs.size() - h->sub_first.back());
         vec += 2 * P.nn;
     }
-    if (h->maxm > ras::MAX_M)
+    if (maxm_all > ras::MAX_MW)
         return fail(h, RAS_EINVAL,
-                    "a local block row has more than 160 unknowns (2 wx > 160; on the cube 2 wx wy > 160)");
+                    "a local block row has more than 512 unknowns (2 wx > 512; on the cube 2 wx wy > 512)");
     h->nsub = (int)h->subs.size();
     h->Lsum = voff; h->Nsum = noff; h->Gsum = goff; h->L = vec;
     // register-tile classes of the FP32 factorisation: tile = mp / 16
@@ -1844,6 +1899,7 @@ int ensure_pools(ras_problem* h, bool own_data) {
     TRY(ensure(h, &h->d_segs, count));
     TRY(ensure(h, &h->d_lists, std::max<size_t>(1, h->h_lists.size())));
     TRY(ensure(h, &h->d_order, h->nsub));
+    TRY(ensure(h, &h->d_wide, std::max<size_t>(1, h->h_wide.size())));
     TRY(ensure(h, &h->d_ticket, 1));
     for (double** q : {&h->cpool, &h->dpool, &h->Kpool, &h->Ktpool, &h->rpool}) TRY(ensure(h, q, h->Lsum));
     if (h->own_factors) TRY(ensure(h, &h->coef, 3 * h->Nsum));
@@ -1906,6 +1962,9 @@ int upload_layout(ras_problem* h) {
                (long long)h->subs[b].bw * h->subs[b].mp * h->subs[b].mp;
     });
     CK(cudaMemcpyAsync(h->d_order, order.data(), h->nsub * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    if (!h->h_wide.empty())
+        CK(cudaMemcpyAsync(h->d_wide, h->h_wide.data(), h->h_wide.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           h->st));
     TRY(sync(h));
     CK(cudaMemcpyAsync(h->d_subs, h->subs.data(), h->nsub * sizeof(SubDev), cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->d_probs, h->probs.data(), h->nprob * sizeof(ProbDev), cudaMemcpyHostToDevice, h->st));
@@ -2660,7 +2719,7 @@ int ras_server_submit(ras_server* s, const ras_problem_desc* d, long long* id) {
     r->d = *d;
     if (request_bytes(r->d, s->o, r->slot, r->scratch) != RAS_OK) {
         delete r;
-        return sfail(s, RAS_EINVAL, "a subdomain is wider than 80 nodes (2 wx > 160)");
+        return sfail(s, RAS_EINVAL, "a subdomain is wider than 256 nodes (2 wx > 512)");
     }
     if (r->slot + 2 * r->scratch > s->budget) {
         delete r;

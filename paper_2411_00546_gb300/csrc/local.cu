@@ -254,6 +254,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_local_factor(int nsub, int max
     if (only_active && !ls[i].active) return;
     if (ls[i].status == ST_SKIP) return;
     const SubDev s = subs[i];
+    if (s.mp > MAX_M) return;   // wide block: k_local_factor_big
     const ProbDev P = probs[s.prob];
     const int m = 2 * s.bl, W = s.bw, nn = s.wx * s.wy * s.wz, LD = maxm + 1;
     const bool cube = P.nz > 1;
@@ -648,6 +649,7 @@ __global__ void __launch_bounds__(FACT_THREADS, 2) k_local_factor_panel(int nsub
     if (only_active && !ls[i].active) return;
     if (ls[i].status == ST_SKIP) return;
     const SubDev s = subs[i];
+    if (s.mp > 16 * R) return;   // not this register-tile class (wide blocks: k_local_factor_big)
     const ProbDev P = probs[s.prob];
     const int m = 2 * s.bl, W = s.bw, nn = s.wx * s.wy * s.wz, mp = s.mp;
     const bool cube = P.nz > 1;
@@ -943,6 +945,7 @@ __global__ void __launch_bounds__(1024, 1) k_local_factor_wide(int nsub, const S
     if (only_active && !ls[i].active) return;
     if (ls[i].status == ST_SKIP) return;
     const SubDev s = subs[i];
+    if (s.mp > 32 * R) return;   // not this register-tile class (wide blocks: k_local_factor_big)
     const ProbDev P = probs[s.prob];
     const int m = 2 * s.bl, W = s.bw, nn = s.wx * s.wy * s.wz, mp = s.mp;
     const bool cube = P.nz > 1;
@@ -1158,6 +1161,283 @@ __global__ void __launch_bounds__(1024, 1) k_local_factor_wide(int nsub, const S
     }
 }
 
+// ------------------------------------------------------------- wide blocks
+// Factorisation of a wide-block subdomain (MAX_M < m = 2 bl <= MAX_MW), one
+// 1024-thread CTA per subdomain. Block row j is formed and inverted in place
+// in its own factor slot (row-major, mp x mp): S_j = D_j - beta^2 G_{j-1},
+// inverted by the Gauss-Jordan sweep of k_local_factor_panel taken BIG_PANEL
+// pivots at a time. The column panel and the row panel (with zeros at the
+// panel's own columns) are staged in shared memory; the column panel is swept
+// with one thread per row, the pivot row passed on in a double-buffered copy
+// (one barrier per pivot); then one rank-BIG_PANEL update of the block in
+// HBM/L2 leaves the column panel at C', rows K at C'[K,K] M[K,J] and every
+// other row at M[I,J] + C'[I,K] M[K,J]. The partial-pivoting check is the
+// panel kernel's (a pivot smaller than an entry below it in its column, or
+// not finite); a block row that fails it is redone by unblocked Gauss-Jordan
+// with row interchanges (max |.| in the column, ties to the lowest row), the
+// interchanges undone on the columns at the end, last first. When all block
+// rows are done every slot is transposed in place: the wide solves read G_j
+// column-major.
+template <typename T>
+__global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, const int* __restrict__ list,
+                                                                  const SubDev* __restrict__ subs,
+                                                                  const ProbDev* __restrict__ probs,
+                                                                  const double* X, LocalState* ls,
+                                                                  const double* cpool, double* coef, T* gpool,
+                                                                  int only_active) {
+    constexpr int NTH = BIG_THREADS, NWB = NTH / 32, RB = BIG_PANEL, CS = RB + 1;
+    static_assert(MAX_MW <= NTH, "one panel row per thread in the sweep");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Cs = reinterpret_cast<T*>(smem_raw);   // column panel: row r at Cs + r * CS (odd stride)
+    T* Rs = Cs + MAX_MW * CS;                 // row panel: pivot kk at Rs + kk * MAX_MW
+    T* colk = Rs + RB * MAX_MW;               // pivot column of the pivoted fallback
+    T* prow = colk + MAX_MW;                  // pivot row of the sweep, two copies
+    __shared__ int piv[MAX_MW];
+    __shared__ T red_v[NWB];
+    __shared__ int red_i[NWB];
+    __shared__ int sh_fail, sh_r;
+    if ((int)blockIdx.x >= count) return;
+    const int i = list[blockIdx.x];
+    if (only_active && !ls[i].active) return;
+    if (ls[i].status == ST_SKIP) return;
+    const SubDev s = subs[i];
+    const ProbDev P = probs[s.prob];
+    const int m = 2 * s.bl, W = s.bw, nn = s.wx * s.wy * s.wz, mp = s.mp;
+    const bool cube = P.nz > 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    const double eps = ls[i].eps;
+    const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu;
+    double* ca = s.cptr;
+    double* cb = ca + nn;
+    double* cc = cb + nn;
+    {
+        const double* c = cpool + s.voff;
+        const LocalView V = make_view(s, P, X, c, nullptr, 0.0);
+        for (int q = tid; q < nn; q += NTH) {
+            const double y = V.at(q, 0), p = V.at(q, 1);
+            double ph, d1, d2;
+            phi_eval(P.phi, P.kappa, y, ph, d1, d2);
+            ca[q] = d1;
+            cb[q] = inu * one_minus_dP_eps(-p / mu, eps);
+            cc[q] = d2 * p - 1.0;
+        }
+    }
+    if (tid == 0) sh_fail = 0;
+    __syncthreads();
+
+    const T tbeta = (T)beta, tbeta2 = (T)(beta * beta), tdiag = (T)P.diag;
+    T* G = static_cast<T*>(s.gptr);
+    const long long blk = (long long)mp * mp;
+    auto dval = [&](int j, int r, int c) -> T {   // entry (r, c) of D_j
+        const int ix = r >> 1, f = r & 1, cx = c >> 1, cf = c & 1;
+        const int q = j * s.bl + ix;
+        if (cx == ix) {
+            if (cf == f) return tdiag + (T)ca[q];
+            return (f == 0) ? (T)cb[q] : (T)cc[q];
+        }
+        return (cf == f && row_neighbour(ix, cx, s.wx, cube)) ? -tbeta : (T)0;
+    };
+    auto form = [&](int j, T* M) {                 // M = S_j (G_{j-1} still row-major)
+        const T* Gp = G + (long long)(j > 0 ? j - 1 : 0) * blk;
+        for (int e = tid; e < m * m; e += NTH) {
+            const int r = e / m, c = e - r * m;
+            const T g = (j > 0) ? -tbeta2 * Gp[(long long)r * mp + c] : (T)0;
+            M[(long long)r * mp + c] = g + dval(j, r, c);
+        }
+    };
+    const int mc = ((m + 31) / 32) * 32;           // update: columns padded to whole warps,
+    const int rows_par = NTH / mc;                  // rows_par threads per column
+    const int ucol = tid % mc, urow = tid / mc;
+
+    bool failed = false;
+    for (int j = 0; j < W && !failed; ++j) {
+        T* M = G + (long long)j * blk;
+        form(j, M);
+        bool viol = false;   // the pivoting check failed (the same on every thread)
+        __syncthreads();
+        for (int k0 = 0; k0 < m; k0 += RB) {
+            const int nk = min(RB, m - k0);
+            for (int e = tid; e < m * RB; e += NTH) {
+                const int r = e / RB, kk = e - r * RB;
+                Cs[r * CS + kk] = (kk < nk) ? M[(long long)r * mp + k0 + kk] : (T)0;
+            }
+            for (int e = tid; e < RB * m; e += NTH) {
+                const int kk = e / m, c = e - kk * m;
+                Rs[kk * MAX_MW + c] =
+                    (kk < nk && (c < k0 || c >= k0 + nk)) ? M[(long long)(k0 + kk) * mp + c] : (T)0;
+            }
+            __syncthreads();
+            if (tid < RB) prow[tid] = Cs[k0 * CS + tid];
+            __syncthreads();
+            {
+                // thread r < m sweeps row r of the column panel; the pivot
+                // row reaches everyone through prow (its next version written
+                // by the owner of the next pivot row while it updates)
+                bool bad = false;
+                T* row = Cs + tid * CS;
+                for (int kk = 0; kk < nk; ++kk) {
+                    const T* pr = prow + (kk & 1) * RB;
+                    const int r0 = k0 + kk;
+                    const T d = pr[kk], ad = fabs(d);
+                    const T inv = (T)1 / d;
+                    if (tid == r0) {
+                        bad |= !(ad > (T)0 && ad < (T)INFINITY);
+#pragma unroll
+                        for (int c = 0; c < RB; ++c) row[c] = (c == kk) ? inv : pr[c] * inv;
+                    } else if (tid < m) {
+                        T* nx = (tid == r0 + 1 && kk + 1 < nk) ? prow + ((kk + 1) & 1) * RB : nullptr;
+                        const T f = row[kk];
+                        bad |= (tid > r0) && (fabs(f) > ad);
+#pragma unroll
+                        for (int c = 0; c < RB; ++c) {
+                            const T t = (c == kk) ? inv : pr[c] * inv;
+                            const T v = fma(-f, t, (c == kk) ? (T)0 : row[c]);
+                            row[c] = v;
+                            if (nx) nx[c] = v;
+                        }
+                    }
+                    __syncthreads();
+                }
+                if (__syncthreads_or(bad)) {
+                    viol = true;
+                    break;
+                }
+            }
+            if (ucol < m && urow < rows_par) {
+                const int c = ucol;
+                if (c >= k0 && c < k0 + nk) {
+                    for (int r = urow; r < m; r += rows_par) M[(long long)r * mp + c] = Cs[r * CS + (c - k0)];
+                } else {
+                    T rv[RB];
+#pragma unroll
+                    for (int kk = 0; kk < RB; ++kk) rv[kk] = Rs[kk * MAX_MW + c];
+                    // UR rows at a time, their loads issued before any is used
+                    constexpr int UR = 8;
+                    for (int r0 = urow; r0 < m; r0 += UR * rows_par) {
+                        T acc[UR];
+#pragma unroll
+                        for (int u = 0; u < UR; ++u) {
+                            const int r = r0 + u * rows_par;
+                            acc[u] = (r < m && (r < k0 || r >= k0 + nk)) ? M[(long long)r * mp + c] : (T)0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < UR; ++u) {
+                            const int r = r0 + u * rows_par;
+                            if (r < m) {
+                                const T* cr = Cs + r * CS;
+#pragma unroll
+                                for (int kk = 0; kk < RB; ++kk) acc[u] = fma(cr[kk], rv[kk], acc[u]);
+                                M[(long long)r * mp + c] = acc[u];
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (!viol) continue;
+        // Gauss-Jordan with row interchanges, from S_j again
+        form(j, M);
+        __syncthreads();
+        for (int k = 0; k < m; ++k) {
+            T best = (T)-1;
+            int bi = 0x7fffffff;
+            for (int r = k + tid; r < m; r += NTH) {
+                const T v = fabs(M[(long long)r * mp + k]);
+                if (v > best) { best = v; bi = r; }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const T ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) {
+                red_v[warp] = best;
+                red_i[warp] = bi;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                best = (lane < NWB) ? red_v[lane] : (T)-1;
+                bi = (lane < NWB) ? red_i[lane] : 0x7fffffff;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const T ob = __shfl_xor_sync(0xffffffffu, best, off);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                }
+                if (lane == 0) {
+                    if (bi >= m || !(best > (T)0) || !(best < (T)INFINITY)) {
+                        sh_fail = 1;
+                    } else {
+                        sh_r = bi;
+                        piv[k] = bi;
+                    }
+                }
+            }
+            __syncthreads();
+            if (sh_fail) break;
+            const int pr = sh_r;
+            if (pr != k) {
+                for (int c = tid; c < m; c += NTH) {
+                    const T a = M[(long long)k * mp + c];
+                    M[(long long)k * mp + c] = M[(long long)pr * mp + c];
+                    M[(long long)pr * mp + c] = a;
+                }
+            }
+            __syncthreads();
+            for (int r = tid; r < m; r += NTH) colk[r] = M[(long long)r * mp + k];
+            __syncthreads();
+            const T inv = (T)1 / colk[k];
+            for (int c = tid; c < m; c += NTH)
+                M[(long long)k * mp + c] = ((c == k) ? (T)1 : M[(long long)k * mp + c]) * inv;
+            __syncthreads();
+            for (int e = tid; e < m * m; e += NTH) {
+                const int r = e / m, c = e - r * m;
+                if (r == k) continue;
+                const T old = (c == k) ? (T)0 : M[(long long)r * mp + c];
+                M[(long long)r * mp + c] = old - colk[r] * M[(long long)k * mp + c];
+            }
+            __syncthreads();
+        }
+        if (sh_fail) {
+            failed = true;
+            break;
+        }
+        for (int k = m - 1; k >= 0; --k) {
+            const int pr = piv[k];
+            if (pr != k) {
+                for (int r = tid; r < m; r += NTH) {
+                    const T a = M[(long long)r * mp + k];
+                    M[(long long)r * mp + k] = M[(long long)r * mp + pr];
+                    M[(long long)r * mp + pr] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (failed) {
+        if (tid == 0) {
+            ls[i].status = ST_ESINGULAR;
+            ls[i].active = 0;
+        }
+        return;
+    }
+    // every G_j to column-major, in place
+    for (int j = 0; j < W; ++j) {
+        T* M = G + (long long)j * blk;
+        for (int e = tid; e < m * m; e += NTH) {
+            const int r = e / m, c = e - r * m;
+            if (r < c) {
+                const T a = M[(long long)r * mp + c];
+                M[(long long)r * mp + c] = M[(long long)c * mp + r];
+                M[(long long)c * mp + r] = a;
+            }
+        }
+    }
+}
+
 template <typename T>
 size_t factor_smem(int maxm) {
     return (size_t)maxm * (maxm + 1) * sizeof(T) + (size_t)maxm * sizeof(T) + 3 * (size_t)maxm * sizeof(int);
@@ -1248,6 +1528,20 @@ cudaError_t launch_local_factor(cudaStream_t st, int nsub, int maxm, const SubDe
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_local_factor_big(cudaStream_t st, int count, const int* list, const SubDev* subs,
+                                    const ProbDev* probs, const double* X, LocalState* ls, const double* cpool,
+                                    double* coef, T* gpool, int only_active) {
+    if (count <= 0) return cudaSuccess;
+    const size_t sm = (size_t)(MAX_MW * (BIG_PANEL + 1) + BIG_PANEL * MAX_MW + MAX_MW + 2 * BIG_PANEL) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(k_local_factor_big<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_local_factor_big<T><<<count, BIG_THREADS, sm, st>>>(count, list, subs, probs, X, ls, cpool, coef, gpool,
+                                                          only_active);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_local_linesearch(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,
                                     const double* X, LocalState* ls, NewtonParams np, double* cpool,
                                     const double* dpool, double* Kpool, double* Ktpool,
@@ -1284,10 +1578,13 @@ cudaError_t launch_local_prolong(cudaStream_t st, int nsub, const SubDev* subs, 
     return cudaGetLastError();
 }
 
-#define RAS_INSTANTIATE(T)                                                                            \
-    template cudaError_t launch_local_factor<T>(cudaStream_t, int, int, const SubDev*, const ProbDev*,  \
-                                                const double*, LocalState*, const double*, double*, T*, \
-                                                int);
+#define RAS_INSTANTIATE(T)                                                                                 \
+    template cudaError_t launch_local_factor<T>(cudaStream_t, int, int, const SubDev*, const ProbDev*,       \
+                                                const double*, LocalState*, const double*, double*, T*,      \
+                                                int);                                                        \
+    template cudaError_t launch_local_factor_big<T>(cudaStream_t, int, const int*, const SubDev*,            \
+                                                    const ProbDev*, const double*, LocalState*, const double*, \
+                                                    double*, T*, int);
 RAS_INSTANTIATE(float)
 RAS_INSTANTIATE(double)
 #undef RAS_INSTANTIATE

@@ -20,14 +20,20 @@
 //                     packed_index(): the streaming solve reads it as mp/32
 //                     contiguous slabs, one per group of 32 rows, and thread t
 //                     of a 256-thread CTA finds its share of every slab as
-//                     contiguous 16-byte vectors.
+//                     contiguous 16-byte vectors. Wide blocks (MAX_M < 2*bl
+//                     <= MAX_MW) are stored transposed instead: element
+//                     (r, c) of G_j at c*mp + r (column-major), so that the
+//                     threads of a CTA, one row each, read a column together.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace ras {
 
-constexpr int MAX_M = 160;          // max unknowns of one local block row (2*bl)
+constexpr int MAX_M = 160;          // max unknowns of a block row on the register / streaming path (2*bl)
+constexpr int MAX_MW = 512;         // max unknowns of a block row on the wide-block path
+constexpr int BIG_THREADS = 1024;   // threads of the wide-block factorisation kernel
+constexpr int BIG_PANEL = 16;       // pivots per panel of the wide-block factorisation
 constexpr int FACT_THREADS = 256;   // threads of the factorisation kernel
 constexpr int LOC_THREADS = 256;    // threads of the per-subdomain kernels
 constexpr int VEC_THREADS = 256;    // threads of the grid-stride vector kernels
@@ -329,6 +335,14 @@ template <typename T>
 cudaError_t launch_local_factor(cudaStream_t st, int nsub, int maxm, const SubDev* subs,
                                 const ProbDev* probs, const double* X, LocalState* ls,
                                 const double* cpool, double* coef, T* gpool, int only_active);
+// Factorisation of the `count` wide-block subdomains in `list` (device
+// indices, MAX_M < 2*bl <= MAX_MW): one 1024-thread CTA each, the block in
+// its own factor slot in HBM (blocked Gauss-Jordan, panels of BIG_PANEL
+// pivots staged in shared memory), G_j stored column-major.
+template <typename T>
+cudaError_t launch_local_factor_big(cudaStream_t st, int count, const int* list, const SubDev* subs,
+                                    const ProbDev* probs, const double* X, LocalState* ls, const double* cpool,
+                                    double* coef, T* gpool, int only_active);
 // The local-solve kernels (direction, Jacobian action, linear RAS) are
 // persistent: the grid holds as many CTAs as fit at once, and each takes the
 // next of the nsub positions of `order` (subdomain indices, largest factors
@@ -355,5 +369,22 @@ template <typename T>
 cudaError_t launch_local_precond(cudaStream_t st, int nsub, int ctas_per_sm, const SubDev* subs,
                                  const ProbDev* probs, const T* gpool, T* wpool, const double* R,
                                  double* Z, int* err, const int* order, int* ticket);
+// The same three solves for the `count` wide-block subdomains of `list` (one
+// 256-thread CTA each, the transposed factor blocks read with plain loads).
+// The kernels above skip wide-block subdomains.
+template <typename T>
+cudaError_t launch_local_direction_wide(cudaStream_t st, int count, const int* list, const SubDev* subs,
+                                        const ProbDev* probs, LocalState* ls, NewtonParams np,
+                                        const double* coef, const T* gpool, const double* Kpool, double* dpool,
+                                        double* rpool, T* wpool, int* err);
+template <typename T>
+cudaError_t launch_local_jvp_wide(cudaStream_t st, int count, const int* list, const SubDev* subs,
+                                  const ProbDev* probs, const T* gpool, T* wpool, const double* coef,
+                                  double* zpool, double* rpool, double* bpool, int nir, const double* D, double* O,
+                                  const int* pmask, int* err);
+template <typename T>
+cudaError_t launch_local_precond_wide(cudaStream_t st, int count, const int* list, const SubDev* subs,
+                                      const ProbDev* probs, const T* gpool, T* wpool, const double* R, double* Z,
+                                      int* err);
 cudaError_t solve_ctas_per_sm_max(bool f32, int* per_sm);
 }  // namespace ras

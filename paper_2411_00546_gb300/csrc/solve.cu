@@ -257,6 +257,145 @@ __device__ __forceinline__ int next_position(int* ticket, int* slot) {
     return *slot;
 }
 
+// The same solve for a wide block (MAX_M < m <= MAX_MW = 2 NT) with the
+// factor blocks stored column-major (element (r, c) of G_j at c*mp + r).
+// Every product reads its block as chunks of whole columns (CB columns, at
+// most WSLOT bytes), copied by TMA bulk copies (cp.async.bulk) into a ring of
+// WNS shared-memory slots; thread 0 keeps WNS chunks in flight across block
+// boundaries (the products run through blocks 0 .. W-2, then W-1 .. 0), and
+// thread t adds the chunk's columns times vec into rows t and t + NT. Every
+// wait is bounded; on a timeout the copies in flight are waited for (bounded)
+// and the solve returns false with ST_ETIMEOUT in *err. err[1] != 0 makes the
+// first wait poll zero times (the timeout test of ras_opts.wait_test). rhs,
+// pre and out as in stream_solve.
+constexpr int WNS = 6;                       // ring slots of the wide solves
+constexpr uint32_t WSLOT = 32 * 1024;        // bytes per slot
+template <typename T>
+size_t wide_solve_smem() {
+    return (size_t)WNS * WSLOT + WNS * sizeof(uint64_t) + 16;
+}
+
+template <typename T>
+__device__ void wide_stream_init(Stream<T>& S, unsigned char* smem) {
+    S.ring = smem;
+    S.full = reinterpret_cast<uint64_t*>(smem + (size_t)WNS * WSLOT);
+    S.fail = reinterpret_cast<int*>(S.full + WNS);
+    S.phase = 0u;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < WNS; ++k) mbar_init(&S.full[k], 1);
+        *S.fail = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+}
+
+template <typename T, class Rhs, class Pre, class Out>
+__device__ bool wide_solve(Stream<T>& S, const T* __restrict__ G, int m, int mp, int W, T beta, T* w, T* vec,
+                           T* tmp, Rhs rhs, Pre pre, Out out, int* err) {
+    const int r0 = threadIdx.x, r1 = threadIdx.x + NT;
+    const bool h0 = r0 < m, h1 = r1 < m;
+    const long long blk = (long long)mp * mp;
+    const uint32_t colb = (uint32_t)mp * (uint32_t)sizeof(T);   // a multiple of 128 bytes
+    const int CB = (int)(WSLOT / colb);                          // >= 1: mp <= MAX_MW
+    const int nch = (m + CB - 1) / CB;
+    const uint32_t total = (uint32_t)((2 * W - 1) * nch);
+    const bool first_zero = err && err[1] != 0;
+    auto issue = [&](uint32_t x) {   // chunk x of the sequence into slot x % WNS (thread 0)
+        const int v = (int)(x / (uint32_t)nch), ch = (int)(x % (uint32_t)nch);
+        const int jb = (v < W - 1) ? v : 2 * W - 2 - v;
+        const int c0 = ch * CB, nc = min(CB, m - c0);
+        const uint32_t k = x % WNS;
+        fence_proxy_async();
+        tma_load_1d(S.ring + (size_t)k * WSLOT, G + (long long)jb * blk + (long long)c0 * mp, (uint32_t)nc * colb,
+                    &S.full[k]);
+    };
+    if (threadIdx.x == 0)
+        for (uint32_t x = 0; x < (uint32_t)WNS && x < total; ++x) issue(x);
+    uint32_t q = 0;   // next chunk to consume
+    auto matvec = [&]() -> bool {   // tmp = G_(next block) vec
+        T a0 = (T)0, a1 = (T)0;
+        for (int ch = 0; ch < nch; ++ch, ++q) {
+            const uint32_t k = q % WNS;
+            const bool ok = mbar_wait(&S.full[k], (S.phase >> k) & 1u, (q == 0 && first_zero) ? 0 : WAIT_LIMIT);
+            if (__syncthreads_or(!ok)) {
+                // drain the copies issued and not consumed (chunks q .. q + WNS - 1), then report
+                if (threadIdx.x == 0) {
+                    for (uint32_t x = q; x < total && x < q + WNS; ++x) {
+                        const uint32_t kx = x % WNS;
+                        mbar_wait(&S.full[kx], (S.phase >> kx) & 1u);
+                    }
+                    if (err) atomicExch(err, ST_ETIMEOUT);
+                }
+                __syncthreads();
+                return false;
+            }
+            S.phase ^= 1u << k;
+            const T* cols = reinterpret_cast<const T*>(S.ring + (size_t)k * WSLOT);
+            const int c0 = ch * CB, nc = min(CB, m - c0);
+            for (int cc = 0; cc < nc; ++cc) {
+                const T v = vec[c0 + cc];
+                const T* col = cols + cc * mp;
+                if (h0) a0 = fma(col[r0], v, a0);
+                if (h1) a1 = fma(col[r1], v, a1);
+            }
+            __syncthreads();   // slot k read by every thread
+            if (threadIdx.x == 0 && q + WNS < total) issue(q + WNS);
+        }
+        if (h0) tmp[r0] = a0;
+        if (h1) tmp[r1] = a1;
+        __syncthreads();
+        return true;
+    };
+    for (int j = 0; j < W; ++j) {
+        if (h0) {
+            T v = rhs(j, r0);
+            if (j > 0) v += beta * tmp[r0];
+            vec[r0] = v;
+            w[j * m + r0] = v;
+        }
+        if (h1) {
+            T v = rhs(j, r1);
+            if (j > 0) v += beta * tmp[r1];
+            vec[r1] = v;
+            w[j * m + r1] = v;
+        }
+        __syncthreads();
+        if (j < W - 1 && !matvec()) return false;
+    }
+    for (int j = W - 1; j >= 0; --j) {
+        if (h0) vec[r0] = w[j * m + r0] + ((j < W - 1) ? beta * tmp[r0] : (T)0);
+        if (h1) vec[r1] = w[j * m + r1] + ((j < W - 1) ? beta * tmp[r1] : (T)0);
+        __syncthreads();
+        if (!matvec()) return false;
+        if (h0) out(j, r0, tmp[r0], pre(j, r0));
+        if (h1) out(j, r1, tmp[r1], pre(j, r1));
+    }
+    __syncthreads();
+    return true;
+}
+
+// One local solve: the slab stream (narrow blocks) or the column-chunk stream (wide blocks).
+template <typename T, bool WIDE, class Rhs, class Pre, class Out>
+__device__ __forceinline__ bool local_solve(Stream<T>& S, const T* G, int m, int mp, int W, T beta, T* w, T* vec,
+                                            T* tmp, Rhs rhs, Pre pre, Out out, int* err) {
+    if constexpr (WIDE) {
+        return wide_solve<T>(S, G, m, mp, W, beta, w, vec, tmp, rhs, pre, out, err);
+    } else {
+        return stream_solve<T>(S, G, m, mp, W, beta, w, vec, tmp, rhs, pre, out, err);
+    }
+}
+
+// Subdomain position of a solve kernel: the persistent kernels take the next
+// ticket; the wide-block ones run one CTA per listed subdomain.
+template <bool WIDE>
+__device__ __forceinline__ int solve_position(int it, int* ticket, int* slot) {
+    if constexpr (WIDE) {
+        return it == 0 ? (int)blockIdx.x : 0x7fffffff;
+    } else {
+        return next_position(ticket, slot);
+    }
+}
+
 // r = bsign * B - J_i z in FP64 with the Jacobian coefficients stored by the
 // factor kernel (the stencil's coupling inside Omega_i only; diag = 4 beta on
 // the square, 6 beta on the cube); returns ||r||^2.
@@ -293,24 +432,27 @@ __device__ double local_linear_residual(const SubDev& s, double beta, double dia
 // followed by FP64 iterative refinement: r = -K - J d with the FP64 Jacobian
 // (matrix-free, from the coefficients the factor kernel stored), d += J^-1 r,
 // until ||r|| <= ir_rtol ||K|| or ir_max corrections.
-template <typename T>
+template <typename T, bool WIDE>
 __global__ void __launch_bounds__(NT) k_local_direction(int nsub, const SubDev* __restrict__ subs,
                                                         const ProbDev* __restrict__ probs, LocalState* ls,
                                                         NewtonParams np, const double* coef, const T* gpool,
                                                         const double* Kpool, double* dpool, double* rpool,
                                                         T* wpool, int* err, const int* order, int* ticket) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ T vec[MAX_M], tmp[MAX_M];
+    __shared__ __align__(16) T vec[WIDE ? MAX_MW : MAX_M];
+    __shared__ __align__(16) T tmp[WIDE ? MAX_MW : MAX_M];
     __shared__ double red[2 * NT];
     __shared__ int sh_next;
     Stream<T> S;
-    stream_init(S, smem);
-    for (;;) {
-    const int pos = next_position(ticket, &sh_next);
+    if constexpr (WIDE) wide_stream_init(S, smem);
+    else stream_init(S, smem);
+    for (int it = 0;; ++it) {
+    const int pos = solve_position<WIDE>(it, ticket, &sh_next);
     if (pos >= nsub) break;
     const int i = order[pos];
     if (!ls[i].active) continue;
     const SubDev s = subs[i];
+    if (!WIDE && s.mp > MAX_M) continue;
     const ProbDev P = probs[s.prob];
     const int m = 2 * s.bl, W = s.bw, L = m * W;
     const double beta = P.beta, sdiag = P.nz > 1 ? 6.0 : 4.0;
@@ -331,7 +473,7 @@ __global__ void __launch_bounds__(NT) k_local_direction(int nsub, const SubDev* 
     int nsolves = 0;
     for (int it = 0;; ++it) {
         ++nsolves;
-        if (!stream_solve<T>(
+        if (!local_solve<T, WIDE>(
                 S, G, m, s.mp, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)r[j * m + t]; },
                 [=](int j, int t) { return d[j * m + t]; },
                 [=](int j, int t, T z, double old) { d[j * m + t] = old + (double)z; }, err)) {
@@ -354,24 +496,27 @@ __global__ void __launch_bounds__(NT) k_local_direction(int nsub, const SubDev* 
 // i.e. b = -beta * (sum of D over the stencil neighbours outside Omega_i).
 // With nir > 0 (mixed precision) the local solve is refined nir times in FP64:
 // z += J^-1 (b - J z), J from the coefficients at x^(i).
-template <typename T>
+template <typename T, bool WIDE>
 __global__ void __launch_bounds__(NT) k_local_jvp(int nsub, const SubDev* __restrict__ subs,
                                                   const ProbDev* __restrict__ probs, const T* gpool, T* wpool,
                                                   const double* coef, double* zpool, double* rpool,
                                                   double* bpool, int nir, const double* D, double* O,
                                                   const int* pmask, int* err, const int* order, int* ticket) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ T vec[MAX_M], tmp[MAX_M];
+    __shared__ __align__(16) T vec[WIDE ? MAX_MW : MAX_M];
+    __shared__ __align__(16) T tmp[WIDE ? MAX_MW : MAX_M];
     __shared__ double red[2 * NT];
     __shared__ int sh_next;
     Stream<T> S;
-    stream_init(S, smem);
-    for (;;) {
-    const int pos = next_position(ticket, &sh_next);
+    if constexpr (WIDE) wide_stream_init(S, smem);
+    else stream_init(S, smem);
+    for (int it = 0;; ++it) {
+    const int pos = solve_position<WIDE>(it, ticket, &sh_next);
     if (pos >= nsub) break;
     const int i = order[pos];
     const SubDev s = subs[i];
     if (pmask && !pmask[s.prob]) continue;
+    if (!WIDE && s.mp > MAX_M) continue;
     const ProbDev P = probs[s.prob];
     const int n = P.n, nz = P.nz, m = 2 * s.bl, W = s.bw;
     const long long nn = P.nn;
@@ -412,7 +557,7 @@ __global__ void __launch_bounds__(NT) k_local_jvp(int nsub, const SubDev* __rest
         if (g >= 0) Oy[g] = -Dy[g] - z;
     };
     if (nir == 0) {
-        if (!stream_solve<T>(
+        if (!local_solve<T, WIDE>(
                 S, G, m, s.mp, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)bval(j, t); },
                 [=](int j, int t) {
                     const long long g = owned(j, t);
@@ -435,13 +580,13 @@ __global__ void __launch_bounds__(NT) k_local_jvp(int nsub, const SubDev* __rest
         z[q] = 0.0;
     }
     __syncthreads();
-    if (!stream_solve<T>(
+    if (!local_solve<T, WIDE>(
             S, G, m, s.mp, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)b[j * m + t]; },
             [=](int, int) { return 0.0; }, [=](int j, int t, T zz, double) { z[j * m + t] = (double)zz; }, err))
         return;
     for (int it = 0; it < nir; ++it) {
         local_linear_residual(s, beta, sdiag, coef, 1.0, b, z, r, red);
-        if (!stream_solve<T>(
+        if (!local_solve<T, WIDE>(
                 S, G, m, s.mp, W, (T)beta, w, vec, tmp, [=](int j, int t) { return (T)r[j * m + t]; },
                 [=](int j, int t) { return z[j * m + t]; },
                 [=](int j, int t, T zz, double old) { z[j * m + t] = old + (double)zz; }, err))
@@ -452,21 +597,24 @@ __global__ void __launch_bounds__(NT) k_local_jvp(int nsub, const SubDev* __rest
 }
 
 // Linear RAS preconditioner: Z = sum_i tilde P_i J_i^-1 R_i R.
-template <typename T>
+template <typename T, bool WIDE>
 __global__ void __launch_bounds__(NT) k_local_precond(int nsub, const SubDev* __restrict__ subs,
                                                       const ProbDev* __restrict__ probs, const T* gpool,
                                                       T* wpool, const double* R, double* Z, int* err,
                                                       const int* order, int* ticket) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ T vec[MAX_M], tmp[MAX_M];
+    __shared__ __align__(16) T vec[WIDE ? MAX_MW : MAX_M];
+    __shared__ __align__(16) T tmp[WIDE ? MAX_MW : MAX_M];
     __shared__ int sh_next;
     Stream<T> S;
-    stream_init(S, smem);
-    for (;;) {
-    const int pos = next_position(ticket, &sh_next);
+    if constexpr (WIDE) wide_stream_init(S, smem);
+    else stream_init(S, smem);
+    for (int it = 0;; ++it) {
+    const int pos = solve_position<WIDE>(it, ticket, &sh_next);
     if (pos >= nsub) break;
     const int i = order[pos];
     const SubDev s = subs[i];
+    if (!WIDE && s.mp > MAX_M) continue;
     const ProbDev P = probs[s.prob];
     const int m = 2 * s.bl, W = s.bw;
     const long long nn = P.nn;
@@ -487,7 +635,7 @@ __global__ void __launch_bounds__(NT) k_local_precond(int nsub, const SubDev* __
             gz < s.oz0 + s.owz)
             Zy[f * nn + grid_index(P, gx, gy, gz)] = (double)z;
     };
-    if (!stream_solve<T>(S, static_cast<const T*>(s.gptr), m, s.mp, W, (T)P.beta, wpool + s.voff, vec, tmp, rhs,
+    if (!local_solve<T, WIDE>(S, static_cast<const T*>(s.gptr), m, s.mp, W, (T)P.beta, wpool + s.voff, vec, tmp, rhs,
                          [=](int, int) { return 0.0; }, out, err))
         return;
     }
@@ -524,12 +672,12 @@ cudaError_t launch_local_direction(cudaStream_t st, int nsub, int ctas_per_sm, c
                                    double* dpool, double* rpool, T* wpool, int* err, const int* order,
                                    int* ticket) {
     const size_t sm = solve_smem<T>();
-    cudaError_t e = set_smem(k_local_direction<T>, sm);
+    cudaError_t e = set_smem(k_local_direction<T, false>, sm);
     int grid = 0;
-    if (e == cudaSuccess) e = persistent_grid(k_local_direction<T>, sm, nsub, ctas_per_sm, st, ticket, grid);
+    if (e == cudaSuccess) e = persistent_grid(k_local_direction<T, false>, sm, nsub, ctas_per_sm, st, ticket, grid);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_local_direction<T><<<grid, NT, sm, st>>>(nsub, subs, probs, ls, np, coef, gpool, Kpool, dpool, rpool,
+    k_local_direction<T, false><<<grid, NT, sm, st>>>(nsub, subs, probs, ls, np, coef, gpool, Kpool, dpool, rpool,
                                                wpool, err, order, ticket);
     return cudaGetLastError();
 }
@@ -540,12 +688,12 @@ cudaError_t launch_local_jvp(cudaStream_t st, int nsub, int ctas_per_sm, const S
                              double* zpool, double* rpool, double* bpool, int nir, const double* D,
                              double* O, const int* pmask, int* err, const int* order, int* ticket) {
     const size_t sm = solve_smem<T>();
-    cudaError_t e = set_smem(k_local_jvp<T>, sm);
+    cudaError_t e = set_smem(k_local_jvp<T, false>, sm);
     int grid = 0;
-    if (e == cudaSuccess) e = persistent_grid(k_local_jvp<T>, sm, nsub, ctas_per_sm, st, ticket, grid);
+    if (e == cudaSuccess) e = persistent_grid(k_local_jvp<T, false>, sm, nsub, ctas_per_sm, st, ticket, grid);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_local_jvp<T><<<grid, NT, sm, st>>>(nsub, subs, probs, gpool, wpool, coef, zpool, rpool, bpool, nir, D, O,
+    k_local_jvp<T, false><<<grid, NT, sm, st>>>(nsub, subs, probs, gpool, wpool, coef, zpool, rpool, bpool, nir, D, O,
                                          pmask, err, order, ticket);
     return cudaGetLastError();
 }
@@ -555,12 +703,55 @@ cudaError_t launch_local_precond(cudaStream_t st, int nsub, int ctas_per_sm, con
                                  const ProbDev* probs, const T* gpool, T* wpool, const double* R,
                                  double* Z, int* err, const int* order, int* ticket) {
     const size_t sm = solve_smem<T>();
-    cudaError_t e = set_smem(k_local_precond<T>, sm);
+    cudaError_t e = set_smem(k_local_precond<T, false>, sm);
     int grid = 0;
-    if (e == cudaSuccess) e = persistent_grid(k_local_precond<T>, sm, nsub, ctas_per_sm, st, ticket, grid);
+    if (e == cudaSuccess) e = persistent_grid(k_local_precond<T, false>, sm, nsub, ctas_per_sm, st, ticket, grid);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_local_precond<T><<<grid, NT, sm, st>>>(nsub, subs, probs, gpool, wpool, R, Z, err, order, ticket);
+    k_local_precond<T, false><<<grid, NT, sm, st>>>(nsub, subs, probs, gpool, wpool, R, Z, err, order, ticket);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_local_direction_wide(cudaStream_t st, int count, const int* list, const SubDev* subs,
+                                        const ProbDev* probs, LocalState* ls, NewtonParams np,
+                                        const double* coef, const T* gpool, const double* Kpool, double* dpool,
+                                        double* rpool, T* wpool, int* err) {
+    if (count <= 0) return cudaSuccess;
+    const size_t sm = wide_solve_smem<T>();
+    cudaError_t e = set_smem(k_local_direction<T, true>, sm);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_local_direction<T, true><<<count, NT, sm, st>>>(count, subs, probs, ls, np, coef, gpool, Kpool, dpool, rpool,
+                                                     wpool, err, list, nullptr);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_local_jvp_wide(cudaStream_t st, int count, const int* list, const SubDev* subs,
+                                  const ProbDev* probs, const T* gpool, T* wpool, const double* coef,
+                                  double* zpool, double* rpool, double* bpool, int nir, const double* D, double* O,
+                                  const int* pmask, int* err) {
+    if (count <= 0) return cudaSuccess;
+    const size_t sm = wide_solve_smem<T>();
+    cudaError_t e = set_smem(k_local_jvp<T, true>, sm);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_local_jvp<T, true><<<count, NT, sm, st>>>(count, subs, probs, gpool, wpool, coef, zpool, rpool, bpool, nir, D,
+                                               O, pmask, err, list, nullptr);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_local_precond_wide(cudaStream_t st, int count, const int* list, const SubDev* subs,
+                                      const ProbDev* probs, const T* gpool, T* wpool, const double* R, double* Z,
+                                      int* err) {
+    if (count <= 0) return cudaSuccess;
+    const size_t sm = wide_solve_smem<T>();
+    cudaError_t e = set_smem(k_local_precond<T, true>, sm);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_local_precond<T, true><<<count, NT, sm, st>>>(count, subs, probs, gpool, wpool, R, Z, err, list, nullptr);
     return cudaGetLastError();
 }
 
@@ -568,13 +759,13 @@ cudaError_t launch_local_precond(cudaStream_t st, int nsub, int ctas_per_sm, con
 cudaError_t solve_ctas_per_sm_max(bool f32, int* per_sm) {
     *per_sm = 0;
     if (f32) {
-        cudaError_t e = set_smem(k_local_precond<float>, solve_smem<float>());
+        cudaError_t e = set_smem(k_local_precond<float, false>, solve_smem<float>());
         if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_precond<float>, NT, solve_smem<float>());
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_precond<float, false>, NT, solve_smem<float>());
     }
-    cudaError_t e = set_smem(k_local_precond<double>, solve_smem<double>());
+    cudaError_t e = set_smem(k_local_precond<double, false>, solve_smem<double>());
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_precond<double>, NT, solve_smem<double>());
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_local_precond<double, false>, NT, solve_smem<double>());
 }
 
 #define RAS_INSTANTIATE(T)                                                                              \
@@ -586,7 +777,17 @@ cudaError_t solve_ctas_per_sm_max(bool f32, int* per_sm) {
                                              T*, const double*, double*, double*, double*, int,                \
                                              const double*, double*, const int*, int*, const int*, int*);      \
     template cudaError_t launch_local_precond<T>(cudaStream_t, int, int, const SubDev*, const ProbDev*,        \
-                                                 const T*, T*, const double*, double*, int*, const int*, int*);
+                                                 const T*, T*, const double*, double*, int*, const int*, int*);  \
+    template cudaError_t launch_local_direction_wide<T>(cudaStream_t, int, const int*, const SubDev*,         \
+                                                        const ProbDev*, LocalState*, NewtonParams,             \
+                                                        const double*, const T*, const double*, double*,       \
+                                                        double*, T*, int*);                                    \
+    template cudaError_t launch_local_jvp_wide<T>(cudaStream_t, int, const int*, const SubDev*, const ProbDev*, \
+                                                  const T*, T*, const double*, double*, double*, double*, int, \
+                                                  const double*, double*, const int*, int*);                   \
+    template cudaError_t launch_local_precond_wide<T>(cudaStream_t, int, const int*, const SubDev*,           \
+                                                      const ProbDev*, const T*, T*, const double*, double*,    \
+                                                      int*);
 RAS_INSTANTIATE(float)
 RAS_INSTANTIATE(double)
 #undef RAS_INSTANTIATE

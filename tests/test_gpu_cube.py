@@ -217,8 +217,27 @@ def test_cube_manufactured_root():
         ras.ras_destroy(h)
 
 
-def test_cube_refuses_planes_over_80_nodes():
-    cfg = inputs.problem3("c15", sx=1, sy=1, sz=3)   # planes of 15 x 15 nodes
+@pytest.mark.parametrize("prec,tol", PRECS)
+def test_cube_wide_planes(prec, tol):
+    """Box planes of 9 x 9 nodes (162 unknowns): the wide-block path on the
+    cube, a full RASPEN solve against the oracle."""
+    cfg = inputs.problem3("c15", sx=2, sy=2, sz=3)
+    ref = t3.raspen(oracle_problem3(cfg), cfg["sx"], cfg["sy"], cfg["sz"], cfg["overlap"], oracle_opts3(cfg))
+    n = cfg["n"]
+    h = gpu_problem3(cfg, prec)
+    try:
+        y, p = zeros3(n), zeros3(n)
+        rc, st = ras.ras_raspen_solve(h, y, p)
+        assert rel_inf(y.cpu().numpy(), ref.Y) <= tol
+        assert rel_inf(p.cpu().numpy(), ref.P) <= tol
+        assert st.outer_its == ref.outer
+        assert st.inner_its_sum == sum(sum(i) for i in ref.inner_its)
+    finally:
+        ras.ras_destroy(h)
+
+
+def test_cube_refuses_planes_over_256_nodes():
+    cfg = inputs.problem3("c15", n=17, sx=1, sy=1, sz=3)   # planes of 17 x 17 nodes
     with pytest.raises(ras.RasError):
         gpu_problem3(cfg, ras.RAS_FP64)
     cfg = inputs.problem3("c15", sz=0)

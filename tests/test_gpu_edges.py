@@ -1,5 +1,6 @@
 """Edge cases of the CUDA path against the oracle: the smallest grid, data
-whose root is x = 0, the widest local block the kernels take (2 wx = 160),
+whose root is x = 0, the widest local block of the register-tile and
+streaming kernels (2 wx = 160; wider blocks take the wide-block path),
 an inactive control (mu large: u = 0 everywhere), and empty batches."""
 import numpy as np
 import pytest
@@ -75,7 +76,8 @@ def test_zero_data_root_is_zero(solve):
 @pytest.mark.parametrize("prec,tol", PRECS)
 def test_widest_block_matches_oracle(prec, tol):
     """One 80 x 80 subdomain: local block rows of 2 wx = 160 unknowns, the
-    most the kernels take (the 10 x 10 and 5 x 5 register tiles of 160)."""
+    most the register-tile factorisations and the streaming solves take (the
+    10 x 10 and 5 x 5 register tiles of 160)."""
     n = 80
     c = _cfg(n=n, sx=1, sy=1, overlap=0, nu=1e-4, mu=1e-3)
     prob = oracle_problem(c)

@@ -221,7 +221,7 @@ def test_invalid_arguments():
     with pytest.raises(ras.RasError):
         ras.ras_create(n, 2, 2, 1, 0, -1.0, 1e-3, yd)              # nu <= 0
     with pytest.raises(ras.RasError):
-        ras.ras_create(200, 1, 1, 0, 0, 1e-4, 1e-3, to_dev(inputs.yd_sine(200)))  # 2*wx > 160
+        ras.ras_create(300, 1, 1, 0, 0, 1e-4, 1e-3, to_dev(inputs.yd_sine(300)))  # 2*wx > 512
     with pytest.raises(ras.RasError):
         ras.ras_create(n, 2, 2, 1, 7, 1e-4, 1e-3, yd)              # unknown phi
     h = ras.ras_create(n, 2, 2, 1, 0, 1e-4, 1e-3, yd)

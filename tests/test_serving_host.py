@@ -49,7 +49,7 @@ def test_request_bytes_rejects_invalid_and_too_wide():
     with pytest.raises(ras.RasError):
         ras.ras_server_request_bytes(_d(63, nu=-1.0))
     with pytest.raises(ras.RasError):
-        ras.ras_server_request_bytes(dict(n=255, sx=1, sy=1, overlap=2, phi=0, nu=1e-4, mu=1e-3))   # 2 wx > 160
+        ras.ras_server_request_bytes(dict(n=300, sx=1, sy=1, overlap=2, phi=0, nu=1e-4, mu=1e-3))   # 2 wx > 512
 
 
 def test_uneven_batch_fits_the_serving_budget():
