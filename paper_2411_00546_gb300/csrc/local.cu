@@ -1162,22 +1162,108 @@ __global__ void __launch_bounds__(1024, 1) k_local_factor_wide(int nsub, const S
 }
 
 // ------------------------------------------------------------- wide blocks
-// Factorisation of a wide-block subdomain (MAX_M < m = 2 bl <= MAX_MW), one
-// 1024-thread CTA per subdomain. Block row j is formed and inverted in place
-// in its own factor slot (row-major, mp x mp): S_j = D_j - beta^2 G_{j-1},
-// inverted by the Gauss-Jordan sweep of k_local_factor_panel taken BIG_PANEL
-// pivots at a time. The column panel and the row panel (with zeros at the
-// panel's own columns) are staged in shared memory; the column panel is swept
-// with one thread per row, the pivot row passed on in a double-buffered copy
-// (one barrier per pivot); then one rank-BIG_PANEL update of the block in
-// HBM/L2 leaves the column panel at C', rows K at C'[K,K] M[K,J] and every
-// other row at M[I,J] + C'[I,K] M[K,J]. The partial-pivoting check is the
-// panel kernel's (a pivot smaller than an entry below it in its column, or
-// not finite); a block row that fails it is redone by unblocked Gauss-Jordan
-// with row interchanges (max |.| in the column, ties to the lowest row), the
-// interchanges undone on the columns at the end, last first. When all block
-// rows are done every slot is transposed in place: the wide solves read G_j
-// column-major.
+// Cluster primitives (the CTAs of one thread-block cluster).
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_size() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// Every thread of every CTA of the cluster; memory operations before it are
+// visible to the cluster after it.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// An int in the shared memory of CTA `rank` of the cluster, at the offset of
+// `p` in this CTA's.
+__device__ __forceinline__ int ld_cluster_int(const int* p, uint32_t rank) {
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    uint32_t ra;
+    int v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
+    return v;
+}
+
+// 16 consecutive T of a panel row (16-byte aligned) <-> registers.
+template <typename T>
+__device__ __forceinline__ void ld_row16(const T* src, T (&v)[BIG_PANEL]) {
+    static_assert(BIG_PANEL == 16, "16 entries per panel row");
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 t = reinterpret_cast<const float4*>(src)[q];
+            v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const double2 t = reinterpret_cast<const double2*>(src)[q];
+            v[2 * q] = t.x; v[2 * q + 1] = t.y;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void st_row16(T* dst, const T (&v)[BIG_PANEL]) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) reinterpret_cast<double2*>(dst)[q] = make_double2(v[2 * q], v[2 * q + 1]);
+    }
+}
+
+// A T in the shared memory of CTA `rank` of the cluster, at the offset of `p`
+// in this CTA's.
+template <typename T>
+__device__ __forceinline__ T ld_cluster(const T* p, uint32_t rank) {
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    if constexpr (sizeof(T) == 4) {
+        float v;
+        asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(ra) : "memory");
+        return v;
+    } else {
+        double v;
+        asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
+        return v;
+    }
+}
+
+// Factorisation of a wide-block subdomain (MAX_M < m = 2 bl <= MAX_MW) by one
+// cluster of 1024-thread CTAs (BIG_CLUSTER of them; the kernel reads the
+// cluster's size, so one CTA per subdomain works too). Block row j is formed
+// and inverted in place in its own factor slot (row-major, mp x mp):
+// S_j = D_j - beta^2 G_{j-1}, inverted by the Gauss-Jordan sweep of
+// k_local_factor_panel taken BIG_PANEL pivots at a time. The columns of the
+// block are split among the CTAs in whole panels; CTA b forms and updates its
+// own columns only. For the panel K of CTA o: thread r of CTA o holds row r
+// of the column panel in registers and sweeps it (the pivot row passed on in
+// a double-buffered shared copy, one barrier per pivot), then writes C' back
+// into M[:, K]; after one cluster barrier every CTA reads C' from there into
+// shared memory and applies
+// the rank-BIG_PANEL update to its columns: rows K become C'[K,K] M[K,J] and
+// every other row M[I,J] + C'[I,K] M[K,J]. One cluster barrier per panel
+// suffices: M[:, K] changes again only in the next panel's update, after the
+// next barrier. The partial-pivoting check is the panel kernel's (a pivot
+// smaller than an entry below it in its column, or not finite), reported by
+// CTA o in a double-buffered flag in its shared memory that the others read;
+// a block row that fails it is redone by unblocked Gauss-Jordan with row
+// interchanges (max |.| in the column, ties to the lowest row) over the
+// cluster, the interchanges undone on the columns at the end, last first.
+// Each G_j is transposed in place once the next block row has read it (G_{W-1}
+// at the end), while it is still in L2: the wide solves read G_j column-major.
 template <typename T>
 __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, const int* __restrict__ list,
                                                                   const SubDev* __restrict__ subs,
@@ -1185,10 +1271,10 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
                                                                   const double* X, LocalState* ls,
                                                                   const double* cpool, double* coef, T* gpool,
                                                                   int only_active) {
-    constexpr int NTH = BIG_THREADS, NWB = NTH / 32, RB = BIG_PANEL, CS = RB + 1;
+    constexpr int NTH = BIG_THREADS, NWB = NTH / 32, RB = BIG_PANEL, CS = RB;
     static_assert(MAX_MW <= NTH, "one panel row per thread in the sweep");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* Cs = reinterpret_cast<T*>(smem_raw);   // column panel: row r at Cs + r * CS (odd stride)
+    T* Cs = reinterpret_cast<T*>(smem_raw);   // C' of the panel: row r at Cs + r * CS
     T* Rs = Cs + MAX_MW * CS;                 // row panel: pivot kk at Rs + kk * MAX_MW
     T* colk = Rs + RB * MAX_MW;               // pivot column of the pivoted fallback
     T* prow = colk + MAX_MW;                  // pivot row of the sweep, two copies
@@ -1196,8 +1282,13 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
     __shared__ T red_v[NWB];
     __shared__ int red_i[NWB];
     __shared__ int sh_fail, sh_r;
-    if ((int)blockIdx.x >= count) return;
-    const int i = list[blockIdx.x];
+    __shared__ int sh_bad[2];                 // pivoting check of the last two panels this CTA swept
+    __shared__ int pub_row[2];                // pivoted fallback: the pivot rows this CTA published
+    __shared__ T pub_col[2 * MAX_MW];         // and the columns k (after the interchange)
+    const uint32_t nct = cluster_size(), rank = cluster_rank();
+    const int sidx = (int)(blockIdx.x / nct);
+    if (sidx >= count) return;
+    const int i = list[sidx];
     if (only_active && !ls[i].active) return;
     if (ls[i].status == ST_SKIP) return;
     const SubDev s = subs[i];
@@ -1205,6 +1296,9 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
     const int m = 2 * s.bl, W = s.bw, nn = s.wx * s.wy * s.wz, mp = s.mp;
     const bool cube = P.nz > 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // columns of this CTA: [cl, ch), whole panels
+    const int pw = ((m + (int)nct * RB - 1) / ((int)nct * RB)) * RB;
+    const int cl = min(m, (int)rank * pw), ch = min(m, cl + pw), ncol = ch - cl;
 
     const double eps = ls[i].eps;
     const double beta = P.beta, inu = 1.0 / P.nu, mu = P.mu;
@@ -1214,7 +1308,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
     {
         const double* c = cpool + s.voff;
         const LocalView V = make_view(s, P, X, c, nullptr, 0.0);
-        for (int q = tid; q < nn; q += NTH) {
+        for (int q = (int)rank * NTH + tid; q < nn; q += (int)nct * NTH) {
             const double y = V.at(q, 0), p = V.at(q, 1);
             double ph, d1, d2;
             phi_eval(P.phi, P.kappa, y, ph, d1, d2);
@@ -1224,7 +1318,8 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
         }
     }
     if (tid == 0) sh_fail = 0;
-    __syncthreads();
+    __threadfence();
+    cluster_sync();   // coefficients of the whole box written
 
     const T tbeta = (T)beta, tbeta2 = (T)(beta * beta), tdiag = (T)P.diag;
     T* G = static_cast<T*>(s.gptr);
@@ -1238,82 +1333,126 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
         }
         return (cf == f && row_neighbour(ix, cx, s.wx, cube)) ? -tbeta : (T)0;
     };
-    auto form = [&](int j, T* M) {                 // M = S_j (G_{j-1} still row-major)
+    // columns [c0, c0 + nc) of M = S_j; G_{j-1} row-major, or column-major once transposed
+    auto form = [&](int j, T* M, int c0, int nc, bool gp_colmajor) {
         const T* Gp = G + (long long)(j > 0 ? j - 1 : 0) * blk;
-        for (int e = tid; e < m * m; e += NTH) {
-            const int r = e / m, c = e - r * m;
-            const T g = (j > 0) ? -tbeta2 * Gp[(long long)r * mp + c] : (T)0;
+        for (int e = tid; e < m * nc; e += NTH) {
+            const int r = e / nc, c = c0 + (e - r * nc);
+            const long long gi = gp_colmajor ? (long long)c * mp + r : (long long)r * mp + c;
+            const T g = (j > 0) ? -tbeta2 * Gp[gi] : (T)0;
             M[(long long)r * mp + c] = g + dval(j, r, c);
         }
     };
-    const int mc = ((m + 31) / 32) * 32;           // update: columns padded to whole warps,
-    const int rows_par = NTH / mc;                  // rows_par threads per column
-    const int ucol = tid % mc, urow = tid / mc;
+    // G_j to column-major in place, while it is still in L2: CTA b swaps the
+    // pairs (r, c), r < c, of its own columns c
+    auto transpose = [&](int j) {
+        T* M = G + (long long)j * blk;
+        for (int e = tid; e < m * ncol; e += NTH) {
+            const int r = e / ncol, c = cl + (e - r * ncol);
+            if (r < c) {
+                const T a = M[(long long)r * mp + c];
+                M[(long long)r * mp + c] = M[(long long)c * mp + r];
+                M[(long long)c * mp + r] = a;
+            }
+        }
+    };
+    const int mc = ((ncol + 31) / 32) * 32;        // update: own columns padded to whole warps,
+    const int rows_par = (mc > 0) ? NTH / mc : 1;  // rows_par threads per column
+    const int ucol = (mc > 0) ? tid % mc : 0, urow = (mc > 0) ? tid / mc : NTH;
 
     bool failed = false;
     for (int j = 0; j < W && !failed; ++j) {
         T* M = G + (long long)j * blk;
-        form(j, M);
-        bool viol = false;   // the pivoting check failed (the same on every thread)
+        form(j, M, cl, ncol, false);
+        if (j > 0) {
+            cluster_sync();   // every CTA has read G_{j-1}
+            transpose(j - 1);
+        }
+        bool viol = false;   // the pivoting check failed (the same on every thread of the cluster)
         __syncthreads();
         for (int k0 = 0; k0 < m; k0 += RB) {
             const int nk = min(RB, m - k0);
-            for (int e = tid; e < m * RB; e += NTH) {
-                const int r = e / RB, kk = e - r * RB;
-                Cs[r * CS + kk] = (kk < nk) ? M[(long long)r * mp + k0 + kk] : (T)0;
+            const uint32_t owner = (uint32_t)(k0 / pw);
+            // the owner's flag slot: parity of its panels before this one in the block row
+            const int slot = ((k0 - (int)owner * pw) / RB) & 1;
+            if (rank == owner) {
+                // thread r < m: row r of the column panel in registers
+                T v[RB];
+                if (tid < m) {
+                    ld_row16<T>(M + (long long)tid * mp + k0, v);
+#pragma unroll
+                    for (int kk = 0; kk < RB; ++kk)
+                        if (kk >= nk) v[kk] = (T)0;
+                }
+                if (tid == k0) {
+#pragma unroll
+                    for (int c = 0; c < RB; ++c) prow[c] = v[c];
+                }
+                __syncthreads();
+                bool bad = false;
+#pragma unroll
+                for (int kk = 0; kk < RB; ++kk) {
+                    if (kk < nk) {
+                        const T* pv = prow + (kk & 1) * RB;   // the pivot row, after pivot kk - 1
+                        const int r0 = k0 + kk;
+                        const T d = pv[kk], ad = fabs(d);
+                        const T inv = (T)1 / d;
+                        if (tid == r0) {
+                            bad |= !(ad > (T)0 && ad < (T)INFINITY);
+#pragma unroll
+                            for (int c = 0; c < RB; ++c) v[c] = (c == kk) ? inv : pv[c] * inv;
+                        } else if (tid < m) {
+                            const T f = v[kk];
+                            bad |= (tid > r0) && (fabs(f) > ad);
+#pragma unroll
+                            for (int c = 0; c < RB; ++c) {
+                                const T t = (c == kk) ? inv : pv[c] * inv;
+                                v[c] = fma(-f, t, (c == kk) ? (T)0 : v[c]);
+                            }
+                            if (tid == r0 + 1 && kk + 1 < nk) {
+#pragma unroll
+                                for (int c = 0; c < RB; ++c) prow[((kk + 1) & 1) * RB + c] = v[c];
+                            }
+                        }
+                        __syncthreads();
+                    }
+                }
+                const int b = __syncthreads_or(bad) ? 1 : 0;
+                if (tid == 0) sh_bad[slot] = b;
+                // C' into M[:, K] (columns past m are padding) and into shared memory
+                if (tid < m) {
+                    st_row16<T>(M + (long long)tid * mp + k0, v);
+                    st_row16<T>(Cs + tid * CS, v);
+                }
+                __threadfence();
             }
-            for (int e = tid; e < RB * m; e += NTH) {
-                const int kk = e / m, c = e - kk * m;
+            cluster_sync();   // C' of panel K and its flag visible to the cluster
+            if (ld_cluster_int(&sh_bad[slot], owner)) {
+                viol = true;
+                break;
+            }
+            if (rank != owner && tid < m) {
+                T v[RB];
+                ld_row16<T>(M + (long long)tid * mp + k0, v);
+#pragma unroll
+                for (int kk = 0; kk < RB; ++kk)
+                    if (kk >= nk) v[kk] = (T)0;
+                st_row16<T>(Cs + tid * CS, v);
+            }
+            for (int e = tid; e < RB * ncol; e += NTH) {
+                const int kk = e / ncol, c = cl + (e - kk * ncol);
                 Rs[kk * MAX_MW + c] =
                     (kk < nk && (c < k0 || c >= k0 + nk)) ? M[(long long)(k0 + kk) * mp + c] : (T)0;
             }
             __syncthreads();
-            if (tid < RB) prow[tid] = Cs[k0 * CS + tid];
-            __syncthreads();
-            {
-                // thread r < m sweeps row r of the column panel; the pivot
-                // row reaches everyone through prow (its next version written
-                // by the owner of the next pivot row while it updates)
-                bool bad = false;
-                T* row = Cs + tid * CS;
-                for (int kk = 0; kk < nk; ++kk) {
-                    const T* pr = prow + (kk & 1) * RB;
-                    const int r0 = k0 + kk;
-                    const T d = pr[kk], ad = fabs(d);
-                    const T inv = (T)1 / d;
-                    if (tid == r0) {
-                        bad |= !(ad > (T)0 && ad < (T)INFINITY);
-#pragma unroll
-                        for (int c = 0; c < RB; ++c) row[c] = (c == kk) ? inv : pr[c] * inv;
-                    } else if (tid < m) {
-                        T* nx = (tid == r0 + 1 && kk + 1 < nk) ? prow + ((kk + 1) & 1) * RB : nullptr;
-                        const T f = row[kk];
-                        bad |= (tid > r0) && (fabs(f) > ad);
-#pragma unroll
-                        for (int c = 0; c < RB; ++c) {
-                            const T t = (c == kk) ? inv : pr[c] * inv;
-                            const T v = fma(-f, t, (c == kk) ? (T)0 : row[c]);
-                            row[c] = v;
-                            if (nx) nx[c] = v;
-                        }
-                    }
-                    __syncthreads();
-                }
-                if (__syncthreads_or(bad)) {
-                    viol = true;
-                    break;
-                }
-            }
-            if (ucol < m && urow < rows_par) {
-                const int c = ucol;
-                if (c >= k0 && c < k0 + nk) {
-                    for (int r = urow; r < m; r += rows_par) M[(long long)r * mp + c] = Cs[r * CS + (c - k0)];
-                } else {
+            if (ucol < ncol && urow < rows_par) {
+                const int c = cl + ucol;
+                if (c < k0 || c >= k0 + nk) {
                     T rv[RB];
 #pragma unroll
                     for (int kk = 0; kk < RB; ++kk) rv[kk] = Rs[kk * MAX_MW + c];
                     // UR rows at a time, their loads issued before any is used
-                    constexpr int UR = 8;
+                    constexpr int UR = sizeof(T) == 4 ? 8 : 4;
                     for (int r0 = urow; r0 < m; r0 += UR * rows_par) {
                         T acc[UR];
 #pragma unroll
@@ -1325,9 +1464,15 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
                         for (int u = 0; u < UR; ++u) {
                             const int r = r0 + u * rows_par;
                             if (r < m) {
-                                const T* cr = Cs + r * CS;
+                                if constexpr (sizeof(T) == 4) {
+                                    T cv[RB];
+                                    ld_row16<T>(Cs + r * CS, cv);
 #pragma unroll
-                                for (int kk = 0; kk < RB; ++kk) acc[u] = fma(cr[kk], rv[kk], acc[u]);
+                                    for (int kk = 0; kk < RB; ++kk) acc[u] = fma(cv[kk], rv[kk], acc[u]);
+                                } else {
+#pragma unroll
+                                    for (int kk = 0; kk < RB; ++kk) acc[u] = fma(Cs[r * CS + kk], rv[kk], acc[u]);
+                                }
                                 M[(long long)r * mp + c] = acc[u];
                             }
                         }
@@ -1337,30 +1482,24 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
             __syncthreads();
         }
         if (!viol) continue;
-        // Gauss-Jordan with row interchanges, from S_j again
-        form(j, M);
+        // Gauss-Jordan with row interchanges over the cluster: the owner of
+        // column k picks the pivot row and publishes it with column k (after
+        // the interchange); every CTA applies the interchange, the scaling of
+        // row k and the elimination to its own columns. One cluster barrier
+        // per pivot; the published copies alternate between two buffers.
+        cluster_sync();   // every CTA has stopped writing the block
+        form(j, M, cl, ncol, true);
         __syncthreads();
         for (int k = 0; k < m; ++k) {
-            T best = (T)-1;
-            int bi = 0x7fffffff;
-            for (int r = k + tid; r < m; r += NTH) {
-                const T v = fabs(M[(long long)r * mp + k]);
-                if (v > best) { best = v; bi = r; }
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const T ob = __shfl_xor_sync(0xffffffffu, best, off);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-            }
-            if (lane == 0) {
-                red_v[warp] = best;
-                red_i[warp] = bi;
-            }
-            __syncthreads();
-            if (warp == 0) {
-                best = (lane < NWB) ? red_v[lane] : (T)-1;
-                bi = (lane < NWB) ? red_i[lane] : 0x7fffffff;
+            const uint32_t owner = (uint32_t)(k / pw);
+            const int sl = k & 1;
+            if (rank == owner) {
+                T best = (T)-1;
+                int bi = 0x7fffffff;
+                for (int r = k + tid; r < m; r += NTH) {
+                    const T v = fabs(M[(long long)r * mp + k]);
+                    if (v > best) { best = v; bi = r; }
+                }
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
                     const T ob = __shfl_xor_sync(0xffffffffu, best, off);
@@ -1368,74 +1507,90 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
                     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
                 }
                 if (lane == 0) {
-                    if (bi >= m || !(best > (T)0) || !(best < (T)INFINITY)) {
-                        sh_fail = 1;
-                    } else {
-                        sh_r = bi;
-                        piv[k] = bi;
+                    red_v[warp] = best;
+                    red_i[warp] = bi;
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    best = (lane < NWB) ? red_v[lane] : (T)-1;
+                    bi = (lane < NWB) ? red_i[lane] : 0x7fffffff;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const T ob = __shfl_xor_sync(0xffffffffu, best, off);
+                        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                    }
+                    if (lane == 0)
+                        pub_row[sl] = (bi >= m || !(best > (T)0) || !(best < (T)INFINITY)) ? -1 : bi;
+                }
+                __syncthreads();
+                const int pr = pub_row[sl];
+                if (pr >= 0) {
+                    for (int r = tid; r < m; r += NTH) {
+                        const int rs = (r == k) ? pr : ((r == pr) ? k : r);
+                        pub_col[sl * MAX_MW + r] = M[(long long)rs * mp + k];
                     }
                 }
             }
-            __syncthreads();
-            if (sh_fail) break;
-            const int pr = sh_r;
-            if (pr != k) {
-                for (int c = tid; c < m; c += NTH) {
-                    const T a = M[(long long)k * mp + c];
-                    M[(long long)k * mp + c] = M[(long long)pr * mp + c];
-                    M[(long long)pr * mp + c] = a;
-                }
+            cluster_sync();   // pivot row and column k published
+            const int pr = ld_cluster_int(&pub_row[sl], owner);
+            if (pr < 0) {
+                if (tid == 0) sh_fail = 1;
+                break;
             }
-            __syncthreads();
-            for (int r = tid; r < m; r += NTH) colk[r] = M[(long long)r * mp + k];
+            for (int r = tid; r < m; r += NTH) colk[r] = ld_cluster<T>(&pub_col[sl * MAX_MW + r], owner);
+            if (tid == 0) piv[k] = pr;
             __syncthreads();
             const T inv = (T)1 / colk[k];
-            for (int c = tid; c < m; c += NTH)
-                M[(long long)k * mp + c] = ((c == k) ? (T)1 : M[(long long)k * mp + c]) * inv;
+            for (int c = cl + tid; c < ch; c += NTH) {
+                T a = M[(long long)k * mp + c];
+                if (pr != k) {
+                    const T b = M[(long long)pr * mp + c];
+                    M[(long long)pr * mp + c] = a;
+                    a = b;
+                }
+                M[(long long)k * mp + c] = ((c == k) ? (T)1 : a) * inv;
+            }
             __syncthreads();
-            for (int e = tid; e < m * m; e += NTH) {
-                const int r = e / m, c = e - r * m;
+            for (int e = tid; e < m * ncol; e += NTH) {
+                const int r = e / ncol, c = cl + (e - r * ncol);
                 if (r == k) continue;
                 const T old = (c == k) ? (T)0 : M[(long long)r * mp + c];
                 M[(long long)r * mp + c] = old - colk[r] * M[(long long)k * mp + c];
             }
             __syncthreads();
         }
-        if (sh_fail) {
-            failed = true;
-            break;
-        }
-        for (int k = m - 1; k >= 0; --k) {
-            const int pr = piv[k];
-            if (pr != k) {
-                for (int r = tid; r < m; r += NTH) {
+        __syncthreads();
+        failed = sh_fail != 0;   // the same on every CTA: all read the same published rows
+        if (!failed) {
+            // undo the interchanges on the columns, last first: CTA b swaps
+            // within its share of the rows
+            cluster_sync();   // every CTA's elimination is done
+            const int rw = (m + (int)nct - 1) / (int)nct;
+            const int rl = min(m, (int)rank * rw), rh = min(m, rl + rw);
+            for (int k = m - 1; k >= 0; --k) {
+                const int pr = piv[k];
+                if (pr == k) continue;
+                for (int r = rl + tid; r < rh; r += NTH) {
                     const T a = M[(long long)r * mp + k];
                     M[(long long)r * mp + k] = M[(long long)r * mp + pr];
                     M[(long long)r * mp + pr] = a;
                 }
             }
-            __syncthreads();
         }
+        __threadfence();
+        cluster_sync();   // the block visible to the cluster
     }
     if (failed) {
-        if (tid == 0) {
+        if (rank == 0 && tid == 0) {
             ls[i].status = ST_ESINGULAR;
             ls[i].active = 0;
         }
-        return;
+    } else {
+        cluster_sync();   // every CTA's last update is done
+        transpose(W - 1);
     }
-    // every G_j to column-major, in place
-    for (int j = 0; j < W; ++j) {
-        T* M = G + (long long)j * blk;
-        for (int e = tid; e < m * m; e += NTH) {
-            const int r = e / m, c = e - r * m;
-            if (r < c) {
-                const T a = M[(long long)r * mp + c];
-                M[(long long)r * mp + c] = M[(long long)c * mp + r];
-                M[(long long)c * mp + r] = a;
-            }
-        }
-    }
+    cluster_sync();   // no CTA leaves while another may read its shared memory
 }
 
 template <typename T>
@@ -1533,13 +1688,39 @@ cudaError_t launch_local_factor_big(cudaStream_t st, int count, const int* list,
                                     const ProbDev* probs, const double* X, LocalState* ls, const double* cpool,
                                     double* coef, T* gpool, int only_active) {
     if (count <= 0) return cudaSuccess;
-    const size_t sm = (size_t)(MAX_MW * (BIG_PANEL + 1) + BIG_PANEL * MAX_MW + MAX_MW + 2 * BIG_PANEL) * sizeof(T);
+    const size_t sm = (size_t)(MAX_MW * BIG_PANEL + BIG_PANEL * MAX_MW + MAX_MW + 2 * BIG_PANEL) * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(k_local_factor_big<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    // one cluster of BIG_CLUSTER CTAs per subdomain, fewer if the device cannot place that many
+    static int csize = 0;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(BIG_THREADS);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    if (csize == 0) {
+        for (int c = BIG_CLUSTER; c >= 1; c /= 2) {
+            cfg.gridDim = dim3((unsigned)c);
+            attr[0].val.clusterDim.x = (unsigned)c;
+            int ncl = 0;
+            if (cudaOccupancyMaxActiveClusters(&ncl, k_local_factor_big<T>, &cfg) == cudaSuccess && ncl > 0) {
+                csize = c;
+                break;
+            }
+            cudaGetLastError();
+        }
+        if (csize == 0) return cudaErrorLaunchOutOfResources;
+    }
+    cfg.gridDim = dim3((unsigned)(count * csize));
+    attr[0].val.clusterDim.x = (unsigned)csize;
     count_launch();
-    k_local_factor_big<T><<<count, BIG_THREADS, sm, st>>>(count, list, subs, probs, X, ls, cpool, coef, gpool,
-                                                          only_active);
-    return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, k_local_factor_big<T>, count, list, subs, probs, X, ls, cpool, coef, gpool,
+                              only_active);
 }
 
 cudaError_t launch_local_linesearch(cudaStream_t st, int nsub, const SubDev* subs, const ProbDev* probs,

@@ -34,6 +34,7 @@ constexpr int MAX_M = 160;          // max unknowns of a block row on the regist
 constexpr int MAX_MW = 512;         // max unknowns of a block row on the wide-block path
 constexpr int BIG_THREADS = 1024;   // threads of the wide-block factorisation kernel
 constexpr int BIG_PANEL = 16;       // pivots per panel of the wide-block factorisation
+constexpr int BIG_CLUSTER = 8;      // CTAs (one per SM) factorising one wide-block subdomain
 constexpr int FACT_THREADS = 256;   // threads of the factorisation kernel
 constexpr int LOC_THREADS = 256;    // threads of the per-subdomain kernels
 constexpr int VEC_THREADS = 256;    // threads of the grid-stride vector kernels
@@ -336,9 +337,10 @@ cudaError_t launch_local_factor(cudaStream_t st, int nsub, int maxm, const SubDe
                                 const ProbDev* probs, const double* X, LocalState* ls,
                                 const double* cpool, double* coef, T* gpool, int only_active);
 // Factorisation of the `count` wide-block subdomains in `list` (device
-// indices, MAX_M < 2*bl <= MAX_MW): one 1024-thread CTA each, the block in
-// its own factor slot in HBM (blocked Gauss-Jordan, panels of BIG_PANEL
-// pivots staged in shared memory), G_j stored column-major.
+// indices, MAX_M < 2*bl <= MAX_MW): one cluster of BIG_CLUSTER 1024-thread
+// CTAs each, the block in its own factor slot in HBM (blocked Gauss-Jordan,
+// panels of BIG_PANEL pivots staged in shared memory, the columns split among
+// the CTAs), G_j stored column-major.
 template <typename T>
 cudaError_t launch_local_factor_big(cudaStream_t st, int count, const int* list, const SubDev* subs,
                                     const ProbDev* probs, const double* X, LocalState* ls, const double* cpool,
