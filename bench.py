@@ -320,7 +320,7 @@ def measure_cfg2(ras, torch, dev, stream):
                                         for r in rows)}
 
 
-def measure_paper_workload(ras, torch, dev, stream):
+def measure_paper_workload(ras, torch, dev, stream, only=None):
     """The paper's model problem (Sec. 4): n = 450, phi = kappa (y^3 +
     exp(kappa y)), kappa = 0.1, nu = 1e-6, mu = 1, f = 0, pbar = 1.3 mu
     sin(10 pi x1) sin(10 pi x2), ybar and y_d from ras_manufacture at eps =
@@ -331,7 +331,7 @@ def measure_paper_workload(ras, torch, dev, stream):
     seconds per solve) timed on their first solve; each with its distance to
     the manufactured pair (which solves the eps = 1e-15 system). The paper's
     schedule down to eps_min = 1e-15 runs on 10 x 10, 6 x 2, 15 x 15, 2 x 2
-    and 2 x 5."""
+    and 2 x 5. only: layouts "SXxSY" to run (None: all)."""
     import numpy as np
     from paper_2411_00546_gb300 import inputs
     n, nu, mu, kappa = 450, 1e-6, 1.0, 0.1
@@ -344,6 +344,8 @@ def measure_paper_workload(ras, torch, dev, stream):
     t_make = None
     wide = ((2, 2), (2, 5), (3, 3), (4, 4), (5, 5))
     for sx, sy in ((6, 6), (9, 9), (10, 10), (15, 15), (6, 2), (9, 2), (15, 2)) + wide:
+        if only is not None and "%dx%d" % (sx, sy) not in only:
+            continue
         h = ras.ras_create(n, sx, sy, 2, ras.RAS_PHI_KAPPA, nu, mu, yd, None, o, stream=stream.cuda_stream)
         if t_make is None:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -376,6 +378,8 @@ def measure_paper_workload(ras, torch, dev, stream):
     o15 = ras.make_opts(tol=1e-10, inner_tol=1e-8, sigma=1.1, eps0=1.0, gamma=0.2, eps_min=1e-15,
                         precision=ras.RAS_MIXED, kappa=kappa)
     for sx, sy in ((10, 10), (6, 2), (15, 15), (2, 2), (2, 5)):
+        if only is not None and "%dx%d" % (sx, sy) not in only:
+            continue
         h = ras.ras_create(n, sx, sy, 2, ras.RAS_PHI_KAPPA, nu, mu, yd, None, o15, stream=stream.cuda_stream)
         y = torch.zeros_like(pbar)
         p = torch.zeros_like(pbar)
@@ -722,6 +726,8 @@ def parse_args():
     ap.add_argument("--no-active", action="store_true")
     ap.add_argument("--no-sensitivity", action="store_true")
     ap.add_argument("--no-cube", action="store_true")
+    ap.add_argument("--paper-layouts", default=None,
+                    help="comma-separated layouts of the model-problem leg, e.g. 2x2,2x5 (default: all)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="GMRES cycles step by step (every kernel visible to a profiler's launch list)")
     ap.add_argument("--serve-requests", type=int, default=32)
@@ -1250,7 +1256,8 @@ def main():
         sweeps = measure_sweeps(ras, torch, dev, stream)
     paper = None
     if rank == 0 and not args.no_paper:
-        paper = measure_paper_workload(ras, torch, dev, stream)
+        paper = measure_paper_workload(ras, torch, dev, stream,
+                                       args.paper_layouts.split(",") if args.paper_layouts else None)
     active = None
     if rank == 0 and not args.no_active and args.workload == "n1023":
         active = measure_active(ras, torch, dev, stream)

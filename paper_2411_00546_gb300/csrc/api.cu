@@ -1845,7 +1845,8 @@ int build_layout(ras_problem* h, int count, const ras_problem_desc* pd, const in
                     s.voff = voff; s.noff = noff; s.goff = goff;
                     voff += 2LL * s.wx * s.wy * s.wz;
                     noff += (long long)s.wx * s.wy * s.wz;
-                    goff += (long long)s.bw * s.mp * s.mp;
+                    // wide blocks: one scratch block after the bw factor blocks
+                    goff += (long long)(s.bw + (s.mp > ras::MAX_M ? 1 : 0)) * s.mp * s.mp;
                     maxm_all = std::max(maxm_all, 2 * s.bl);
                     if (s.mp > ras::MAX_M) h->h_wide.push_back((int)h->subs.size());
                     else h->maxm = std::max(h->maxm, 2 * s.bl);

@@ -1223,47 +1223,28 @@ __device__ __forceinline__ void st_row16(T* dst, const T (&v)[BIG_PANEL]) {
     }
 }
 
-// A T in the shared memory of CTA `rank` of the cluster, at the offset of `p`
-// in this CTA's.
-template <typename T>
-__device__ __forceinline__ T ld_cluster(const T* p, uint32_t rank) {
-    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
-    uint32_t ra;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
-    if constexpr (sizeof(T) == 4) {
-        float v;
-        asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(ra) : "memory");
-        return v;
-    } else {
-        double v;
-        asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
-        return v;
-    }
-}
-
 // Factorisation of a wide-block subdomain (MAX_M < m = 2 bl <= MAX_MW) by one
 // cluster of 1024-thread CTAs (BIG_CLUSTER of them; the kernel reads the
 // cluster's size, so one CTA per subdomain works too). Block row j is formed
-// and inverted in place in its own factor slot (row-major, mp x mp):
-// S_j = D_j - beta^2 G_{j-1}, inverted by the Gauss-Jordan sweep of
-// k_local_factor_panel taken BIG_PANEL pivots at a time. The columns of the
-// block are split among the CTAs in whole panels; CTA b forms and updates its
-// own columns only. For the panel K of CTA o: thread r of CTA o holds row r
-// of the column panel in registers and sweeps it (the pivot row passed on in
-// a double-buffered shared copy, one barrier per pivot), then writes C' back
-// into M[:, K]; after one cluster barrier every CTA reads C' from there into
-// shared memory and applies
-// the rank-BIG_PANEL update to its columns: rows K become C'[K,K] M[K,J] and
-// every other row M[I,J] + C'[I,K] M[K,J]. One cluster barrier per panel
-// suffices: M[:, K] changes again only in the next panel's update, after the
-// next barrier. The partial-pivoting check is the panel kernel's (a pivot
-// smaller than an entry below it in its column, or not finite), reported by
-// CTA o in a double-buffered flag in its shared memory that the others read;
-// a block row that fails it is redone by unblocked Gauss-Jordan with row
-// interchanges (max |.| in the column, ties to the lowest row) over the
-// cluster, the interchanges undone on the columns at the end, last first.
-// Each G_j is transposed in place once the next block row has read it (G_{W-1}
-// at the end), while it is still in L2: the wide solves read G_j column-major.
+// and inverted in place in its own factor slot (mp x mp): S_j = D_j -
+// beta^2 G_{j-1}, inverted by Gauss-Jordan elimination with partial pivoting
+// (max |.| among the rows not yet pivots, ties to the lowest row), BIG_PANEL
+// pivots at a time and with implicit interchanges: rows never move, perm[k]
+// records the row that pivots column k, and the slot ends up holding
+// S_j^-1[k][c] at (perm[k], perm^-1[c]). The columns of the block are split
+// among the CTAs in whole panels; CTA b forms and updates its own columns only.
+// For the panel K of CTA o: thread r of CTA o holds row r of the column panel
+// in registers and sweeps it (per pivot: an argmax over the CTA, the pivot row
+// passed on in shared memory), writes C' back into M[:, K] and publishes the
+// panel's pivot rows P in its shared memory; after one cluster barrier every
+// CTA reads C' and P and applies the rank-BIG_PANEL update to its columns: the
+// rows of P become C'[P,K] M[P,J] and every other row M[I,J] + C'[I,K] M[P,J].
+// One cluster barrier per panel suffices: M[:, K] changes again only in the
+// next panel's update, after the next barrier. Once block row j + 1 has read
+// G_j (through the pivoting, by gathers that hit L2), slot j is rewritten in
+// plain column-major order through a scratch block (the wide solves read G_j
+// column-major). A pivot that is 0 or not finite stops the subdomain with
+// ST_ESINGULAR.
 template <typename T>
 __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, const int* __restrict__ list,
                                                                   const SubDev* __restrict__ subs,
@@ -1271,20 +1252,22 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
                                                                   const double* X, LocalState* ls,
                                                                   const double* cpool, double* coef, T* gpool,
                                                                   int only_active) {
-    constexpr int NTH = BIG_THREADS, NWB = NTH / 32, RB = BIG_PANEL, CS = RB;
+    constexpr int NTH = BIG_THREADS, NWB = NTH / 32, RB = BIG_PANEL;
     static_assert(MAX_MW <= NTH, "one panel row per thread in the sweep");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* Cs = reinterpret_cast<T*>(smem_raw);   // C' of the panel: row r at Cs + r * CS
-    T* Rs = Cs + MAX_MW * CS;                 // row panel: pivot kk at Rs + kk * MAX_MW
-    T* colk = Rs + RB * MAX_MW;               // pivot column of the pivoted fallback
-    T* prow = colk + MAX_MW;                  // pivot row of the sweep, two copies
-    __shared__ int piv[MAX_MW];
+    T* Cs = reinterpret_cast<T*>(smem_raw);   // C' of the panel: row r at Cs + r * RB
+    T* Rs = Cs + MAX_MW * RB;                 // pivot rows of the panel: kk at Rs + kk * MAX_MW
+    T* prow = Rs + RB * MAX_MW;               // the pivot row of the current pivot
+    __shared__ int perm[MAX_MW];              // perm[k]: row pivoting column k (this block row)
+    __shared__ int pprev[MAX_MW], rprev[MAX_MW];   // perm of block row j - 1 and its inverse
+    __shared__ unsigned char used[MAX_MW];    // row already a pivot row in this block row
+    __shared__ unsigned char inp[MAX_MW];     // row is a pivot row of the current panel
     __shared__ T red_v[NWB];
     __shared__ int red_i[NWB];
-    __shared__ int sh_fail, sh_r;
-    __shared__ int sh_bad[2];                 // pivoting check of the last two panels this CTA swept
-    __shared__ int pub_row[2];                // pivoted fallback: the pivot rows this CTA published
-    __shared__ T pub_col[2 * MAX_MW];         // and the columns k (after the interchange)
+    __shared__ int sh_p;                      // pivot row of the current pivot (-1: singular)
+    __shared__ int pk[RB];                    // pivot rows of the current panel (every CTA)
+    __shared__ int pub[2][RB];                // pivot rows of the panels this CTA swept
+    __shared__ int pubf[2];                   // and whether a pivot was 0 or not finite
     const uint32_t nct = cluster_size(), rank = cluster_rank();
     const int sidx = (int)(blockIdx.x / nct);
     if (sidx >= count) return;
@@ -1317,13 +1300,13 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
             cc[q] = d2 * p - 1.0;
         }
     }
-    if (tid == 0) sh_fail = 0;
     __threadfence();
     cluster_sync();   // coefficients of the whole box written
 
     const T tbeta = (T)beta, tbeta2 = (T)(beta * beta), tdiag = (T)P.diag;
     T* G = static_cast<T*>(s.gptr);
     const long long blk = (long long)mp * mp;
+    T* scratch = G + (long long)W * blk;      // one more block after the bw factor blocks
     auto dval = [&](int j, int r, int c) -> T {   // entry (r, c) of D_j
         const int ix = r >> 1, f = r & 1, cx = c >> 1, cf = c & 1;
         const int q = j * s.bl + ix;
@@ -1333,47 +1316,52 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
         }
         return (cf == f && row_neighbour(ix, cx, s.wx, cube)) ? -tbeta : (T)0;
     };
-    // columns [c0, c0 + nc) of M = S_j; G_{j-1} row-major, or column-major once transposed
-    auto form = [&](int j, T* M, int c0, int nc, bool gp_colmajor) {
+    // own columns of M = S_j; G_{j-1}[r][c] = slot j-1 at (pprev[r], rprev[c])
+    auto form = [&](int j, T* M) {
         const T* Gp = G + (long long)(j > 0 ? j - 1 : 0) * blk;
-        for (int e = tid; e < m * nc; e += NTH) {
-            const int r = e / nc, c = c0 + (e - r * nc);
-            const long long gi = gp_colmajor ? (long long)c * mp + r : (long long)r * mp + c;
-            const T g = (j > 0) ? -tbeta2 * Gp[gi] : (T)0;
+        for (int e = tid; e < m * ncol; e += NTH) {
+            const int r = e / ncol, c = cl + (e - r * ncol);
+            const T g = (j > 0) ? -tbeta2 * Gp[(long long)pprev[r] * mp + rprev[c]] : (T)0;
             M[(long long)r * mp + c] = g + dval(j, r, c);
         }
     };
-    // G_j to column-major in place, while it is still in L2: CTA b swaps the
-    // pairs (r, c), r < c, of its own columns c
-    auto transpose = [&](int j) {
+    // slot j (pivoting pprev / rprev) to plain column-major order: copy the
+    // own columns to the scratch block, then write rows c of the storage
+    // (column c of G_j) from it
+    auto finalize = [&](int j) {
         T* M = G + (long long)j * blk;
         for (int e = tid; e < m * ncol; e += NTH) {
             const int r = e / ncol, c = cl + (e - r * ncol);
-            if (r < c) {
-                const T a = M[(long long)r * mp + c];
-                M[(long long)r * mp + c] = M[(long long)c * mp + r];
-                M[(long long)c * mp + r] = a;
-            }
+            scratch[(long long)r * mp + c] = M[(long long)r * mp + c];
+        }
+        __threadfence();
+        cluster_sync();   // the whole slot copied
+        for (int e = tid; e < ncol * m; e += NTH) {
+            const int c = cl + e / m, k = e - (e / m) * m;
+            M[(long long)c * mp + k] = scratch[(long long)pprev[k] * mp + rprev[c]];
         }
     };
     const int mc = ((ncol + 31) / 32) * 32;        // update: own columns padded to whole warps,
     const int rows_par = (mc > 0) ? NTH / mc : 1;  // rows_par threads per column
     const int ucol = (mc > 0) ? tid % mc : 0, urow = (mc > 0) ? tid / mc : NTH;
+    for (int r = tid; r < MAX_MW; r += NTH) inp[r] = 0;
 
     bool failed = false;
     for (int j = 0; j < W && !failed; ++j) {
         T* M = G + (long long)j * blk;
-        form(j, M, cl, ncol, false);
+        // G_{j-1}[r][c] lies in other CTAs' columns: every update of block row j - 1 is done first
+        if (j > 0) cluster_sync();
+        form(j, M);
         if (j > 0) {
             cluster_sync();   // every CTA has read G_{j-1}
-            transpose(j - 1);
+            finalize(j - 1);
         }
-        bool viol = false;   // the pivoting check failed (the same on every thread of the cluster)
+        for (int r = tid; r < m; r += NTH) used[r] = 0;
         __syncthreads();
         for (int k0 = 0; k0 < m; k0 += RB) {
             const int nk = min(RB, m - k0);
             const uint32_t owner = (uint32_t)(k0 / pw);
-            // the owner's flag slot: parity of its panels before this one in the block row
+            // the owner's slot: parity of its panels before this one in the block row
             const int slot = ((k0 - (int)owner * pw) / RB) & 1;
             if (rank == owner) {
                 // thread r < m: row r of the column panel in registers
@@ -1384,52 +1372,81 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
                     for (int kk = 0; kk < RB; ++kk)
                         if (kk >= nk) v[kk] = (T)0;
                 }
-                if (tid == k0) {
-#pragma unroll
-                    for (int c = 0; c < RB; ++c) prow[c] = v[c];
-                }
-                __syncthreads();
-                bool bad = false;
+                int fail = 0;
 #pragma unroll
                 for (int kk = 0; kk < RB; ++kk) {
-                    if (kk < nk) {
-                        const T* pv = prow + (kk & 1) * RB;   // the pivot row, after pivot kk - 1
-                        const int r0 = k0 + kk;
-                        const T d = pv[kk], ad = fabs(d);
-                        const T inv = (T)1 / d;
-                        if (tid == r0) {
-                            bad |= !(ad > (T)0 && ad < (T)INFINITY);
+                    if (kk < nk && !fail) {
+                        // pivot: max |.| of column kk among the rows not yet pivots
+                        T best = (tid < m && !used[tid]) ? fabs(v[kk]) : (T)-1;
+                        int bi = (tid < m && !used[tid]) ? tid : 0x7fffffff;
 #pragma unroll
-                            for (int c = 0; c < RB; ++c) v[c] = (c == kk) ? inv : pv[c] * inv;
-                        } else if (tid < m) {
-                            const T f = v[kk];
-                            bad |= (tid > r0) && (fabs(f) > ad);
-#pragma unroll
-                            for (int c = 0; c < RB; ++c) {
-                                const T t = (c == kk) ? inv : pv[c] * inv;
-                                v[c] = fma(-f, t, (c == kk) ? (T)0 : v[c]);
-                            }
-                            if (tid == r0 + 1 && kk + 1 < nk) {
-#pragma unroll
-                                for (int c = 0; c < RB; ++c) prow[((kk + 1) & 1) * RB + c] = v[c];
-                            }
+                        for (int off = 16; off > 0; off >>= 1) {
+                            const T ob = __shfl_xor_sync(0xffffffffu, best, off);
+                            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                        }
+                        if (lane == 0) {
+                            red_v[warp] = best;
+                            red_i[warp] = bi;
                         }
                         __syncthreads();
+                        if (warp == 0) {
+                            best = (lane < NWB) ? red_v[lane] : (T)-1;
+                            bi = (lane < NWB) ? red_i[lane] : 0x7fffffff;
+#pragma unroll
+                            for (int off = 16; off > 0; off >>= 1) {
+                                const T ob = __shfl_xor_sync(0xffffffffu, best, off);
+                                const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                            }
+                            if (lane == 0) sh_p = (bi < m && best > (T)0 && best < (T)INFINITY) ? bi : -1;
+                        }
+                        __syncthreads();
+                        const int p = sh_p;
+                        if (p < 0) {
+                            fail = 1;   // the same on every thread
+                        } else {
+                            if (tid == p) {
+#pragma unroll
+                                for (int c = 0; c < RB; ++c) prow[c] = v[c];
+                                used[p] = 1;
+                            }
+                            if (tid == 0) pub[slot][kk] = p;
+                            __syncthreads();
+                            const T inv = (T)1 / prow[kk];
+                            if (tid == p) {
+#pragma unroll
+                                for (int c = 0; c < RB; ++c) v[c] = (c == kk) ? inv : prow[c] * inv;
+                            } else if (tid < m) {
+                                const T f = v[kk];
+#pragma unroll
+                                for (int c = 0; c < RB; ++c) {
+                                    const T t = (c == kk) ? inv : prow[c] * inv;
+                                    v[c] = fma(-f, t, (c == kk) ? (T)0 : v[c]);
+                                }
+                            }
+                        }
                     }
                 }
-                const int b = __syncthreads_or(bad) ? 1 : 0;
-                if (tid == 0) sh_bad[slot] = b;
+                if (tid == 0) pubf[slot] = fail;
                 // C' into M[:, K] (columns past m are padding) and into shared memory
-                if (tid < m) {
+                if (!fail && tid < m) {
                     st_row16<T>(M + (long long)tid * mp + k0, v);
-                    st_row16<T>(Cs + tid * CS, v);
+                    st_row16<T>(Cs + tid * RB, v);
                 }
                 __threadfence();
             }
-            cluster_sync();   // C' of panel K and its flag visible to the cluster
-            if (ld_cluster_int(&sh_bad[slot], owner)) {
-                viol = true;
+            cluster_sync();   // C' of panel K and its pivot rows visible to the cluster
+            if (ld_cluster_int(&pubf[slot], owner)) {
+                failed = true;
                 break;
+            }
+            if (tid < nk) {
+                const int p = ld_cluster_int(&pub[slot][tid], owner);
+                pk[tid] = p;
+                perm[k0 + tid] = p;
+                used[p] = 1;
+                inp[p] = 1;
             }
             if (rank != owner && tid < m) {
                 T v[RB];
@@ -1437,12 +1454,13 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
 #pragma unroll
                 for (int kk = 0; kk < RB; ++kk)
                     if (kk >= nk) v[kk] = (T)0;
-                st_row16<T>(Cs + tid * CS, v);
+                st_row16<T>(Cs + tid * RB, v);
             }
+            __syncthreads();
             for (int e = tid; e < RB * ncol; e += NTH) {
                 const int kk = e / ncol, c = cl + (e - kk * ncol);
                 Rs[kk * MAX_MW + c] =
-                    (kk < nk && (c < k0 || c >= k0 + nk)) ? M[(long long)(k0 + kk) * mp + c] : (T)0;
+                    (kk < nk && (c < k0 || c >= k0 + nk)) ? M[(long long)pk[kk] * mp + c] : (T)0;
             }
             __syncthreads();
             if (ucol < ncol && urow < rows_par) {
@@ -1458,7 +1476,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
 #pragma unroll
                         for (int u = 0; u < UR; ++u) {
                             const int r = r0 + u * rows_par;
-                            acc[u] = (r < m && (r < k0 || r >= k0 + nk)) ? M[(long long)r * mp + c] : (T)0;
+                            acc[u] = (r < m && !inp[r]) ? M[(long long)r * mp + c] : (T)0;
                         }
 #pragma unroll
                         for (int u = 0; u < UR; ++u) {
@@ -1466,12 +1484,12 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
                             if (r < m) {
                                 if constexpr (sizeof(T) == 4) {
                                     T cv[RB];
-                                    ld_row16<T>(Cs + r * CS, cv);
+                                    ld_row16<T>(Cs + r * RB, cv);
 #pragma unroll
                                     for (int kk = 0; kk < RB; ++kk) acc[u] = fma(cv[kk], rv[kk], acc[u]);
                                 } else {
 #pragma unroll
-                                    for (int kk = 0; kk < RB; ++kk) acc[u] = fma(Cs[r * CS + kk], rv[kk], acc[u]);
+                                    for (int kk = 0; kk < RB; ++kk) acc[u] = fma(Cs[r * RB + kk], rv[kk], acc[u]);
                                 }
                                 M[(long long)r * mp + c] = acc[u];
                             }
@@ -1480,106 +1498,16 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
                 }
             }
             __syncthreads();
+            if (tid < nk) inp[pk[tid]] = 0;
         }
-        if (!viol) continue;
-        // Gauss-Jordan with row interchanges over the cluster: the owner of
-        // column k picks the pivot row and publishes it with column k (after
-        // the interchange); every CTA applies the interchange, the scaling of
-        // row k and the elimination to its own columns. One cluster barrier
-        // per pivot; the published copies alternate between two buffers.
-        cluster_sync();   // every CTA has stopped writing the block
-        form(j, M, cl, ncol, true);
+        if (failed) break;
+        // this block row's pivoting becomes the previous one's
         __syncthreads();
-        for (int k = 0; k < m; ++k) {
-            const uint32_t owner = (uint32_t)(k / pw);
-            const int sl = k & 1;
-            if (rank == owner) {
-                T best = (T)-1;
-                int bi = 0x7fffffff;
-                for (int r = k + tid; r < m; r += NTH) {
-                    const T v = fabs(M[(long long)r * mp + k]);
-                    if (v > best) { best = v; bi = r; }
-                }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    const T ob = __shfl_xor_sync(0xffffffffu, best, off);
-                    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-                    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-                }
-                if (lane == 0) {
-                    red_v[warp] = best;
-                    red_i[warp] = bi;
-                }
-                __syncthreads();
-                if (warp == 0) {
-                    best = (lane < NWB) ? red_v[lane] : (T)-1;
-                    bi = (lane < NWB) ? red_i[lane] : 0x7fffffff;
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) {
-                        const T ob = __shfl_xor_sync(0xffffffffu, best, off);
-                        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-                        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-                    }
-                    if (lane == 0)
-                        pub_row[sl] = (bi >= m || !(best > (T)0) || !(best < (T)INFINITY)) ? -1 : bi;
-                }
-                __syncthreads();
-                const int pr = pub_row[sl];
-                if (pr >= 0) {
-                    for (int r = tid; r < m; r += NTH) {
-                        const int rs = (r == k) ? pr : ((r == pr) ? k : r);
-                        pub_col[sl * MAX_MW + r] = M[(long long)rs * mp + k];
-                    }
-                }
-            }
-            cluster_sync();   // pivot row and column k published
-            const int pr = ld_cluster_int(&pub_row[sl], owner);
-            if (pr < 0) {
-                if (tid == 0) sh_fail = 1;
-                break;
-            }
-            for (int r = tid; r < m; r += NTH) colk[r] = ld_cluster<T>(&pub_col[sl * MAX_MW + r], owner);
-            if (tid == 0) piv[k] = pr;
-            __syncthreads();
-            const T inv = (T)1 / colk[k];
-            for (int c = cl + tid; c < ch; c += NTH) {
-                T a = M[(long long)k * mp + c];
-                if (pr != k) {
-                    const T b = M[(long long)pr * mp + c];
-                    M[(long long)pr * mp + c] = a;
-                    a = b;
-                }
-                M[(long long)k * mp + c] = ((c == k) ? (T)1 : a) * inv;
-            }
-            __syncthreads();
-            for (int e = tid; e < m * ncol; e += NTH) {
-                const int r = e / ncol, c = cl + (e - r * ncol);
-                if (r == k) continue;
-                const T old = (c == k) ? (T)0 : M[(long long)r * mp + c];
-                M[(long long)r * mp + c] = old - colk[r] * M[(long long)k * mp + c];
-            }
-            __syncthreads();
+        for (int r = tid; r < m; r += NTH) {
+            pprev[r] = perm[r];
+            rprev[perm[r]] = r;
         }
         __syncthreads();
-        failed = sh_fail != 0;   // the same on every CTA: all read the same published rows
-        if (!failed) {
-            // undo the interchanges on the columns, last first: CTA b swaps
-            // within its share of the rows
-            cluster_sync();   // every CTA's elimination is done
-            const int rw = (m + (int)nct - 1) / (int)nct;
-            const int rl = min(m, (int)rank * rw), rh = min(m, rl + rw);
-            for (int k = m - 1; k >= 0; --k) {
-                const int pr = piv[k];
-                if (pr == k) continue;
-                for (int r = rl + tid; r < rh; r += NTH) {
-                    const T a = M[(long long)r * mp + k];
-                    M[(long long)r * mp + k] = M[(long long)r * mp + pr];
-                    M[(long long)r * mp + pr] = a;
-                }
-            }
-        }
-        __threadfence();
-        cluster_sync();   // the block visible to the cluster
     }
     if (failed) {
         if (rank == 0 && tid == 0) {
@@ -1588,7 +1516,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_local_factor_big(int count, con
         }
     } else {
         cluster_sync();   // every CTA's last update is done
-        transpose(W - 1);
+        finalize(W - 1);
     }
     cluster_sync();   // no CTA leaves while another may read its shared memory
 }
@@ -1688,7 +1616,7 @@ cudaError_t launch_local_factor_big(cudaStream_t st, int count, const int* list,
                                     const ProbDev* probs, const double* X, LocalState* ls, const double* cpool,
                                     double* coef, T* gpool, int only_active) {
     if (count <= 0) return cudaSuccess;
-    const size_t sm = (size_t)(MAX_MW * BIG_PANEL + BIG_PANEL * MAX_MW + MAX_MW + 2 * BIG_PANEL) * sizeof(T);
+    const size_t sm = (size_t)(2 * MAX_MW * BIG_PANEL + BIG_PANEL) * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(k_local_factor_big<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     // one cluster of BIG_CLUSTER CTAs per subdomain, fewer if the device cannot place that many

@@ -61,7 +61,7 @@ struct SubDev {
     int bl, bw;               // nodes per block row and block rows (wx, wy; wx*wy, wz on the cube)
     int mp;                   // 2*bl rounded up to a multiple of 32 (packed block size)
     int pad_;
-    long long goff;           // factor offset (elements of T); bw blocks of mp*mp
+    long long goff;           // factor offset (elements of T); bw blocks of mp*mp (bw + 1 for wide blocks)
     long long voff;           // local-vector offset (doubles), length 2*wx*wy*wz
     long long noff;           // node-array offset (doubles), length wx*wy*wz
     void* gptr;               // this subdomain's factor blocks (bw blocks of mp*mp T)
@@ -338,9 +338,10 @@ cudaError_t launch_local_factor(cudaStream_t st, int nsub, int maxm, const SubDe
                                 const double* cpool, double* coef, T* gpool, int only_active);
 // Factorisation of the `count` wide-block subdomains in `list` (device
 // indices, MAX_M < 2*bl <= MAX_MW): one cluster of BIG_CLUSTER 1024-thread
-// CTAs each, the block in its own factor slot in HBM (blocked Gauss-Jordan,
-// panels of BIG_PANEL pivots staged in shared memory, the columns split among
-// the CTAs), G_j stored column-major.
+// CTAs each, the block in its own factor slot in HBM (blocked Gauss-Jordan
+// with partial pivoting by implicit interchanges, panels of BIG_PANEL pivots,
+// the columns split among the CTAs), G_j stored column-major. Each such
+// subdomain has one scratch block after its bw factor blocks.
 template <typename T>
 cudaError_t launch_local_factor_big(cudaStream_t st, int count, const int* list, const SubDev* subs,
                                     const ProbDev* probs, const double* X, LocalState* ls, const double* cpool,
