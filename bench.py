@@ -320,7 +320,7 @@ def measure_cfg2(ras, torch, dev, stream):
                                         for r in rows)}
 
 
-def measure_paper_workload(ras, torch, dev, stream, only=None):
+def measure_paper_workload(ras, torch, dev, stream, only=None, graphs=True):
     """The paper's model problem (Sec. 4): n = 450, phi = kappa (y^3 +
     exp(kappa y)), kappa = 0.1, nu = 1e-6, mu = 1, f = 0, pbar = 1.3 mu
     sin(10 pi x1) sin(10 pi x2), ybar and y_d from ras_manufacture at eps =
@@ -331,7 +331,8 @@ def measure_paper_workload(ras, torch, dev, stream, only=None):
     seconds per solve) timed on their first solve; each with its distance to
     the manufactured pair (which solves the eps = 1e-15 system). The paper's
     schedule down to eps_min = 1e-15 runs on 10 x 10, 6 x 2, 15 x 15, 2 x 2
-    and 2 x 5. only: layouts "SXxSY" to run (None: all)."""
+    and 2 x 5. only: layouts "SXxSY" to run (None: all); graphs False runs
+    every kernel step by step (as --no-graphs does for the main leg)."""
     import numpy as np
     from paper_2411_00546_gb300 import inputs
     n, nu, mu, kappa = 450, 1e-6, 1.0, 0.1
@@ -347,6 +348,8 @@ def measure_paper_workload(ras, torch, dev, stream, only=None):
         if only is not None and "%dx%d" % (sx, sy) not in only:
             continue
         h = ras.ras_create(n, sx, sy, 2, ras.RAS_PHI_KAPPA, nu, mu, yd, None, o, stream=stream.cuda_stream)
+        if not graphs:
+            ras.ras_use_graphs(h, False)
         if t_make is None:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -381,6 +384,8 @@ def measure_paper_workload(ras, torch, dev, stream, only=None):
         if only is not None and "%dx%d" % (sx, sy) not in only:
             continue
         h = ras.ras_create(n, sx, sy, 2, ras.RAS_PHI_KAPPA, nu, mu, yd, None, o15, stream=stream.cuda_stream)
+        if not graphs:
+            ras.ras_use_graphs(h, False)
         y = torch.zeros_like(pbar)
         p = torch.zeros_like(pbar)
         for rep in range(1 if (sx, sy) in wide else 2):
@@ -1257,7 +1262,8 @@ def main():
     paper = None
     if rank == 0 and not args.no_paper:
         paper = measure_paper_workload(ras, torch, dev, stream,
-                                       args.paper_layouts.split(",") if args.paper_layouts else None)
+                                       args.paper_layouts.split(",") if args.paper_layouts else None,
+                                       graphs=not args.no_graphs)
     active = None
     if rank == 0 and not args.no_active and args.workload == "n1023":
         active = measure_active(ras, torch, dev, stream)

@@ -2,8 +2,9 @@
 2 x s and small s x s layouts) against the oracle: the RASPEN function with
 per-subdomain local counts, its Jacobian action, the linear RAS
 preconditioner, full RASPEN and Newton_RAS solves in FP64 and mixed precision
-with equal outer and local counts, the pivoting fallback, a batch mixing wide
-and narrow blocks, and the upper limit. Same bars as the other parity tests."""
+with equal outer and local counts, a case that needs row interchanges, a
+batch mixing wide and narrow blocks, and the upper limit. Same bars as the
+other parity tests."""
 import numpy as np
 import pytest
 
@@ -150,8 +151,9 @@ def test_wide_newton_ras_solve(prec, tol):
 
 def test_wide_pivoting_fallback():
     """nu tiny on one 90 x 90 subdomain (180 unknowns per block row): the
-    coupling (1/nu)(1 - P_eps') dwarfs the diagonal, the blocked inversion's
-    check fails and the block rows are redone with row interchanges."""
+    coupling (1/nu)(1 - P_eps') dwarfs the diagonal, so partial pivoting must
+    interchange rows (the oracle's band LU does, and so does the wide-block
+    kernel's blocked sweep)."""
     n, nu = 90, 1e-9
     cfg = inputs.problem("n63", n=n, sx=1, sy=1, overlap=0, nu=nu, mu=1e-3, eps0=1e-1, eps_min=1e-3)
     yd = 3.0 * inputs.yd_fourier(n, 11)
