@@ -142,10 +142,11 @@ int ras_default_opts(ras_opts* o);
  * has 2*wx <= 512 unknowns (wx = subdomain width in nodes, overlap included)
  * -> RAS_EINVAL. Rows of up to 160 unknowns take the register-tile
  * factorisation and the streamed solves; wider ones (the paper's 2 x s and
- * small s x s layouts) a factorisation of the block in its HBM slot by one
- * 1024-thread CTA and solves with plain loads, one CTA per subdomain. Partial
- * pivoting is checked per block (on S_j for narrow rows, on S_j^T for wide
- * ones) and a block that needs row interchanges is redone with them.
+ * small s x s layouts) a factorisation of the block in its HBM slot by a
+ * cluster of eight 1024-thread CTAs, and solves that stream the blocks by TMA,
+ * one CTA per subdomain. Narrow rows check partial pivoting per block and
+ * redo a block that needs row interchanges with them; wide rows pivot inside
+ * their blocked elimination (partial pivoting with implicit interchanges).
  * On success *out receives the handle. */
 int ras_create(int n, int sx, int sy, int overlap, int phi, double nu, double mu,
                const double* y_d, const double* f, const ras_opts* o,

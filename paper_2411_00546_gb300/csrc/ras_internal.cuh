@@ -21,9 +21,11 @@
 //                     contiguous slabs, one per group of 32 rows, and thread t
 //                     of a 256-thread CTA finds its share of every slab as
 //                     contiguous 16-byte vectors. Wide blocks (MAX_M < 2*bl
-//                     <= MAX_MW) are stored transposed instead: element
-//                     (r, c) of G_j at c*mp + r (column-major), so that the
-//                     threads of a CTA, one row each, read a column together.
+//                     <= MAX_MW) are stored column-major instead: element
+//                     (r, c) of G_j at c*mp + r, so that the threads of a
+//                     CTA, one row each, read a column together.
+//                     A wide-block subdomain has one more block after its bw
+//                     factor blocks: the factorisation's scratch.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -61,7 +63,7 @@ struct SubDev {
     int bl, bw;               // nodes per block row and block rows (wx, wy; wx*wy, wz on the cube)
     int mp;                   // 2*bl rounded up to a multiple of 32 (packed block size)
     int pad_;
-    long long goff;           // factor offset (elements of T); bw blocks of mp*mp (bw + 1 for wide blocks)
+    long long goff;           // factor offset (elements of T); bw blocks of mp*mp
     long long voff;           // local-vector offset (doubles), length 2*wx*wy*wz
     long long noff;           // node-array offset (doubles), length wx*wy*wz
     void* gptr;               // this subdomain's factor blocks (bw blocks of mp*mp T)
@@ -373,7 +375,8 @@ cudaError_t launch_local_precond(cudaStream_t st, int nsub, int ctas_per_sm, con
                                  const ProbDev* probs, const T* gpool, T* wpool, const double* R,
                                  double* Z, int* err, const int* order, int* ticket);
 // The same three solves for the `count` wide-block subdomains of `list` (one
-// 256-thread CTA each, the transposed factor blocks read with plain loads).
+// 256-thread CTA each, the column-major factor blocks streamed by TMA as
+// chunks of whole columns).
 // The kernels above skip wide-block subdomains.
 template <typename T>
 cudaError_t launch_local_direction_wide(cudaStream_t st, int count, const int* list, const SubDev* subs,
