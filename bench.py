@@ -694,6 +694,55 @@ def measure_methods(ras, torch, dev, stream):
     return out
 
 
+def measure_paper_methods(ras, torch, dev, stream):
+    """The paper's own comparison (Sec. 5, its tables for the 2 x 2 and 2 x 5
+    decompositions at eps_min = 1e-15): the model problem of Sec. 4 at n = 450
+    (manufactured pbar, y_d from ras_manufacture), overlap 2, the paper's
+    schedule (eps0 = 1, gamma = 1/5, sigma = 1.1, tol 1e-10, inner tol 1e-8),
+    mixed precision; RASPEN and Newton_RAS without continuation (eps0 =
+    eps_min) and with it. Per run: outer iterations, GMRES steps per outer
+    iteration, local Newton steps (sum over subdomains and evaluations, and the
+    largest per subdomain), time (CUDA events), and the distance to the
+    manufactured pair."""
+    import numpy as np
+    from paper_2411_00546_gb300 import inputs
+    n, nu, mu, kappa = 450, 1e-6, 1.0, 0.1
+    pbar = torch.tensor(inputs.yd_manufactured_paper(n, mu, 5), dtype=torch.float64, device=dev)
+    ybar = torch.zeros_like(pbar)
+    yd = torch.zeros_like(pbar)
+    o0 = ras.make_opts(precision=ras.RAS_MIXED, kappa=kappa)
+    h = ras.ras_create(n, 10, 10, 2, ras.RAS_PHI_KAPPA, nu, mu, yd, None, o0, stream=stream.cuda_stream)
+    ras.ras_manufacture(h, pbar, 1e-15, ybar, yd)
+    ras.ras_destroy(h)
+    ybn, pbn = ybar.cpu().numpy(), pbar.cpu().numpy()
+    out = {"workload": "Sec. 4 model problem, n=450, kappa (y^3 + exp(kappa y)), nu=1e-6, mu=1, overlap 2, "
+                       "eps_min 1e-15 (eps0 1, gamma 1/5 with continuation), mixed precision", "rows": []}
+    for sx, sy in ((2, 2), (2, 5)):
+        for name, fn in (("RASPEN", ras.ras_raspen_solve), ("Newton_RAS", ras.ras_newton_ras_solve)):
+            for cont in (False, True):
+                o = ras.make_opts(precision=ras.RAS_MIXED, tol=1e-10, inner_tol=1e-8, sigma=1.1, gamma=0.2,
+                                  eps_min=1e-15, eps0=1.0 if cont else 1e-15, kappa=kappa)
+                h = ras.ras_create(n, sx, sy, 2, ras.RAS_PHI_KAPPA, nu, mu, yd, None, o, stream=stream.cuda_stream)
+                y = torch.zeros_like(pbar)
+                p = torch.zeros_like(pbar)
+                torch.cuda.synchronize(dev)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                rc, st = fn(h, y, p, check=False)
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                ras.ras_destroy(h)
+                yn, pn = y.cpu().numpy(), p.cpu().numpy()
+                out["rows"].append({
+                    "layout": "%dx%d" % (sx, sy), "method": name + ("_eps" if cont else ""), "status": rc,
+                    "outer": st.outer_its, "gmres_per_outer": round(st.gmres_its / max(st.outer_its, 1), 1),
+                    "evaluations": st.evaluations, "inner_its_sum": st.inner_its_sum,
+                    "inner_its_max": st.inner_its_max, "ms": round(a.elapsed_time(b), 2),
+                    "dist_y": float(np.abs(yn - ybn).max() / np.abs(ybn).max()),
+                    "dist_p": float(np.abs(pn - pbn).max() / np.abs(pbn).max())})
+    return out
+
+
 def max_over_ranks(value, dist, device):
     """Largest per-rank value over all ranks (the value itself without a
     process group). The whole-job time of a replicated step is the slowest
@@ -731,6 +780,9 @@ def parse_args():
     ap.add_argument("--no-active", action="store_true")
     ap.add_argument("--no-sensitivity", action="store_true")
     ap.add_argument("--no-cube", action="store_true")
+    ap.add_argument("--paper-methods", action="store_true",
+                    help="also run RASPEN and Newton_RAS, with and without continuation, on the n = 450 "
+                         "model problem's 2 x 2 and 2 x 5 layouts (minutes)")
     ap.add_argument("--paper-layouts", default=None,
                     help="comma-separated layouts of the model-problem leg, e.g. 2x2,2x5 (default: all)")
     ap.add_argument("--no-graphs", action="store_true",
@@ -1273,6 +1325,9 @@ def main():
     cube = None
     if rank == 0 and not args.no_cube:
         cube = measure_cube(ras, torch, dev, stream)
+    paper_methods = None
+    if rank == 0 and args.paper_methods:
+        paper_methods = measure_paper_methods(ras, torch, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -1326,7 +1381,7 @@ def main():
                           "kernels": kernels, "kernel_rooflines": kernel_rooflines,
                           "uneven_batch": batch, "serving": serving, "methods": methods, "n255_family": cfg2,
                           "sweeps": sweeps, "paper_workload": paper, "n1023_active": active,
-                          "sensitivity": sensitivity, "cube": cube,
+                          "sensitivity": sensitivity, "cube": cube, "paper_methods": paper_methods,
                           "autotune": autotune,
                           "y_max": float(np.abs(y_mixed).max()),
                           "p_max": float(np.abs(p_mixed).max())},
