@@ -198,7 +198,7 @@ def measure_batch(ras, torch, dev, stream, autotune=True):
             "max_err_batched_vs_alone": err, "autotune": tuned}
 
 
-def measure_serving(ras, torch, dev, stream, count, rate=None, seq_mixed=True):
+def measure_serving(ras, torch, dev, stream, count, rate=None, seq_mixed=True, seq_fp64=True):
     """Serving: the first `count` requests of the Poisson stream (lambda = 200/s,
     seed 5, n ~ U{127,255,511,1023}) through the continuous-batching server
     (HBM budget 150 GB, up to 64 admitted), mixed precision; p50/p99 latency
@@ -260,7 +260,8 @@ def measure_serving(ras, torch, dev, stream, count, rate=None, seq_mixed=True):
         return {"p50_ms": 1e3 * serve.percentile(seq_lat, 50), "p99_ms": 1e3 * serve.percentile(seq_lat, 99),
                 "solves_per_s": len(seq_lat) / (t_free - reqs[0][0]), "solve_s_sum": sum(solve_s)}
 
-    res["sequential_fp64"] = sequential(ras.RAS_FP64)
+    if seq_fp64:
+        res["sequential_fp64"] = sequential(ras.RAS_FP64)
     if seq_mixed:
         res["sequential_mixed"] = sequential(ras.RAS_MIXED)
     return res
@@ -780,6 +781,10 @@ def parse_args():
     ap.add_argument("--no-active", action="store_true")
     ap.add_argument("--no-sensitivity", action="store_true")
     ap.add_argument("--no-cube", action="store_true")
+    ap.add_argument("--full", action="store_true",
+                    help="every study leg at full extent (about 13 minutes): the (nu, mu) sensitivity study, "
+                         "all twelve model-problem layouts and the FP64 one-at-a-time serving baseline; "
+                         "without it those are left out and the run takes a few minutes")
     ap.add_argument("--paper-methods", action="store_true",
                     help="also run RASPEN and Newton_RAS, with and without continuation, on the n = 450 "
                          "model problem's 2 x 2 and 2 x 5 layouts (minutes)")
@@ -1031,6 +1036,7 @@ def oracle_solve_timed(workload, workers):
 
 def main():
     args = parse_args()
+    t_main = time.perf_counter()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -1296,40 +1302,48 @@ def main():
 
     # the uneven batch, the serving sample and the method comparison describe
     # one GPU: rank 0 runs them (replicas would only repeat them)
-    batch = None
+    # wall seconds from start-up to here: build check, headline, FP64, e2e, profiled pass
+    leg_s = {"headline": round(time.perf_counter() - t_main, 1)}
+    print("bench: headline section %.1f s" % leg_s["headline"], file=sys.stderr, flush=True)
+
+    def leg(name, fn):
+        t0 = time.perf_counter()
+        r = fn()
+        leg_s[name] = round(time.perf_counter() - t0, 1)
+        print("bench: %s leg %.1f s" % (name, leg_s[name]), file=sys.stderr, flush=True)
+        return r
+
+    if args.paper_layouts:
+        layouts = args.paper_layouts.split(",")
+    else:
+        # the paper's own 2 x 2 and 2 x 5 layouts and one narrow layout; all twelve with --full
+        layouts = None if args.full else ["10x10", "2x2", "2x5"]
+    batch = serving = methods = cfg2 = sweeps = paper = active = sensitivity = cube = paper_methods = None
     if rank == 0 and not args.no_batch:
-        batch = measure_batch(ras, torch, dev, stream, autotune=not args.no_autotune)
-    serving = None
+        batch = leg("uneven_batch", lambda: measure_batch(ras, torch, dev, stream, autotune=not args.no_autotune))
     if rank == 0 and not args.no_serve:
-        serving = measure_serving(ras, torch, dev, stream, args.serve_requests, args.serve_rate)
-    methods = None
+        serving = leg("serving", lambda: measure_serving(ras, torch, dev, stream, args.serve_requests,
+                                                         args.serve_rate, seq_fp64=args.full))
     if rank == 0 and not args.no_methods:
-        methods = measure_methods(ras, torch, dev, stream)
-    cfg2 = None
+        methods = leg("methods", lambda: measure_methods(ras, torch, dev, stream))
     if rank == 0 and not args.no_cfg2:
-        cfg2 = measure_cfg2(ras, torch, dev, stream)
-    sweeps = None
+        cfg2 = leg("n255_family", lambda: measure_cfg2(ras, torch, dev, stream))
     if rank == 0 and not args.no_sweeps:
-        sweeps = measure_sweeps(ras, torch, dev, stream)
-    paper = None
+        sweeps = leg("sweeps", lambda: measure_sweeps(ras, torch, dev, stream))
     if rank == 0 and not args.no_paper:
-        paper = measure_paper_workload(ras, torch, dev, stream,
-                                       args.paper_layouts.split(",") if args.paper_layouts else None,
-                                       graphs=not args.no_graphs)
-    active = None
+        paper = leg("paper_workload", lambda: measure_paper_workload(ras, torch, dev, stream, layouts,
+                                                                     graphs=not args.no_graphs))
     if rank == 0 and not args.no_active and args.workload == "n1023":
-        active = measure_active(ras, torch, dev, stream)
-    sensitivity = None
-    if rank == 0 and not args.no_sensitivity:
-        sensitivity = measure_sensitivity(ras, torch, dev, stream)
-    cube = None
+        active = leg("n1023_active", lambda: measure_active(ras, torch, dev, stream))
+    if rank == 0 and args.full and not args.no_sensitivity:
+        sensitivity = leg("sensitivity", lambda: measure_sensitivity(ras, torch, dev, stream))
     if rank == 0 and not args.no_cube:
-        cube = measure_cube(ras, torch, dev, stream)
-    paper_methods = None
+        cube = leg("cube", lambda: measure_cube(ras, torch, dev, stream))
     if rank == 0 and args.paper_methods:
-        paper_methods = measure_paper_methods(ras, torch, dev, stream)
+        paper_methods = leg("paper_methods", lambda: measure_paper_methods(ras, torch, dev, stream))
 
     cpu = None
+    t_cpu = time.perf_counter()
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
             cores = host_cores()
@@ -1358,6 +1372,7 @@ def main():
                    "gpu_vs_oracle": parity}
         except Exception as exc:  # the baseline is reported, never required
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: %s" % exc}
+        leg_s["cpu_baseline"] = round(time.perf_counter() - t_cpu, 1)
 
     dev_bytes = ras.ras_device_bytes(h)
     ras.ras_destroy(h)
@@ -1382,7 +1397,7 @@ def main():
                           "uneven_batch": batch, "serving": serving, "methods": methods, "n255_family": cfg2,
                           "sweeps": sweeps, "paper_workload": paper, "n1023_active": active,
                           "sensitivity": sensitivity, "cube": cube, "paper_methods": paper_methods,
-                          "autotune": autotune,
+                          "autotune": autotune, "full": args.full, "leg_seconds": leg_s,
                           "y_max": float(np.abs(y_mixed).max()),
                           "p_max": float(np.abs(p_mixed).max())},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
