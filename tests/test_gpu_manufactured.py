@@ -1,7 +1,9 @@
 """The paper's model problem (Sec. 4) on the GPU: ras_manufacture's ybar and
 y_d against the oracle's construction, and RASPEN solves of that workload
 (phi = kappa (y^3 + exp(kappa y)), nu = 1e-6, mu = 1, eps_min = 1e-6) against
-the oracle in FP64 and mixed precision with equal counts."""
+the oracle in FP64 and mixed precision with equal counts; at the paper's
+own size (n = 450, 2 x 5 subdomains, eps_min = 1e-15) the outer iteration
+counts it prints for RASPEN and Newton_RAS with and without continuation."""
 import numpy as np
 import pytest
 
@@ -98,5 +100,45 @@ def test_paper_workload_at_the_paper_eps(n63_paper_tiny_eps, prec, tol):
         assert rel_inf(p.cpu().numpy(), ref.P) <= tol
         assert st.outer_its == ref.outer
         assert st.inner_its_sum == sum(sum(i) for i in ref.inner_its)
+    finally:
+        ras.ras_destroy(h)
+
+
+# Outer iterations the paper prints for its model problem at n = 450 with
+# eps_min = 1e-15, tol 1e-10, inner tol 1e-8, sigma = 1.1 and overlap 2h (Sec. 5,
+# its table comparing all methods on the 2 x 2 and 2 x 5 decompositions; the
+# same counts on both): Newton_RAS 40, Newton_RAS_eps 23, RASPEN 3, RASPEN_eps 3.
+PAPER_OUTER_N450 = {("raspen", False): 3, ("raspen", True): 3, ("newton_ras", False): 40,
+                    ("newton_ras", True): 23}
+
+
+@pytest.fixture(scope="module")
+def n450_paper():
+    n = 450
+    pbar = inputs.yd_manufactured_paper(n, PAPER["mu"], 5)
+    Y, yd = wl.manufactured(pbar, n)   # the oracle's state solve at eps = 1e-15
+    return n, yd, Y, pbar
+
+
+@pytest.mark.parametrize("method,cont", sorted(PAPER_OUTER_N450))
+def test_paper_outer_counts_n450_2x5(n450_paper, method, cont):
+    """The paper's own workload on its 2 x 5 decomposition in mixed precision:
+    without continuation (eps0 = eps_min) and with the paper's (eps0 = 1,
+    gamma = 1/5), RASPEN and Newton_RAS take the outer iterations the paper
+    prints and end at the manufactured pair. The paper's GMRES counts follow
+    GMRES settings it does not state, and its inner counts an average it does
+    not define, so only the outer counts are compared."""
+    n, yd, Y, pbar = n450_paper
+    o = ras.make_opts(tol=1e-10, inner_tol=1e-8, sigma=1.1, eps0=1.0 if cont else 1e-15, gamma=0.2,
+                      eps_min=1e-15, precision=ras.RAS_MIXED, kappa=PAPER["kappa"])
+    h = ras.ras_create(n, 2, 5, 2, PAPER["phi"], PAPER["nu"], PAPER["mu"], to_dev(yd), None, o)
+    try:
+        y, p = zeros(n), zeros(n)
+        solve = ras.ras_raspen_solve if method == "raspen" else ras.ras_newton_ras_solve
+        rc, st = solve(h, y, p)
+        assert rc in (ras.RAS_OK, ras.RAS_OK_FLOOR)
+        assert st.outer_its == PAPER_OUTER_N450[(method, cont)]
+        assert rel_inf(y.cpu().numpy(), Y) <= MIXED_TOL
+        assert rel_inf(p.cpu().numpy(), pbar) <= MIXED_TOL
     finally:
         ras.ras_destroy(h)
