@@ -114,3 +114,12 @@ def test_bench_names_are_all_defined():
             defined.add(node.id)
     used = {n.id for n in ast.walk(tree) if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load)}
     assert sorted(used - defined) == []
+
+
+def test_default_run_leaves_the_long_studies_to_flags(monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse_args()
+    assert (a.gpus, a.full, a.paper_methods, a.paper_layouts) == (1, False, False, None)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--full", "--paper-methods", "--paper-layouts", "2x2,2x5"])
+    a = bench.parse_args()
+    assert a.full and a.paper_methods and a.paper_layouts.split(",") == ["2x2", "2x5"]
